@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark: batched 3DGS RGB-D rendering, env-frames/s on one GB300.
+
+Workload (default): 2048 envs x 640x480, a 500k-Gaussian static room-shell
+background plus a 20-link robot with 5k Gaussians per link, per-env joint
+angles and jittered head cameras (seeded synthetic stand-in for the paper's
+scenes; paper Sec. III-C "Throughput Scaling": 2048 environments at 640x480).
+One step renders the whole batch (RGB + depth) through gs_render_batch with
+inputs resident in HBM.  `e2e` times the same batch through
+gs_render_batch_host (pinned host poses in, RGB + depth copied back).
+
+`--impl reference` times the CPU oracle (plain FP64 renderer) on a bounded
+sample of the same workload on the host cores.
+
+Multi-GPU (torchrun): envs are independent, so every rank renders its own
+replica batch (weak scaling, no data-path collective); the step time is the
+max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-frames/s at 2048x640x480 RGB-D"
+UNIT = "env-frames/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--envs", type=int, default=2048)
+    ap.add_argument("--width", type=int, default=640)
+    ap.add_argument("--height", type=int, default=480)
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-envs", type=int, default=2, help="envs in the CPU-baseline sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+
+def oracle_sample(w, envs, threads=None):
+    """Time the plain FP64 oracle on `envs` of workload w; returns (seconds, cores)."""
+    from oracle import oracle
+
+    if threads:
+        oracle.set_num_threads(threads)
+    cores = oracle.num_threads()
+    S = oracle.scene_arrays(w)
+    t0 = time.perf_counter()
+    for e in envs:
+        oracle.render_env(w, e, S=S)
+    return time.perf_counter() - t0, cores
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    from paper_2604_25459_gb300 import synth
+
+    w = synth.make_c1(n_envs=a.envs, width=a.width, height=a.height, f=500.0 * a.width / 640)
+    for k in range(a.warmup):
+        oracle_sample(w, [k % a.envs])
+    ts = []
+    cores = 1
+    for k in range(a.steps):
+        t, cores = oracle_sample(w, [(a.warmup + k) % a.envs])
+        ts.append(t)
+    tot = sum(ts)
+    val = a.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"c1: {a.envs} envs x {a.width}x{a.height}, 500k bg + 20x5k link Gaussians",
+                       "step": "one env rendered by the plain FP64 CPU oracle"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "1 env per step of the c1 workload, plain FP64 oracle"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2604_25459_gb300 import gsbatch, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    tw, th = (int(x) for x in a.tile.split("x"))
+    f = 500.0 * a.width / 640
+    w = synth.make_c1(n_envs=a.envs, width=a.width, height=a.height, f=f)
+    E, H, W = a.envs, a.height, a.width
+    scene = gsbatch.scene_from_workload(w, a.dtype)
+    scene.set_tile(tw, th)
+    poses = torch.from_numpy(w.link_poses).to(dev)
+    rgb = torch.empty((E, H, W, 3), dtype=torch.float32, device=dev)
+    depth = torch.empty((E, H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        scene.render(poses, w.cams, rgb=rgb, depth=depth, want_alpha=False, stream=stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    scene.sync_status()
+    # algorithmic work of one batch: composited (pixel, Gaussian) pairs (untimed pass)
+    scene.set_counters(True)
+    step()
+    torch.cuda.synchronize()
+    st = scene.stats()
+    n_eval = st["composited"]
+    intersections = st["intersections"]
+    launches_per_step = st["kernel_launches"]
+    scene.set_counters(False)
+
+    scene.set_profile(True)
+    scene.timings(reset=True)
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    evs[0].record(stream)
+    for k in range(a.steps):
+        step()
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    scene.set_profile(False)
+    tim = scene.timings(reset=True)
+    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(a.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    scene.sync_status()
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_step = t_max / a.steps
+    value = world * E * a.steps / (t_max / 1e3)
+
+    # roofline of the dominant kernel (compositing): plain-ALU bound.
+    comp_ms, comp_launches = tim["composite"]
+    per_launch_ms = comp_ms / max(comp_launches, 1)
+    launches_per_batch = comp_launches / a.steps
+    evals_per_launch = n_eval / max(launches_per_batch, 1)
+    ops_per_eval = 20.0  # quadratic form, ex2, alpha, T, 3 colour + 1 depth FMA (lane-ops)
+    sm_mhz = ck.get("sm_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    peak_lane_ops = props.multi_processor_count * 128 * sm_mhz * 1e6
+    achieved = evals_per_launch * ops_per_eval / (per_launch_ms / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_lane_ops / 1e9, "unit": "Glane-op/s",
+                "frac": achieved / peak_lane_ops, "traffic": None,
+                "kernel": "k_composite", "per_launch_ms": per_launch_ms,
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x median {sm_mhz:.0f} MHz "
+                              "(1 lane-op per lane per clock, FMA counted once)"}
+    phase_ms = {k: v[0] / a.steps for k, v in tim.items()}
+
+    # whole-step roofline: algorithmic HBM bytes vs FP32 work (paper's hot path, all steps)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    attr_bytes = (w.background.n + w.links.n) * (236 if a.dtype == "f32" else 132)
+    out_bytes = E * H * W * 16
+    io_bytes = attr_bytes + E * (w.n_links * 28 + 56) + out_bytes
+
+    e2e = None
+    if not a.no_e2e:
+        pin = lambda shape: torch.empty(shape, dtype=torch.float32, pin_memory=True).numpy()
+        rgb_h, depth_h = pin((E, H, W, 3)), pin((E, H, W))
+        poses_h = torch.from_numpy(w.link_poses).pin_memory().numpy()
+        scene.render_host(poses_h, w.cams, rgb_h, depth_h)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            scene.render_host(poses_h, w.cams, rgb_h, depth_h)
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * E * a.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(poses_h.nbytes + w.cams.nbytes),
+               "d2h_bytes_per_step": int(rgb_h.nbytes + depth_h.nbytes),
+               "ms_per_step": 1e3 * dt / a.e2e_steps, "api": "gs_render_batch_host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        envs = list(range(a.oracle_envs))
+        t, cores = oracle_sample(w, envs)
+        cpu = {"value": len(envs) / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"envs {envs} of the same c1 batch, plain FP64 oracle, {t:.1f} s"}
+
+    if rank == 0:
+        lat_sorted = sorted(lat)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": a.dtype if a.dtype != "f32" else "f32", "data": "synthetic",
+            "config": {"workload": f"c1: {E} envs x {W}x{H} RGB-D, 500k room-shell background + 20 links x 5k "
+                                   f"Gaussians, SH degree 3, tile {a.tile}",
+                       "envs_per_gpu": E, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": f"outputs of {out_bytes / 1e9:.1f} GB written per step (> 129 MB L2)"},
+            "mpix_per_s": value * H * W / 1e6,
+            "latency_ms": {"p50": lat_sorted[len(lat) // 2], "p99": lat_sorted[min(len(lat) - 1,
+                                                                                   int(math.ceil(0.99 * len(lat))) - 1)],
+                           "mean": sum(lat) / len(lat)},
+            "clocks": ck,
+            "roofline": roofline,
+            "step_roofline": {"io_bytes": io_bytes, "hbm_floor_ms": io_bytes / (hbm * 1e9) * 1e3,
+                              "hbm_gbs_peak": hbm, "composited_pairs": n_eval,
+                              "intersections": intersections},
+            "phase_ms_per_step": phase_ms,
+            "gpu_launches": int(launches_per_step * a.steps),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    scene.close()
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        if a.impl == "ours":
+            import torch
+
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_ours(a, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

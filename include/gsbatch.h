@@ -1,0 +1,220 @@
+/* gsbatch -- batched forward 3D Gaussian Splatting (RGB + depth) for many
+ * environments on one GB300 (sm_103a).
+ *
+ * The problem statement follows the paper's simulation loop (Sec. III-A
+ * "Data Flow"): a physics step yields rigid-body poses, Rigid-Link Gaussian
+ * Kinematics (Sec. III-C "RLGK") moves the Gaussian clusters bound to each
+ * rigid link, and the batch 3DGS renderer (Sec. III-C "Throughput Scaling",
+ * built on the 3DGS forward pass the paper cites in Sec. II-B) returns RGB
+ * images and depth maps for every environment.
+ *
+ * Conventions (the paper states none; these are the library's readings):
+ *   world z up; camera axes x right, y down, z forward (OpenCV);
+ *   a pose is a unit quaternion (w,x,y,z) then a translation;
+ *   link poses map link -> world, camera poses map world -> camera;
+ *   pixel (i,j) has its centre at (i+0.5, j+0.5);
+ *   near plane per camera, 1.3 frustum guard band, 0.3 px^2 low-pass,
+ *   alpha = min(0.99, o exp(-q/2)), alpha floor 1/255, stop when
+ *   T (1 - alpha) < 1e-4, depth order ties broken by ascending global index
+ *   (background 0..N_b-1, then link Gaussians in link-major order),
+ *   black background, rgb clamped to [0,1], depth = sum(alpha T z)/(1-T)
+ *   (0 where 1-T = 0), SH colour max(0, sum sh_k Y_k(d) + 0.5) with the view
+ *   direction d taken in the link frame for link Gaussians.
+ *
+ * Errors: every call returns a gs_status; no call throws, exits or traps.
+ * gs_last_error() returns a thread-local message for the last failure.
+ * Argument checks fail with GS_ERR_INVALID before anything is launched.
+ * Faults found on the device (a zero or non-finite pose quaternion, a
+ * capacity overflow) are recorded in the scene's device status word and
+ * reported by gs_scene_sync_status().
+ *
+ * Threading: a gs_scene may be used from one host thread at a time.
+ */
+#ifndef GSBATCH_H
+#define GSBATCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gs_scene_s* gs_scene;
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID = -1,     /* bad argument; nothing was launched */
+    GS_ERR_OOM = -2,         /* device allocation failed or the scratch budget is too small */
+    GS_ERR_CUDA = -3,        /* a CUDA runtime call failed (message in gs_last_error) */
+    GS_ERR_TIMEOUT = -4,     /* a bounded device wait gave up */
+    GS_ERR_UNSUPPORTED = -5, /* valid request outside what this build implements */
+    GS_ERR_DEVICE = -6       /* the device status word reports a fault (see gs_scene_sync_status) */
+} gs_status;
+
+typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
+
+/* A borrowed structure-of-arrays view of n Gaussians.  The library copies what
+ * it needs during the call; the caller keeps ownership.
+ *   mean      float32 [n][3]
+ *   quat      float32 [n][4]  (w,x,y,z), need not be normalised, must be non-zero
+ *   log_scale dtype   [n][3]  per-axis log standard deviation
+ *   opacity   dtype   [n]     activated opacity in (0,1]
+ *   sh        dtype   [n][sh_coeffs][3]  coefficient-major, channel-minor,
+ *             coefficient k = l*l + l + m (3DGS order), sh_coeffs = (sh_degree+1)^2
+ *   on_device non-zero if the pointers are device memory, else host memory.
+ * dtype GS_BF16 / GS_F16 applies to log_scale, opacity and sh (the storage
+ * form of the precision variant); mean and quat are always float32. */
+typedef struct {
+    int64_t n;
+    const float* mean;
+    const float* quat;
+    const void* log_scale;
+    const void* opacity;
+    const void* sh;
+    int sh_degree; /* 0..3 */
+    gs_dtype dtype;
+    int on_device;
+} gs_gaussians;
+
+/* One pinhole camera, world -> camera.  56 bytes, no padding. */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float q_cw[4]; /* (w,x,y,z) */
+    float t_cw[3];
+    float near_plane; /* > 0; 0.01 m in the standard workloads */
+} gs_camera;
+
+/* Create a scene holding a static background (world-frame Gaussians, may be
+ * empty: n = 0).  The scene owns device copies of the attributes in its own
+ * layout (per-Gaussian 3D covariance derived from quat and log_scale, SH in
+ * coefficient-plane-major order).  Uses the current CUDA device; synchronises
+ * that device.  Errors: GS_ERR_INVALID (null/negative/ill-formed view, zero
+ * quaternion), GS_ERR_OOM, GS_ERR_CUDA. */
+gs_status gs_scene_create(const gs_gaussians* background, gs_scene* out);
+
+/* Bind link-frame Gaussian clusters to n_links rigid links (RLGK, Sec. III-C):
+ * link l owns link_gaussians[link_offsets[l] .. link_offsets[l+1]) (host array
+ * of n_links+1 non-decreasing offsets, link_offsets[0] = 0,
+ * link_offsets[n_links] = link_gaussians->n).  Replaces any earlier links.
+ * The dtype and sh_degree must equal the background's (if it is non-empty).
+ * Errors as gs_scene_create. */
+gs_status gs_scene_attach_links(gs_scene s, int n_links, const int64_t* link_offsets,
+                                const gs_gaussians* link_gaussians);
+
+/* Render n_envs environments of one resolution (all cams[e].width/height equal).
+ *   link_poses  DEVICE float32 [n_envs][n_links][7], (qw,qx,qy,qz,tx,ty,tz), link -> world
+ *               (may be NULL when n_links = 0)
+ *   cams        HOST   gs_camera [n_envs]
+ *   rgb         DEVICE float32 [n_envs][H][W][3]
+ *   depth       DEVICE float32 [n_envs][H][W]
+ *   alpha       DEVICE float32 [n_envs][H][W] or NULL
+ *   cuda_stream cudaStream_t (NULL = legacy default stream)
+ * All launches are ordered on cuda_stream.  The call blocks the host once per
+ * wave of environments for a 16-byte read of the intersection total (to size
+ * the scratch), so it returns after the last wave's launches are queued, not
+ * after they finish.  Scratch memory is owned by the scene, grown on demand
+ * up to the budget (gs_scene_set_budget).  n_envs = 0 is a no-op.
+ * Errors: GS_ERR_INVALID (bad pointers or camera parameters), GS_ERR_OOM,
+ * GS_ERR_CUDA; device-side faults via gs_scene_sync_status. */
+gs_status gs_render_batch(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
+                          float* depth, float* alpha, void* cuda_stream);
+
+/* As gs_render_batch, but link_poses, rgb, depth and alpha are HOST buffers
+ * (pinned memory gives the fastest copies).  The library copies the poses in,
+ * renders wave by wave and copies each wave's images out while the next wave
+ * renders; the call returns when all images are on the host. */
+gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
+                               float* depth, float* alpha, void* cuda_stream);
+
+/* Tile shape used by the binning and compositing kernels.  Allowed:
+ * 8x8, 16x8, 16x16, 32x8 (tw x th).  Results do not depend on the tile shape
+ * (each splat's support box is inflated by a relative 1e-4 so every tile it
+ * may reach sees it).  Default 16x16. */
+gs_status gs_scene_set_tile(gs_scene s, int tile_w, int tile_h);
+
+/* Upper bound, in bytes, on the scene's device scratch (records, masks,
+ * intersection lists).  Environments are rendered in waves sized to fit.
+ * Default 64 GiB.  GS_ERR_OOM from gs_render_batch if one env does not fit. */
+gs_status gs_scene_set_budget(gs_scene s, int64_t bytes);
+
+/* Maximum environments per wave (0 = as many as the budget allows). */
+gs_status gs_scene_set_wave(gs_scene s, int max_envs_per_wave);
+
+/* Wait for the scene's work on cuda_stream, then read and clear the device
+ * status word.  GS_OK, or GS_ERR_DEVICE with a description in gs_last_error. */
+gs_status gs_scene_sync_status(gs_scene s, void* cuda_stream);
+
+/* Counters of the last gs_render_batch call (host-side values; the pair total
+ * is the sum over waves of the intersection totals read during the call). */
+typedef struct {
+    int64_t waves;          /* waves rendered */
+    int64_t kernel_launches;/* kernels launched by the call */
+    int64_t intersections;  /* (env, tile) intersections, all waves */
+    int64_t scratch_bytes;  /* device scratch currently held by the scene */
+    int64_t n_gaussians;    /* background + link Gaussians */
+    int64_t composited;     /* with counters on: (pixel, Gaussian) pairs with alpha >= 1/255
+                               examined before termination, summed since counters were enabled */
+} gs_stats;
+/* Synchronises the device when counters are on (to read the device counter). */
+gs_status gs_scene_get_stats(gs_scene s, gs_stats* out);
+
+/* Count composited (pixel, Gaussian) pairs in the compositor (adds one shared
+ * reduction and one atomic per tile; off by default).  Enabling resets the count. */
+gs_status gs_scene_set_counters(gs_scene s, int enable);
+
+/* Per-kernel device time.  With profiling on, every launch of a render is
+ * bracketed by CUDA events recorded on the render's stream; gs_scene_get_timings
+ * waits for the recorded events and returns milliseconds and launch counts per
+ * phase, accumulated since the last reset. */
+enum {
+    GS_PHASE_LINK = 0,      /* A1: link composition */
+    GS_PHASE_PROJECT = 1,   /* A2: projection + SH */
+    GS_PHASE_COUNT = 2,     /* A3: intersection counting */
+    GS_PHASE_SCAN = 3,      /* A3: prefix scans */
+    GS_PHASE_SCATTER = 4,   /* A4: bucketed key scatter */
+    GS_PHASE_COMPOSITE = 5, /* A4 sort + A5 compositing */
+    GS_PHASES = 6
+};
+typedef struct {
+    double ms[GS_PHASES];
+    int64_t launches[GS_PHASES];
+} gs_timings;
+gs_status gs_scene_set_profile(gs_scene s, int enable);
+gs_status gs_scene_get_timings(gs_scene s, gs_timings* out, int reset);
+
+/* Debug hooks for parity tests.  When enabled, the next gs_render_batch
+ * keeps, for the env of the LAST wave given by gs_debug_copy_* (local index
+ * within that wave), the projected records and the depth-sorted per-tile
+ * lists, in addition to its normal outputs (slower; off by default). */
+gs_status gs_scene_set_debug(gs_scene s, int enable);
+
+/* Copy env `env` (absolute index, must belong to the last wave rendered) of
+ * the projected records to HOST arrays of n = background + link Gaussians:
+ *   visible u8 [n]; u, v, hx, hy, z, opacity f32 [n]; conic f32 [n][3];
+ *   rgb f32 [n][3]; range i32 [n][4] (i0,i1,j0,j1).
+ * Entries of invisible Gaussians are left as they were.  Synchronises. */
+gs_status gs_debug_copy_records(gs_scene s, int env, uint8_t* visible, float* u, float* v, float* hx, float* hy,
+                                float* z, float* opacity, float* conic, float* rgb, int32_t* range);
+
+/* Copy env `env`'s per-tile intersection counts (u32 [tiles], row-major tile
+ * grid) and, if lists is non-NULL, the depth-ordered per-tile lists of global
+ * indices (u32 [sum counts], tiles in order).  Lists are available only when
+ * debug was enabled for that render.  Synchronises. */
+gs_status gs_debug_copy_tiles(gs_scene s, int env, uint32_t* counts, int64_t n_counts, uint32_t* lists,
+                              int64_t n_lists);
+
+/* Destroy a scene and free its device memory (NULL is a no-op). */
+void gs_scene_destroy(gs_scene s);
+
+/* Thread-local description of the last failure ("" if none). */
+const char* gs_last_error(void);
+
+/* Library version string. */
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSBATCH_H */

@@ -1,0 +1,202 @@
+// (env, tile) intersection counting, prefix scan and bucketed scatter of
+// depth keys (steps A3 and A4).  The renderer of the paper (Sec. III-C
+// "Throughput Scaling", built on gsplat) bins projected splats into screen
+// tiles before compositing; this file is that binning, designed for many envs.
+//
+// Each splat's support box [i0,i1]x[j0,j1] (pixels) touches the tiles
+// [i0/tw, i1/tw] x [j0/th, j1/th].  Counting and scattering first aggregate in
+// a shared-memory histogram per (env, block of Gaussians), so global atomics
+// are one per touched tile per block rather than one per intersection.  The
+// order inside a bucket is arbitrary; the compositor orders each bucket by the
+// unique key (depth bits << 32 | global index).
+#include "gs_internal.cuh"
+
+namespace gsb {
+
+__device__ __forceinline__ void tile_span(uint32_t rx, uint32_t ry, int tw, int th, int& tx0, int& tx1, int& ty0,
+                                          int& ty1) {
+    tx0 = (int)(rx & 0xffffu) / tw;
+    tx1 = (int)(rx >> 16) / tw;
+    ty0 = (int)(ry & 0xffffu) / th;
+    ty1 = (int)(ry >> 16) / th;
+}
+
+// grid: (blocks over mask words, envs); block 256; dynamic smem T u32
+__global__ void __launch_bounds__(256) k_count(BinParams P) {
+    extern __shared__ uint32_t hist[];
+    const int el = P.e_begin + blockIdx.y;
+    for (int t = threadIdx.x; t < P.T; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * P.words_per_block;
+    const int64_t w1 = min(w0 + (int64_t)P.words_per_block, P.mask_words);
+    const uint32_t* mask = P.mask + (size_t)el * P.mask_words;
+    const uint4* r3 = P.r3 + (size_t)el * P.G;
+    for (int64_t w = w0 + warp; w < w1; w += 8) {
+        const uint32_t m = __ldg(mask + w);
+        if ((m >> lane) & 1u) {
+            const uint4 q = r3[w * 32 + lane];
+            int tx0, tx1, ty0, ty1;
+            tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * P.ntx + tx], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t* cnt = P.counts + (size_t)el * P.T;
+    for (int t = threadIdx.x; t < P.T; t += blockDim.x) {
+        const uint32_t h = hist[t];
+        if (h) atomicAdd(cnt + t, h);
+    }
+}
+
+cudaError_t launch_count(const BinParams& P, int n_envs, cudaStream_t st, size_t smem) {
+    if (n_envs == 0) return cudaSuccess;
+    dim3 grid((unsigned)((P.mask_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_count<<<grid, 256, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- scan
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* warp_tot, T& block_total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? warp_tot[lane] : T(0);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        if (lane < nw) warp_tot[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    const T before = warp == 0 ? T(0) : warp_tot[warp - 1];
+    block_total = warp_tot[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// per env: off_local[t] = sum_{t' < t} counts[t'], env_total = sum
+__global__ void __launch_bounds__(1024) k_scan_env(const uint32_t* counts, uint32_t* off_local,
+                                                   unsigned long long* env_total, int T) {
+    __shared__ uint32_t wt[32];
+    const int el = blockIdx.x;
+    const uint32_t* c = counts + (size_t)el * T;
+    uint32_t* o = off_local + (size_t)el * T;
+    uint32_t carry = 0;
+    for (int base = 0; base < T; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const uint32_t v = t < T ? c[t] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(v, wt, tot);
+        if (t < T) o[t] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) env_total[el] = carry;
+}
+
+// env_base[e] = sum_{e' < e} env_total[e'], env_base[We] = total
+__global__ void __launch_bounds__(1024) k_scan_base(const unsigned long long* env_total, unsigned long long* env_base,
+                                                    int We) {
+    __shared__ unsigned long long wt[32];
+    unsigned long long carry = 0;
+    for (int base = 0; base < We; base += blockDim.x) {
+        const int e = base + threadIdx.x;
+        const unsigned long long v = e < We ? env_total[e] : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = block_exclusive_scan<unsigned long long>(v, wt, tot);
+        if (e < We) env_base[e] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) env_base[We] = carry;
+}
+
+cudaError_t launch_scan(const uint32_t* counts, uint32_t* off_local, unsigned long long* env_total,
+                        unsigned long long* env_base, int We, int T, cudaStream_t st) {
+    if (We == 0) return cudaSuccess;
+    k_scan_env<<<We, 1024, 0, st>>>(counts, off_local, env_total, T);
+    k_scan_base<<<1, 1024, 0, st>>>(env_total, env_base, We);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- scatter
+// Same partition as k_count.  Pass 1 rebuilds the block's histogram, then one
+// global atomic per touched tile reserves the block's range of that bucket;
+// pass 2 writes each key at (bucket start + block range + shared cursor).
+
+__global__ void __launch_bounds__(256) k_scatter(BinParams P) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* hist = sm;
+    uint32_t* base = sm + P.T;
+    const int el = P.e_begin + blockIdx.y;
+    for (int t = threadIdx.x; t < P.T; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * P.words_per_block;
+    const int64_t w1 = min(w0 + (int64_t)P.words_per_block, P.mask_words);
+    const uint32_t* mask = P.mask + (size_t)el * P.mask_words;
+    const uint4* r3 = P.r3 + (size_t)el * P.G;
+    for (int64_t w = w0 + warp; w < w1; w += 8) {
+        const uint32_t m = __ldg(mask + w);
+        if ((m >> lane) & 1u) {
+            const uint4 q = r3[w * 32 + lane];
+            int tx0, tx1, ty0, ty1;
+            tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * P.ntx + tx], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t* cur = P.cursor + (size_t)el * P.T;
+    const uint32_t* off = P.off_local + (size_t)el * P.T;
+    const unsigned long long eb = P.env_base[el] - P.pair_base;
+    for (int t = threadIdx.x; t < P.T; t += blockDim.x) {
+        const uint32_t h = hist[t];
+        if (h) base[t] = off[t] + atomicAdd(cur + t, h);
+        hist[t] = 0;
+    }
+    __syncthreads();
+    for (int64_t w = w0 + warp; w < w1; w += 8) {
+        const uint32_t m = __ldg(mask + w);
+        if ((m >> lane) & 1u) {
+            const int64_t g = w * 32 + lane;
+            const uint4 q = r3[g];
+            const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)(uint32_t)g;
+            int tx0, tx1, ty0, ty1;
+            tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    const int t = ty * P.ntx + tx;
+                    const uint32_t k = atomicAdd(&hist[t], 1u);
+                    P.pairs[eb + base[t] + k] = key;
+                }
+        }
+    }
+}
+
+cudaError_t launch_scatter(const BinParams& P, int n_envs, cudaStream_t st, size_t smem) {
+    if (n_envs == 0) return cudaSuccess;
+    dim3 grid((unsigned)((P.mask_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_scatter<<<grid, 256, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace gsb

@@ -1,0 +1,442 @@
+// Scene preparation, link composition (RLGK) and EWA projection + SH colour.
+//
+// Paper: Sec. III-C "RLGK" binds Gaussian clusters to rigid links (step A1
+// here composes each link pose with the env's camera); Sec. II-B cites the 3DGS
+// forward pass that the batch renderer of Sec. III-C "Throughput Scaling"
+// builds on (step A2: projection of every (env, Gaussian) to a 2D conic with
+// view-dependent SH colour).
+#include "gs_internal.cuh"
+
+namespace gsb {
+
+// ------------------------------------------------------------------ helpers
+
+template <int DT>
+__device__ __forceinline__ float load_val(const void* p, int64_t i) {
+    if constexpr (DT == GS_F32) {
+        return static_cast<const float*>(p)[i];
+    } else if constexpr (DT == GS_BF16) {
+        return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+    } else {
+        return __half2float(static_cast<const __half*>(p)[i]);
+    }
+}
+
+// Rotation matrix (row-major) of the normalised quaternion (w,x,y,z).
+template <typename T>
+__device__ __forceinline__ bool quat_rot(T w, T x, T y, T z, T* R) {
+    T nn = w * w + x * x + y * y + z * z;
+    if (!(nn > T(0)) || !isfinite(nn)) {
+        R[0] = 1; R[1] = 0; R[2] = 0; R[3] = 0; R[4] = 1; R[5] = 0; R[6] = 0; R[7] = 0; R[8] = 1;
+        return false;
+    }
+    T inv = T(1) / sqrt(nn);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+    return true;
+}
+
+// ------------------------------------------------------------------ scene preparation
+// Sigma = R diag(exp(2 s)) R^T once per Gaussian (the 3DGS covariance), the
+// support threshold q* = 2 ln(255 o) and the link each Gaussian rides on.
+
+struct PrepArgs {
+    const float* mean;
+    const float* quat;
+    const void* log_scale;
+    const void* opacity;
+    const void* sh;
+    int64_t n;
+    int64_t dst;          // first destination index
+    int link_mode;        // 0: background (link 0), 1: binary search in link_offsets
+    const int64_t* link_offsets;
+    int n_links;
+    int64_t n_total;
+    float4* p0;
+    float4* p1;
+    float4* p2;
+    void* shp;
+    int sh_values;
+    int sh_planes;
+    uint32_t* status;
+};
+
+template <int DT>
+__global__ void k_prep(PrepArgs A) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    const int64_t g = A.dst + i;
+    double R[9];
+    bool ok = quat_rot<double>(A.quat[4 * i], A.quat[4 * i + 1], A.quat[4 * i + 2], A.quat[4 * i + 3], R);
+    double e2[3];
+    for (int k = 0; k < 3; ++k) e2[k] = exp(2.0 * (double)load_val<DT>(A.log_scale, 3 * i + k));
+    double S[6];  // 00 01 02 11 12 22
+    const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int m = 0; m < 6; ++m) {
+        const int a = ij[m][0], b = ij[m][1];
+        S[m] = R[3 * a] * R[3 * b] * e2[0] + R[3 * a + 1] * R[3 * b + 1] * e2[1] + R[3 * a + 2] * R[3 * b + 2] * e2[2];
+    }
+    const float o = load_val<DT>(A.opacity, i);
+    float qstar = -1.0f;
+    if (o >= 1.0f / 255.0f && isfinite(o)) qstar = (float)(2.0 * log(255.0 * (double)o));
+    if (!ok || !isfinite(S[0] + S[3] + S[5])) {
+        atomicOr(A.status, kStBadScene);
+        qstar = -1.0f;
+    }
+    int link = 0;
+    if (A.link_mode) {
+        int lo = 0, hi = A.n_links - 1;
+        while (lo < hi) {  // last l with link_offsets[l] <= i
+            int mid = (lo + hi + 1) >> 1;
+            if (A.link_offsets[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        link = lo + 1;
+    }
+    A.p0[g] = make_float4(A.mean[3 * i], A.mean[3 * i + 1], A.mean[3 * i + 2], o);
+    A.p1[g] = make_float4((float)S[0], (float)S[1], (float)S[2], (float)S[3]);
+    A.p2[g] = make_float4((float)S[4], (float)S[5], qstar, __int_as_float(link));
+    if constexpr (DT == GS_F32) {
+        float* dst = static_cast<float*>(A.shp);
+        for (int p = 0; p < A.sh_planes; ++p)
+            for (int c = 0; c < 4; ++c) {
+                const int f = 4 * p + c;
+                dst[((size_t)p * A.n_total + g) * 4 + c] =
+                    f < A.sh_values ? static_cast<const float*>(A.sh)[i * A.sh_values + f] : 0.0f;
+            }
+    } else {
+        uint16_t* dst = static_cast<uint16_t*>(A.shp);
+        const uint16_t* src = static_cast<const uint16_t*>(A.sh);
+        for (int p = 0; p < A.sh_planes; ++p)
+            for (int c = 0; c < 8; ++c) {
+                const int f = 8 * p + c;
+                dst[((size_t)p * A.n_total + g) * 8 + c] = f < A.sh_values ? src[i * A.sh_values + f] : (uint16_t)0;
+            }
+    }
+}
+
+cudaError_t launch_prep(const float* mean, const float* quat, const void* log_scale, const void* opacity,
+                        const void* sh, int64_t n, int64_t dst_offset, int link_mode, const int64_t* link_offsets,
+                        int n_links, const DevGaussians& D, uint32_t* status, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    PrepArgs A{mean, quat, log_scale, opacity, sh, n, dst_offset, link_mode, link_offsets, n_links, D.n,
+               D.p0, D.p1, D.p2, D.sh, sh_values(D.sh_degree), D.sh_planes, status};
+    dim3 grid((unsigned)((n + 255) / 256));
+    switch (D.dtype) {
+        case GS_F32: k_prep<GS_F32><<<grid, 256, 0, st>>>(A); break;
+        case GS_BF16: k_prep<GS_BF16><<<grid, 256, 0, st>>>(A); break;
+        default: k_prep<GS_F16><<<grid, 256, 0, st>>>(A); break;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ A1: link composition (RLGK)
+// For env e and frame f (f = 0: background/world, f = l+1: link l):
+//   M = [R_c R_l | R_c t_l + t_c]  (camera <- link), o = -M_R^T M_t (camera
+//   centre in the link frame, so that normalize(mu - o) is the view direction
+//   rotated into the link frame).
+
+__global__ void k_link_table(const float* poses, const gs_camera* cams, int We, int nl, LinkXf* out,
+                             uint32_t* status) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= We * (nl + 1)) return;
+    const int e = idx / (nl + 1), f = idx % (nl + 1);
+    const gs_camera& c = cams[e];
+    float Rc[9];
+    quat_rot<float>(c.q_cw[0], c.q_cw[1], c.q_cw[2], c.q_cw[3], Rc);
+    const float tc[3] = {c.t_cw[0], c.t_cw[1], c.t_cw[2]};
+    float M[9], t[3];
+    if (f == 0) {
+        for (int k = 0; k < 9; ++k) M[k] = Rc[k];
+        for (int k = 0; k < 3; ++k) t[k] = tc[k];
+    } else {
+        const float* P = poses + ((size_t)e * nl + (f - 1)) * 7;
+        float Rl[9];
+        bool ok = quat_rot<float>(P[0], P[1], P[2], P[3], Rl);
+        float tl[3] = {P[4], P[5], P[6]};
+        if (!ok || !isfinite(tl[0] + tl[1] + tl[2])) {
+            atomicOr(status, kStBadPose);
+            tl[0] = tl[1] = tl[2] = 0.0f;
+        }
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j)
+                M[3 * i + j] = Rc[3 * i] * Rl[j] + Rc[3 * i + 1] * Rl[3 + j] + Rc[3 * i + 2] * Rl[6 + j];
+            t[i] = Rc[3 * i] * tl[0] + Rc[3 * i + 1] * tl[1] + Rc[3 * i + 2] * tl[2] + tc[i];
+        }
+    }
+    float o[3];
+    for (int j = 0; j < 3; ++j) o[j] = -(M[j] * t[0] + M[3 + j] * t[1] + M[6 + j] * t[2]);
+    LinkXf X;
+    X.r0 = make_float4(M[0], M[1], M[2], t[0]);
+    X.r1 = make_float4(M[3], M[4], M[5], t[1]);
+    X.r2 = make_float4(M[6], M[7], M[8], t[2]);
+    X.o = make_float4(o[0], o[1], o[2], 0.0f);
+    out[idx] = X;
+}
+
+cudaError_t launch_link_table(const float* poses, const gs_camera* cams, int We, int n_links, LinkXf* out,
+                              uint32_t* status, cudaStream_t st) {
+    const int n = We * (n_links + 1);
+    if (n == 0) return cudaSuccess;
+    k_link_table<<<(n + 127) / 128, 128, 0, st>>>(poses, cams, We, n_links, out, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ A2: projection
+
+// 2D covariance J W Sigma W^T J^T of one Gaussian (before the 0.3 px^2
+// low-pass), where W is the rotation part of X and J the EWA Jacobian at the
+// guard-band-clamped centre.
+template <typename T>
+__device__ __forceinline__ void ewa_cov2d(const LinkXf& X, const float4& a0, const float4& a1, const float4& a2,
+                                          float fx, float fy, float limxn, float limxp, float limyn, float limyp,
+                                          T& A, T& B, T& C) {
+    const T mx = (T)X.r0.x * a0.x + (T)X.r0.y * a0.y + (T)X.r0.z * a0.z + (T)X.r0.w;
+    const T my = (T)X.r1.x * a0.x + (T)X.r1.y * a0.y + (T)X.r1.z * a0.z + (T)X.r1.w;
+    const T mz = (T)X.r2.x * a0.x + (T)X.r2.y * a0.y + (T)X.r2.z * a0.z + (T)X.r2.w;
+    const T iz = T(1) / mz;
+    T tx = mx * iz, ty = my * iz;
+    tx = tx < -(T)limxn ? -(T)limxn : (tx > (T)limxp ? (T)limxp : tx);
+    ty = ty < -(T)limyn ? -(T)limyn : (ty > (T)limyp ? (T)limyp : ty);
+    const T j00 = (T)fx * iz, j02 = -(T)fx * tx * iz;
+    const T j11 = (T)fy * iz, j12 = -(T)fy * ty * iz;
+    const T w0x = j00 * X.r0.x + j02 * X.r2.x, w0y = j00 * X.r0.y + j02 * X.r2.y, w0z = j00 * X.r0.z + j02 * X.r2.z;
+    const T w1x = j11 * X.r1.x + j12 * X.r2.x, w1y = j11 * X.r1.y + j12 * X.r2.y, w1z = j11 * X.r1.z + j12 * X.r2.z;
+    const T s00 = a1.x, s01 = a1.y, s02 = a1.z, s11 = a1.w, s12 = a2.x, s22 = a2.y;
+    const T v0x = s00 * w0x + s01 * w0y + s02 * w0z;
+    const T v0y = s01 * w0x + s11 * w0y + s12 * w0z;
+    const T v0z = s02 * w0x + s12 * w0y + s22 * w0z;
+    const T v1x = s00 * w1x + s01 * w1y + s02 * w1z;
+    const T v1y = s01 * w1x + s11 * w1y + s12 * w1z;
+    const T v1z = s02 * w1x + s12 * w1y + s22 * w1z;
+    A = w0x * v0x + w0y * v0y + w0z * v0z;
+    B = w1x * v0x + w1y * v0y + w1z * v0z;
+    C = w1x * v1x + w1y * v1y + w1z * v1z;
+}
+
+// Real SH basis through degree D in the 3DGS order (k = l*l + l + m), with the
+// Condon-Shortley phase.  Constants: sqrt(1/(4 pi)), sqrt(3/(4 pi)),
+// sqrt(15/(4 pi)), sqrt(5/(16 pi)), sqrt(15/(16 pi)), sqrt(35/(32 pi)),
+// sqrt(105/(4 pi)), sqrt(21/(32 pi)), sqrt(7/(16 pi)), sqrt(105/(16 pi)).
+template <int D>
+__device__ __forceinline__ void sh_colour(const float* sh, float x, float y, float z, float& r, float& g,
+                                          float& b) {
+    float Y[16];
+    Y[0] = 0.28209479177387814f;
+    if constexpr (D >= 1) {
+        Y[1] = -0.4886025119029199f * y;
+        Y[2] = 0.4886025119029199f * z;
+        Y[3] = -0.4886025119029199f * x;
+    }
+    if constexpr (D >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;
+        Y[5] = -1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+        Y[7] = -1.0925484305920792f * x * z;
+        Y[8] = 0.5462742152960396f * (xx - yy);
+        if constexpr (D >= 3) {
+            Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);
+            Y[10] = 2.890611442640554f * x * y * z;
+            Y[11] = -0.4570457994644658f * y * (4.0f * zz - xx - yy);
+            Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = -0.4570457994644658f * x * (4.0f * zz - xx - yy);
+            Y[14] = 1.445305721320277f * z * (xx - yy);
+            Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
+        }
+    }
+    constexpr int K = (D + 1) * (D + 1);
+    float cr = 0.0f, cg = 0.0f, cb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        cr += Y[k] * sh[3 * k];
+        cg += Y[k] * sh[3 * k + 1];
+        cb += Y[k] * sh[3 * k + 2];
+    }
+    r = fmaxf(cr + 0.5f, 0.0f);
+    g = fmaxf(cg + 0.5f, 0.0f);
+    b = fmaxf(cb + 0.5f, 0.0f);
+}
+
+template <int D, int DT>
+__device__ __forceinline__ void load_sh(const void* base, int64_t n, int64_t g, float* out) {
+    constexpr int NV = 3 * (D + 1) * (D + 1);
+    if constexpr (DT == GS_F32) {
+        constexpr int NP = (NV + 3) / 4;
+        const float4* P = static_cast<const float4*>(base);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const float4 v = __ldg(P + (size_t)p * n + g);
+            out[4 * p] = v.x;
+            if (4 * p + 1 < NV) out[4 * p + 1] = v.y;
+            if (4 * p + 2 < NV) out[4 * p + 2] = v.z;
+            if (4 * p + 3 < NV) out[4 * p + 3] = v.w;
+        }
+    } else {
+        constexpr int NP = (NV + 7) / 8;
+        const uint4* P = static_cast<const uint4*>(base);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const uint4 v = __ldg(P + (size_t)p * n + g);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int f = 8 * p + h;
+                if (f < NV) {
+                    const uint16_t bits = (uint16_t)(w[h >> 1] >> (16 * (h & 1)));
+                    if constexpr (DT == GS_BF16)
+                        out[f] = __uint_as_float((uint32_t)bits << 16);
+                    else
+                        out[f] = __half2float(__ushort_as_half(bits));
+                }
+            }
+        }
+    }
+}
+
+// Pixel range [lo, hi] of a support interval centred at c with half extent h:
+// lo = max(0, ceil((c - h) - 0.5)), hi = min(n-1, floor((c + h) - 0.5)).
+__device__ __forceinline__ bool pixel_range(float c, float h, int n, int& lo, int& hi) {
+    float a = ceilf(c - h - 0.5f);
+    float b = floorf(c + h - 0.5f);
+    if (!(a <= b)) return false;
+    a = fmaxf(a, 0.0f);
+    b = fminf(b, (float)(n - 1));
+    if (a > b) return false;
+    lo = (int)a;
+    hi = (int)b;
+    return true;
+}
+
+template <int D, int DT>
+__global__ void __launch_bounds__(256) k_project(ProjParams P) {
+    constexpr int NV = 3 * (D + 1) * (D + 1);
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = g < P.G;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = g - lane;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0;
+    if (act) {
+        a0 = __ldg(P.p0 + g);
+        a1 = __ldg(P.p1 + g);
+        a2 = __ldg(P.p2 + g);
+    }
+    const int li = __float_as_int(a2.w);
+    const float qstar = a2.z;
+    const bool live = act && qstar >= 0.0f;
+    const float trace = a1.x + a1.w + a2.y;  // >= largest eigenvalue of Sigma (rotation-invariant)
+    float sh[NV];
+    bool have_sh = false;
+    const int e0 = blockIdx.y * P.env_group;
+    const int e1 = min(P.We, e0 + P.env_group);
+    for (int el = e0; el < e1; ++el) {
+        bool vis = false;
+        if (live) {
+            const LinkXf* Xp = P.xf + (size_t)el * P.L1 + li;
+            LinkXf X;
+            X.r0 = __ldg(&Xp->r0);
+            X.r1 = __ldg(&Xp->r1);
+            X.r2 = __ldg(&Xp->r2);
+            const gs_camera* cam = P.cams + el;
+            const float near = __ldg(&cam->near_plane);
+            const float mz = X.r2.x * a0.x + X.r2.y * a0.y + X.r2.z * a0.z + X.r2.w;
+            if (mz > near) {
+                const float mx = X.r0.x * a0.x + X.r0.y * a0.y + X.r0.z * a0.z + X.r0.w;
+                const float my = X.r1.x * a0.x + X.r1.y * a0.y + X.r1.z * a0.z + X.r1.w;
+                const float fx = __ldg(&cam->fx), fy = __ldg(&cam->fy);
+                const float cx = __ldg(&cam->cx), cy = __ldg(&cam->cy);
+                const int W = __ldg(&cam->width), H = __ldg(&cam->height);
+                const float limxn = 1.3f * cx / fx, limxp = 1.3f * ((float)W - cx) / fx;
+                const float limyn = 1.3f * cy / fy, limyp = 1.3f * ((float)H - cy) / fy;
+                const float iz = 1.0f / mz;
+                const float u = fx * mx * iz + cx;
+                const float v = fy * my * iz + cy;
+                // Conservative cull: the support half extent is at most
+                // sqrt(q* (|J_row|^2 tr(Sigma) + 0.3)) with |J_row|^2 <= (f/z)^2 (1 + lim^2).
+                const float lx = fmaxf(limxn, limxp), ly = fmaxf(limyn, limyp);
+                const float fz = fx * iz, fzy = fy * iz;
+                const float hxb = sqrtf(qstar * (fz * fz * (1.0f + lx * lx) * trace + 0.3f)) * 1.001f + 1.0f;
+                const float hyb = sqrtf(qstar * (fzy * fzy * (1.0f + ly * ly) * trace + 0.3f)) * 1.001f + 1.0f;
+                const bool maybe = (u + hxb >= 0.5f) && (u - hxb <= (float)W - 0.5f) && (v + hyb >= 0.5f) &&
+                                   (v - hyb <= (float)H - 0.5f);
+                if (maybe) {
+                    float A, B, C;
+                    ewa_cov2d<float>(X, a0, a1, a2, fx, fy, limxn, limxp, limyn, limyp, A, B, C);
+                    float cA = A + 0.3f, cC = C + 0.3f;
+                    float det = cA * cC - B * B;
+                    float ca, cb, cc;
+                    bool ok = true;
+                    if (det > 0x1p-10f * cA * cC) {
+                        const float id = 1.0f / det;
+                        ca = cC * id;
+                        cb = -B * id;
+                        cc = cA * id;
+                    } else {
+                        // near-degenerate: the whole 2D covariance and its inverse in FP64
+                        double dA, dB, dC;
+                        ewa_cov2d<double>(X, a0, a1, a2, fx, fy, limxn, limxp, limyn, limyp, dA, dB, dC);
+                        dA += 0.3;
+                        dC += 0.3;
+                        const double ddet = dA * dC - dB * dB;
+                        ok = ddet > 0.0;
+                        ca = (float)(dC / ddet);
+                        cb = (float)(-dB / ddet);
+                        cc = (float)(dA / ddet);
+                        cA = (float)dA;
+                        cC = (float)dC;
+                    }
+                    const float hx = sqrtf(qstar * cA) * 1.0001f;
+                    const float hy = sqrtf(qstar * cC) * 1.0001f;
+                    int i0, i1, j0, j1;
+                    if (ok && pixel_range(u, hx, W, i0, i1) && pixel_range(v, hy, H, j0, j1)) {
+                        if (!have_sh) {
+                            load_sh<D, DT>(P.sh, P.G, g, sh);
+                            have_sh = true;
+                        }
+                        const float4 O = __ldg(&Xp->o);
+                        float dx = a0.x - O.x, dy = a0.y - O.y, dz = a0.z - O.z;
+                        const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+                        dx *= inv;
+                        dy *= inv;
+                        dz *= inv;
+                        float r, gg, b;
+                        sh_colour<D>(sh, dx, dy, dz, r, gg, b);
+                        const uint32_t rx = (uint32_t)i0 | ((uint32_t)i1 << 16);
+                        const uint32_t ry = (uint32_t)j0 | ((uint32_t)j1 << 16);
+                        const size_t ri = (size_t)el * P.G + g;
+                        P.r0[ri] = make_float4(u, v, a0.w, mz);
+                        P.r1[ri] = make_float4(ca, cb, cc, __uint_as_float(rx));
+                        P.r2[ri] = make_float4(r, gg, b, __uint_as_float(ry));
+                        P.r3[ri] = make_uint4(rx, ry, __float_as_uint(mz), 0u);
+                        if (P.dbg_hxy) P.dbg_hxy[ri] = make_float2(hx, hy);
+                        vis = true;
+                    }
+                }
+            }
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, vis);
+        if (lane == 0 && gw < P.G) P.mask[(size_t)el * P.mask_words + (gw >> 5)] = m;
+    }
+}
+
+template <int D>
+static void launch_project_d(const DevGaussians& Dg, const ProjParams& P, dim3 grid, cudaStream_t st) {
+    switch (Dg.dtype) {
+        case GS_F32: k_project<D, GS_F32><<<grid, 256, 0, st>>>(P); break;
+        case GS_BF16: k_project<D, GS_BF16><<<grid, 256, 0, st>>>(P); break;
+        default: k_project<D, GS_F16><<<grid, 256, 0, st>>>(P); break;
+    }
+}
+
+cudaError_t launch_project(const DevGaussians& Dg, const ProjParams& P, dim3 grid, cudaStream_t st) {
+    switch (Dg.sh_degree) {
+        case 0: launch_project_d<0>(Dg, P, grid, st); break;
+        case 1: launch_project_d<1>(Dg, P, grid, st); break;
+        case 2: launch_project_d<2>(Dg, P, grid, st); break;
+        default: launch_project_d<3>(Dg, P, grid, st); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gsb

@@ -1,0 +1,293 @@
+"""Thin Python binding of libgsbatch (ctypes).
+
+Argument marshalling only: every step of the render runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams; host inputs may be
+numpy arrays.  If the compiled library is missing this module raises -- there
+is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .synth import CAMERA_DTYPE
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libgsbatch.so")
+
+GS_OK, GS_ERR_INVALID, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED, GS_ERR_DEVICE = (
+    0, -1, -2, -3, -4, -5, -6)
+DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
+STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID", -2: "GS_ERR_OOM", -3: "GS_ERR_CUDA", -4: "GS_ERR_TIMEOUT",
+                -5: "GS_ERR_UNSUPPORTED", -6: "GS_ERR_DEVICE"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GsGaussians(C.Structure):
+    _fields_ = [("n", C.c_int64), ("mean", C.c_void_p), ("quat", C.c_void_p), ("log_scale", C.c_void_p),
+                ("opacity", C.c_void_p), ("sh", C.c_void_p), ("sh_degree", C.c_int), ("dtype", C.c_int),
+                ("on_device", C.c_int)]
+
+
+class GsStats(C.Structure):
+    _fields_ = [("waves", C.c_int64), ("kernel_launches", C.c_int64), ("intersections", C.c_int64),
+                ("scratch_bytes", C.c_int64), ("n_gaussians", C.c_int64), ("composited", C.c_int64)]
+
+
+PHASES = ("link", "project", "count", "scan", "scatter", "composite")
+
+
+class GsTimings(C.Structure):
+    _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); the exported C ABI declared in include/gsbatch.h
+_SIGS = {
+    "gs_scene_create": (C.c_int, [C.POINTER(GsGaussians), C.POINTER(C.c_void_p)]),
+    "gs_scene_attach_links": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(GsGaussians)]),
+    "gs_render_batch": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
+    "gs_render_batch_host": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
+    "gs_scene_set_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "gs_scene_set_budget": (C.c_int, [C.c_void_p, C.c_int64]),
+    "gs_scene_set_wave": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_scene_set_debug": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_scene_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gs_scene_get_stats": (C.c_int, [C.c_void_p, C.POINTER(GsStats)]),
+    "gs_scene_set_counters": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_scene_set_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_scene_get_timings": (C.c_int, [C.c_void_p, C.POINTER(GsTimings), C.c_int]),
+    "gs_debug_copy_records": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 10),
+    "gs_debug_copy_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
+    "gs_scene_destroy": (None, [C.c_void_p]),
+    "gs_last_error": (C.c_char_p, []),
+    "gs_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libgsbatch.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2604_25459_gb300.build.build() "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != GS_OK:
+        raise GsError(status, lib().gs_last_error().decode())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data_as(C.c_void_p)
+    raise TypeError(type(x))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _view(mean, quat, log_scale, opacity, sh, sh_degree: int, dtype: str):
+    arrs = [mean, quat, log_scale, opacity, sh]
+    on_dev = any(_is_torch(a) and a.is_cuda for a in arrs)
+    n = int(mean.shape[0])
+    v = GsGaussians(n, _ptr(mean), _ptr(quat), _ptr(log_scale), _ptr(opacity), _ptr(sh), sh_degree, DTYPES[dtype],
+                    1 if on_dev else 0)
+    return v, arrs
+
+
+def _host_f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Scene:
+    """A device-resident scene: shared background + link-attached Gaussians.
+
+    ``background``/``links`` expose mean, quat, log_scale, opacity, sh (numpy
+    or torch); with ``stored`` (dict of log_scale/opacity/sh arrays) the
+    precision form passes those bf16/f16 arrays instead."""
+
+    def __init__(self, background, dtype: str = "f32", sh_degree: int = 3, stored=None):
+        self._h = C.c_void_p()
+        self.dtype = dtype
+        self.sh_degree = sh_degree
+        v, keep = self._make_view(background, dtype, sh_degree, stored)
+        _check(lib().gs_scene_create(C.byref(v), C.byref(self._h)))
+        self.n_links = 0
+        self._alive = True
+
+    @staticmethod
+    def _make_view(g, dtype, sh_degree, stored):
+        if g is None:
+            z = np.zeros((0, 3), np.float32)
+            return GsGaussians(0, None, None, None, None, None, sh_degree, DTYPES[dtype], 0), [z]
+        mean, quat = g.mean, g.quat
+        if stored is not None:
+            ls, op, sh = stored["log_scale"], stored["opacity"], stored["sh"]
+        else:
+            ls, op, sh = g.log_scale, g.opacity, g.sh
+        if not _is_torch(mean):
+            mean, quat = _host_f32(mean), _host_f32(quat)
+            if dtype == "f32":
+                ls, op, sh = _host_f32(ls), _host_f32(op), _host_f32(sh)
+            else:
+                ls, op, sh = (np.ascontiguousarray(a) for a in (ls, op, sh))
+            nk = (sh_degree + 1) ** 2
+            if sh.ndim == 3 and sh.shape[1] != nk:
+                sh = np.ascontiguousarray(sh[:, :nk, :])
+        return _view(mean, quat, ls, op, sh, sh_degree, dtype)
+
+    def attach_links(self, link_offsets, links, stored=None):
+        offs = np.ascontiguousarray(link_offsets, dtype=np.int64)
+        v, keep = self._make_view(links, self.dtype, self.sh_degree, stored)
+        _check(lib().gs_scene_attach_links(self._h, len(offs) - 1, _ptr(offs), C.byref(v)))
+        self.n_links = len(offs) - 1
+
+    def set_tile(self, tw: int, th: int):
+        _check(lib().gs_scene_set_tile(self._h, tw, th))
+
+    def set_budget(self, nbytes: int):
+        _check(lib().gs_scene_set_budget(self._h, int(nbytes)))
+
+    def set_wave(self, max_envs: int):
+        _check(lib().gs_scene_set_wave(self._h, int(max_envs)))
+
+    def set_debug(self, on: bool):
+        _check(lib().gs_scene_set_debug(self._h, 1 if on else 0))
+
+    def stats(self) -> dict:
+        s = GsStats()
+        _check(lib().gs_scene_get_stats(self._h, C.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in GsStats._fields_}
+
+    def set_counters(self, on: bool):
+        _check(lib().gs_scene_set_counters(self._h, 1 if on else 0))
+
+    def set_profile(self, on: bool):
+        _check(lib().gs_scene_set_profile(self._h, 1 if on else 0))
+
+    def timings(self, reset: bool = False) -> dict:
+        """Per-phase device milliseconds and kernel launches (profiling on)."""
+        t = GsTimings()
+        _check(lib().gs_scene_get_timings(self._h, C.byref(t), 1 if reset else 0))
+        return {p: (float(t.ms[i]), int(t.launches[i])) for i, p in enumerate(PHASES)}
+
+    def sync_status(self, stream=None):
+        _check(lib().gs_scene_sync_status(self._h, _stream_handle(stream)))
+
+    def render(self, link_poses, cams: np.ndarray, rgb=None, depth=None, alpha=None, want_alpha: bool = True,
+               stream=None):
+        """Device render.  link_poses: CUDA float32 [E][L][7] (or None when the
+        scene has no links); cams: numpy CAMERA_DTYPE [E].  Returns (rgb, depth,
+        alpha) CUDA tensors [E,H,W,3], [E,H,W], [E,H,W] (alpha None if not wanted)."""
+        import torch
+
+        cams = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+        E = int(cams.shape[0])
+        H, W = (int(cams["height"][0]), int(cams["width"][0])) if E else (0, 0)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if rgb is None:
+            rgb = torch.empty((E, H, W, 3), dtype=torch.float32, device=dev)
+        if depth is None:
+            depth = torch.empty((E, H, W), dtype=torch.float32, device=dev)
+        if alpha is None and want_alpha:
+            alpha = torch.empty((E, H, W), dtype=torch.float32, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        _check(lib().gs_render_batch(self._h, E, _ptr(link_poses), _ptr(cams), _ptr(rgb), _ptr(depth), _ptr(alpha),
+                                     _stream_handle(stream)))
+        return rgb, depth, alpha
+
+    def render_host(self, link_poses: np.ndarray, cams: np.ndarray, rgb: np.ndarray, depth: np.ndarray,
+                    alpha=None, stream=None):
+        """Host-buffer render (copies inside the call); returns when done."""
+        cams = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+        E = int(cams.shape[0])
+        _check(lib().gs_render_batch_host(self._h, E, _ptr(link_poses), _ptr(cams), _ptr(rgb), _ptr(depth),
+                                          _ptr(alpha), _stream_handle(stream)))
+        return rgb, depth, alpha
+
+    def debug_records(self, env: int, n: int) -> dict:
+        out = dict(visible=np.zeros(n, np.uint8), u=np.zeros(n, np.float32), v=np.zeros(n, np.float32),
+                   hx=np.zeros(n, np.float32), hy=np.zeros(n, np.float32), z=np.zeros(n, np.float32),
+                   opacity=np.zeros(n, np.float32), conic=np.zeros((n, 3), np.float32),
+                   rgb=np.zeros((n, 3), np.float32), range=np.zeros((n, 4), np.int32))
+        _check(lib().gs_debug_copy_records(self._h, env, *[_ptr(out[k]) for k in (
+            "visible", "u", "v", "hx", "hy", "z", "opacity", "conic", "rgb", "range")]))
+        return out
+
+    def debug_tiles(self, env: int, n_tiles: int, with_lists: bool = True):
+        counts = np.zeros(n_tiles, np.uint32)
+        _check(lib().gs_debug_copy_tiles(self._h, env, _ptr(counts), n_tiles, None, 0))
+        if not with_lists:
+            return counts, None
+        total = int(counts.astype(np.int64).sum())
+        lists = np.zeros(max(total, 1), np.uint32)
+        _check(lib().gs_debug_copy_tiles(self._h, env, _ptr(counts), n_tiles, _ptr(lists), total))
+        return counts, lists[:total]
+
+    def close(self):
+        if getattr(self, "_alive", False):
+            lib().gs_scene_destroy(self._h)
+            self._alive = False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def scene_from_workload(w, dtype: str = "f32", sh_degree: int = 3) -> Scene:
+    """Build a Scene from a synth.Workload (quantising SH/scales/opacity for bf16/f16)."""
+    from . import synth
+    if dtype == "f32":
+        s = Scene(w.background, "f32", sh_degree)
+        if w.n_links > 0:
+            s.attach_links(w.link_offsets, w.links)
+        return s
+    st_bg, _ = synth.quantize(w.background, dtype)
+    s = Scene(w.background, dtype, sh_degree, stored=st_bg)
+    if w.n_links > 0:
+        st_l, _ = synth.quantize(w.links, dtype)
+        s.attach_links(w.link_offsets, w.links, stored=st_l)
+    return s

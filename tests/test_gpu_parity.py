@@ -1,0 +1,227 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: per-channel max abs <= 2e-3 on [0,1] images and depth relative
+error <= 1e-4 where alpha >= 0.5 (FP32 path vs FP64 oracle); binning counts and
+per-tile depth-ordered lists bit-exact when the oracle is fed the GPU's keys.
+Pixels whose result sits on a threshold within FP32 noise (alpha at 1/255,
+T at 1e-4, depth near-ties) are excluded and counted, never hidden.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import (AMB_ALPHA, AMB_T, compare, ensure_built, gpu_render, keyed_zkey, oracle_env)
+from oracle import oracle
+from paper_2604_25459_gb300 import gsbatch, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    ensure_built()
+
+
+def _keyed_check(w, e, out, sh_degree=3):
+    """Independent and keyed comparisons of env e of a debug-mode render."""
+    scene = out["scene"]
+    rec = scene.debug_records(e, w.background.n + w.links.n)
+    S = oracle.scene_arrays(w, sh_degree)
+    proj = oracle.project(S, w.link_poses[e], w.cams[e])
+    zk = keyed_zkey(proj, rec)
+    W, H = int(w.cams[e]["width"]), int(w.cams[e]["height"])
+    ind = oracle.render_projected(proj, W, H)
+    key = oracle.render_projected(proj, W, H, zkey=zk)
+    st_i = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], ind)
+    st_k = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], key, amb_bits=AMB_ALPHA | AMB_T)
+    return st_i, st_k, rec, proj
+
+
+def test_c0_parity_independent_and_keyed():
+    w = synth.make_c0()
+    out = gpu_render(w, debug=True, keep_scene=True)
+    st_i, st_k, rec, proj = _keyed_check(w, 0, out)
+    out["scene"].close()
+    print("c0 independent", st_i, "keyed", st_k)
+    assert st_k["amb_frac"] < 1e-3
+
+
+def test_c0_projection_records():
+    """Per-Gaussian records vs the FP64 projection (steps 1-7)."""
+    w = synth.make_c0()
+    out = gpu_render(w, debug=True, keep_scene=True)
+    rec = out["scene"].debug_records(0, w.background.n)
+    out["scene"].close()
+    S = oracle.scene_arrays(w)
+    p = oracle.project(S, w.link_poses[0], w.cams[0])
+    vis_g, vis_o = rec["visible"] == 1, p["valid"] == 1
+    both = vis_g & vis_o
+    # visibility may differ only for supports whose box edge sits on a pixel boundary (rare)
+    diff = np.nonzero(vis_g != vis_o)[0]
+    assert len(diff) <= max(2, 1e-3 * both.sum())
+    np.testing.assert_allclose(rec["u"][both], p["u"][both], atol=2e-3)
+    np.testing.assert_allclose(rec["v"][both], p["v"][both], atol=2e-3)
+    np.testing.assert_allclose(rec["z"][both], p["z"][both], rtol=2e-6)
+    np.testing.assert_allclose(rec["rgb"][both], p["rgb"][both], atol=2e-5)
+    np.testing.assert_allclose(rec["conic"][both], p["conic"][both], rtol=2e-3, atol=1e-5)
+    np.testing.assert_allclose(rec["hx"][both] / 1.0001, p["hx"][both], rtol=1e-4)
+    np.testing.assert_allclose(rec["hy"][both] / 1.0001, p["hy"][both], rtol=1e-4)
+    np.testing.assert_allclose(rec["opacity"][both], p["opacity"][both], rtol=1e-7)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (16, 8)])
+def test_binning_keyed_bit_exact(tile):
+    """Counts and depth-ordered per-tile lists equal the binning oracle fed the
+    GPU's (u, v, hx, hy, depth bits, index), for a scene whose dense tiles have
+    lists longer than the compositor's shared-memory window."""
+    w = synth.make_c1(n_envs=2, width=160, height=120, f=125.0, n_bg=60_000, per_link=2000)
+    out = gpu_render(w, tile=tile, debug=True, keep_scene=True)
+    scene = out["scene"]
+    W, H = 160, 120
+    ntiles = (-(-W // tile[0])) * (-(-H // tile[1]))
+    for e in range(w.n_envs):
+        rec = scene.debug_records(e, w.background.n + w.links.n)
+        vis = np.nonzero(rec["visible"])[0]
+        counts, lists = scene.debug_tiles(e, ntiles)
+        oc, ol = oracle.bin_records(rec["u"][vis], rec["v"][vis], rec["hx"][vis], rec["hy"][vis],
+                                    rec["z"][vis].view(np.uint32), vis.astype(np.uint32), W, H, *tile)
+        np.testing.assert_array_equal(counts.astype(np.int64), oc)
+        np.testing.assert_array_equal(lists, ol)
+        assert counts.max() > 2048  # the windowed depth selection was exercised
+    scene.close()
+
+
+def test_long_lists_parity():
+    """Dense robot tiles (lists far longer than one shared-memory window)."""
+    w = synth.make_c1(n_envs=2, width=160, height=120, f=125.0, n_bg=60_000, per_link=2000)
+    out = gpu_render(w, debug=True, keep_scene=True)
+    for e in range(w.n_envs):
+        st_i, st_k, _, _ = _keyed_check(w, e, out)
+        print("long lists env", e, st_i, st_k)
+    out["scene"].close()
+
+
+def test_tile_shape_and_batch_invariance_bit_exact():
+    """Results do not depend on the tile shape, on the wave size, or on which
+    other envs share the batch."""
+    w = synth.make_c1(n_envs=6, width=96, height=72, f=75.0, n_bg=40_000, per_link=1000)
+    base = gpu_render(w)
+    for tile in ((8, 8), (32, 8), (16, 8)):
+        o = gpu_render(w, tile=tile)
+        for k in ("rgb", "depth", "alpha"):
+            np.testing.assert_array_equal(o[k], base[k], err_msg=f"{k} {tile}")
+    o = gpu_render(w, wave=2)
+    for k in ("rgb", "depth", "alpha"):
+        np.testing.assert_array_equal(o[k], base[k])
+    alone = gpu_render(w, envs=[3])
+    for k in ("rgb", "depth", "alpha"):
+        np.testing.assert_array_equal(alone[k][0], base[k][3])
+
+
+def test_host_buffers_match_device():
+    import torch
+
+    w = synth.make_c1(n_envs=5, width=64, height=48, f=50.0, n_bg=20_000, per_link=500)
+    base = gpu_render(w)
+    scene = gsbatch.scene_from_workload(w)
+    scene.set_wave(2)
+    E, H, W = 5, 48, 64
+    rgb = torch.empty((E, H, W, 3)).pin_memory().numpy()
+    depth = torch.empty((E, H, W)).pin_memory().numpy()
+    alpha = torch.empty((E, H, W)).pin_memory().numpy()
+    scene.render_host(np.ascontiguousarray(w.link_poses), w.cams, rgb, depth, alpha)
+    scene.close()
+    np.testing.assert_array_equal(rgb, base["rgb"])
+    np.testing.assert_array_equal(depth, base["depth"])
+    np.testing.assert_array_equal(alpha, base["alpha"])
+
+
+def test_c1_full_batch_sampled_envs():
+    """The benchmark's workload (2048 envs x 640x480, 600k Gaussians, default
+    launch configuration): sampled envs against the FP64 oracle."""
+    w = synth.make_c1()
+    out = gpu_render(w)
+    for e in (0, 1023, 2047):
+        ref = oracle_env(w, e)
+        st = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], ref)
+        print("c1 env", e, st)
+        assert st["amb_frac"] < 0.2
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_edge_empty_and_degenerate():
+    import torch
+
+    ensure_built()
+    w = synth.make_tiny(seed=3, n_envs=2)
+    scene = gsbatch.scene_from_workload(w)
+    # zero envs: no-op
+    cams0 = w.cams[:0]
+    r = scene.render(None, cams0, want_alpha=True)
+    assert r[0].shape[0] == 0
+    # camera looking away: nothing visible -> black, alpha 0, depth 0
+    cams = w.cams.copy()
+    cams["q_cw"] = [[0.0, 0.0, 1.0, 0.0]] * 2  # 180 deg about y
+    rgb, depth, alpha = scene.render(torch.from_numpy(w.link_poses).cuda(), cams)
+    torch.cuda.synchronize()
+    assert float(rgb.abs().max()) == 0 and float(alpha.max()) == 0 and float(depth.max()) == 0
+    scene.close()
+    # no Gaussians at all
+    empty = synth.Workload("empty", w.background.slice(0, 0), np.zeros(1, np.int64), w.links.slice(0, 0),
+                           np.zeros((2, 0, 7), np.float32), w.cams)
+    s2 = gsbatch.scene_from_workload(empty)
+    rgb, depth, alpha = s2.render(None, w.cams)
+    torch.cuda.synchronize()
+    assert float(rgb.abs().max()) == 0
+    s2.close()
+
+
+@pytest.mark.parametrize("wh", [(1, 1), (37, 29), (17, 3)])
+def test_edge_ragged_resolutions(wh):
+    W, H = wh
+    w = synth.make_tiny(seed=6, n_envs=2, width=W, height=H, f=max(W, H) * 0.9)
+    out = gpu_render(w)
+    for e in range(2):
+        compare(out["rgb"][e], out["depth"][e], out["alpha"][e], oracle_env(w, e))
+
+
+def test_invalid_arguments_rejected_before_launch():
+    import torch
+
+    ensure_built()
+    w = synth.make_tiny(seed=1, n_envs=2)
+    scene = gsbatch.scene_from_workload(w)
+    poses = torch.from_numpy(w.link_poses).cuda()
+    bad = w.cams.copy()
+    bad["fx"][1] = 0.0
+    with pytest.raises(gsbatch.GsError) as ei:
+        scene.render(poses, bad)
+    assert ei.value.status == gsbatch.GS_ERR_INVALID
+    bad = w.cams.copy()
+    bad["width"][1] = 33
+    with pytest.raises(gsbatch.GsError) as ei:
+        scene.render(poses, bad)
+    assert ei.value.status == gsbatch.GS_ERR_INVALID
+    with pytest.raises(gsbatch.GsError):
+        scene.set_tile(12, 12)
+    # a zero link quaternion is found on the device and reported by the status word
+    p2 = w.link_poses.copy()
+    p2[0, 0, :4] = 0
+    scene.render(torch.from_numpy(p2).cuda(), w.cams)
+    with pytest.raises(gsbatch.GsError) as ei:
+        scene.sync_status()
+    assert ei.value.status == gsbatch.GS_ERR_DEVICE
+    scene.sync_status()  # cleared
+    scene.close()
+
+
+def test_scene_with_zero_quaternion_rejected():
+    ensure_built()
+    w = synth.make_tiny(seed=1)
+    bg = w.background
+    q = bg.quat.copy()
+    q[3] = 0
+    bad = synth.Gaussians(bg.mean, q, bg.log_scale, bg.opacity, bg.sh)
+    with pytest.raises(gsbatch.GsError) as ei:
+        gsbatch.Scene(bad)
+    assert ei.value.status == gsbatch.GS_ERR_INVALID
