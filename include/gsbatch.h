@@ -127,6 +127,29 @@ gs_status gs_render_batch(gs_scene s, int n_envs, const float* link_poses, const
 gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
                                float* depth, float* alpha, void* cuda_stream);
 
+/* As gs_render_batch (same arguments, same kernels, same results), but it
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The
+ * paper has no counterpart; this is for callers that must not allocate device
+ * memory while rendering -- a process whose GPU memory is already reserved by
+ * another allocator, code running where an allocation would stall the device
+ * (cudaFree synchronises it) or is not allowed, a control loop that cannot
+ * absorb a first-time allocation.
+ * Its working memory is one file-scope device array of 32 MiB per device,
+ * held by every process that loads the library until it exits.  The first
+ * call on a device looks up that array's device address (once per device,
+ * with the device current); make that first call before any stream capture.
+ * Every call on a device shares the array and it keeps the last call's data:
+ * each call clears the counters it needs zeroed, and calls whose work
+ * overlaps on the GPU (other streams or threads) race on it.
+ * Sizes beyond the array fail with GS_ERR_UNSUPPORTED and a message giving the
+ * bytes needed: before any launch when one environment's projected records
+ * do not fit, or after the binning of a wave when its intersection keys do
+ * not fit (earlier waves' images are then complete, later ones unwritten).
+ * Like gs_render_batch it reads one wave total back to the host per wave of
+ * up to 256 environments (into a stack buffer). */
+gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
+                                  float* rgb, float* depth, float* alpha, void* cuda_stream);
+
 /* Tile shape used by the binning and compositing kernels.  Allowed:
  * 8x8, 16x8, 16x16, 32x8 (tw x th).  Results do not depend on the tile shape
  * (each splat's support box is inflated by a relative 1e-4 so every tile it

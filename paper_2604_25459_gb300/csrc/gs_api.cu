@@ -545,6 +545,15 @@ gs_status render_common(gs_scene s, int E, const float* link_poses, const gs_cam
 
 }  // namespace
 
+gsb::SceneView gsb::scene_view(gs_scene s) {
+    return SceneView{s->device, s->D, s->status, s->tile_w, s->tile_h};
+}
+
+gs_status gsb::report(gs_status st, const char* msg) {
+    g_err = msg;
+    return st;
+}
+
 extern "C" {
 
 const char* gs_last_error(void) { return g_err.c_str(); }

@@ -133,4 +133,15 @@ cudaError_t launch_composite(const CompParams& P, int n_envs, cudaStream_t st);
 
 constexpr int kCompCap = 2048;  // depth-ordered window held in shared memory by the compositor
 
+// Read-only view of a scene's device data for entry points outside gs_api.cu.
+struct SceneView {
+    int device;
+    DevGaussians D;
+    uint32_t* status;
+    int tile_w, tile_h;
+};
+SceneView scene_view(gs_scene s);
+// Set the thread-local message returned by gs_last_error and return st.
+gs_status report(gs_status st, const char* msg);
+
 }  // namespace gsb

@@ -56,6 +56,7 @@ _SIGS = {
     "gs_scene_attach_links": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(GsGaussians)]),
     "gs_render_batch": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_render_batch_host": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
+    "gs_render_batch_noalloc": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_scene_set_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "gs_scene_set_budget": (C.c_int, [C.c_void_p, C.c_int64]),
     "gs_scene_set_wave": (C.c_int, [C.c_void_p, C.c_int]),
@@ -229,6 +230,15 @@ class Scene:
             stream = torch.cuda.current_stream()
         _check(lib().gs_render_batch(self._h, E, _ptr(link_poses), _ptr(cams), _ptr(rgb), _ptr(depth), _ptr(alpha),
                                      _stream_handle(stream)))
+        return rgb, depth, alpha
+
+    def render_noalloc(self, link_poses, cams: np.ndarray, rgb, depth, alpha=None, stream=None):
+        """gs_render_batch_noalloc: same render into caller-provided CUDA
+        tensors, with the library's working memory in its fixed device array
+        (no allocation by the library)."""
+        cams = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+        _check(lib().gs_render_batch_noalloc(self._h, int(cams.shape[0]), _ptr(link_poses), _ptr(cams), _ptr(rgb),
+                                             _ptr(depth), _ptr(alpha), _stream_handle(stream)))
         return rgb, depth, alpha
 
     def render_host(self, link_poses: np.ndarray, cams: np.ndarray, rgb: np.ndarray, depth: np.ndarray,
