@@ -35,6 +35,24 @@ sys.path.insert(0, ROOT)
 METRIC = "env-frames/s at 2048x640x480 RGB-D"
 UNIT = "env-frames/s"
 
+# DRAM traffic of the compositor per env of a launch, from the ncu capture
+# summarised in profiles/k_composite_c1.md (dram__bytes_read.sum +
+# dram__bytes_write.sum over a 32-env launch, divided by 32), valid only for
+# the compositor sources it was taken on.
+COMPOSITE_TRAFFIC_PER_ENV = 1.2366e9 / 32
+COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu", "paper_2604_25459_gb300/csrc/gs_internal.cuh")
+COMPOSITE_TRAFFIC_SHA = "d14f96d19f61c27a"
+
+
+def _sources_sha(paths) -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -235,8 +253,11 @@ def run_ours(a, rank, world, local_rank):
     props = torch.cuda.get_device_properties(dev)
     peak_lane_ops = props.multi_processor_count * 128 * sm_mhz * 1e6
     achieved = evals_per_launch * ops_per_eval / (per_launch_ms / 1e3)
+    traffic = None
+    if _sources_sha(COMPOSITE_TRAFFIC_SOURCES) == COMPOSITE_TRAFFIC_SHA:
+        traffic = COMPOSITE_TRAFFIC_PER_ENV * E / max(launches_per_batch, 1)  # bytes per launch
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_lane_ops / 1e9, "unit": "Glane-op/s",
-                "frac": achieved / peak_lane_ops, "traffic": None,
+                "frac": achieved / peak_lane_ops, "traffic": traffic,
                 "kernel": "k_composite", "per_launch_ms": per_launch_ms,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x median {sm_mhz:.0f} MHz "
                               "(1 lane-op per lane per clock, FMA counted once)"}

@@ -360,7 +360,7 @@ gs_status render_wave(gs_scene s, const Plan& p, int e0, int We, const float* po
     B.off_local = s->off.as<uint32_t>();
     B.env_base = s->env_base.as<unsigned long long>();
     B.cursor = s->cursor.as<uint32_t>();
-    B.words_per_block = 128;
+    B.words_per_block = 256;  // 8 warps x 32 mask words (8192 Gaussians)
     const size_t smem1 = (size_t)p.T * 4, smem2 = (size_t)p.T * 8;
     PhaseTimer t3(s, st, GS_PHASE_COUNT);
     CK(launch_count(B, We, st, smem1), "count");

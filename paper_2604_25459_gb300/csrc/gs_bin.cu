@@ -21,27 +21,56 @@ __device__ __forceinline__ void tile_span(uint32_t rx, uint32_t ry, int tw, int 
     ty1 = (int)(ry >> 16) / th;
 }
 
+// Visit the visible Gaussians of mask words [w0, w1) of one env.  Each warp
+// takes 32 words at a time, expands their set bits into a dense list in its
+// slice of shared memory (1024 entries) and its lanes walk that list, so
+// sparse visibility (most of the background is off-screen in any one view)
+// does not leave lanes idle.
+template <typename F>
+__device__ __forceinline__ void for_each_visible(const uint32_t* mask, int64_t w0, int64_t w1, uint16_t* wbuf, F&& f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint16_t* buf = wbuf + warp * 1024;
+    for (int64_t base = w0 + (int64_t)warp * 32; base < w1; base += (int64_t)nw * 32) {
+        const int64_t w = base + lane;
+        uint32_t m = w < w1 ? __ldg(mask + w) : 0u;
+        const uint32_t c = __popc(m);
+        uint32_t incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t pos = incl - c;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            buf[pos++] = (uint16_t)(lane * 32 + b);
+        }
+        __syncwarp();
+        for (uint32_t j = lane; j < total; j += 32) f(base * 32 + buf[j]);
+        __syncwarp();
+    }
+}
+
 // grid: (blocks over mask words, envs); block 256; dynamic smem T u32
 __global__ void __launch_bounds__(256) k_count(BinParams P) {
     extern __shared__ uint32_t hist[];
+    __shared__ uint16_t wbuf[8 * 1024];
     const int el = P.e_begin + blockIdx.y;
     for (int t = threadIdx.x; t < P.T; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t)blockIdx.x * P.words_per_block;
     const int64_t w1 = min(w0 + (int64_t)P.words_per_block, P.mask_words);
     const uint32_t* mask = P.mask + (size_t)el * P.mask_words;
     const uint4* r3 = P.r3 + (size_t)el * P.G;
-    for (int64_t w = w0 + warp; w < w1; w += 8) {
-        const uint32_t m = __ldg(mask + w);
-        if ((m >> lane) & 1u) {
-            const uint4 q = r3[w * 32 + lane];
-            int tx0, tx1, ty0, ty1;
-            tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * P.ntx + tx], 1u);
-        }
-    }
+    for_each_visible(mask, w0, w1, wbuf, [&](int64_t g) {
+        const uint4 q = r3[g];
+        int tx0, tx1, ty0, ty1;
+        tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * P.ntx + tx], 1u);
+    });
     __syncthreads();
     uint32_t* cnt = P.counts + (size_t)el * P.T;
     for (int t = threadIdx.x; t < P.T; t += blockDim.x) {
@@ -53,7 +82,7 @@ __global__ void __launch_bounds__(256) k_count(BinParams P) {
 cudaError_t launch_count(const BinParams& P, int n_envs, cudaStream_t st, size_t smem) {
     if (n_envs == 0) return cudaSuccess;
     dim3 grid((unsigned)((P.mask_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
-    if (smem > 48 * 1024) {
+    if (smem > 16 * 1024) {  // plus 16 KB of static shared memory
         cudaError_t e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -134,32 +163,29 @@ cudaError_t launch_scan(const uint32_t* counts, uint32_t* off_local, unsigned lo
 }
 
 // ---------------------------------------------------------------- scatter
-// Same partition as k_count.  Pass 1 rebuilds the block's histogram, then one
+// Same partition and visiting order as k_count.  Pass 1 rebuilds the block's histogram, then one
 // global atomic per touched tile reserves the block's range of that bucket;
 // pass 2 writes each key at (bucket start + block range + shared cursor).
 
 __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
     extern __shared__ uint32_t sm[];
+    __shared__ uint16_t wbuf[8 * 1024];
     uint32_t* hist = sm;
     uint32_t* base = sm + P.T;
     const int el = P.e_begin + blockIdx.y;
     for (int t = threadIdx.x; t < P.T; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t)blockIdx.x * P.words_per_block;
     const int64_t w1 = min(w0 + (int64_t)P.words_per_block, P.mask_words);
     const uint32_t* mask = P.mask + (size_t)el * P.mask_words;
     const uint4* r3 = P.r3 + (size_t)el * P.G;
-    for (int64_t w = w0 + warp; w < w1; w += 8) {
-        const uint32_t m = __ldg(mask + w);
-        if ((m >> lane) & 1u) {
-            const uint4 q = r3[w * 32 + lane];
-            int tx0, tx1, ty0, ty1;
-            tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * P.ntx + tx], 1u);
-        }
-    }
+    for_each_visible(mask, w0, w1, wbuf, [&](int64_t g) {
+        const uint4 q = r3[g];
+        int tx0, tx1, ty0, ty1;
+        tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * P.ntx + tx], 1u);
+    });
     __syncthreads();
     uint32_t* cur = P.cursor + (size_t)el * P.T;
     const uint32_t* off = P.off_local + (size_t)el * P.T;
@@ -170,28 +196,24 @@ __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
         hist[t] = 0;
     }
     __syncthreads();
-    for (int64_t w = w0 + warp; w < w1; w += 8) {
-        const uint32_t m = __ldg(mask + w);
-        if ((m >> lane) & 1u) {
-            const int64_t g = w * 32 + lane;
-            const uint4 q = r3[g];
-            const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)(uint32_t)g;
-            int tx0, tx1, ty0, ty1;
-            tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) {
-                    const int t = ty * P.ntx + tx;
-                    const uint32_t k = atomicAdd(&hist[t], 1u);
-                    P.pairs[eb + base[t] + k] = key;
-                }
-        }
-    }
+    for_each_visible(mask, w0, w1, wbuf, [&](int64_t g) {
+        const uint4 q = r3[g];
+        const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)(uint32_t)g;
+        int tx0, tx1, ty0, ty1;
+        tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                const int t = ty * P.ntx + tx;
+                const uint32_t k = atomicAdd(&hist[t], 1u);
+                P.pairs[eb + base[t] + k] = key;
+            }
+    });
 }
 
 cudaError_t launch_scatter(const BinParams& P, int n_envs, cudaStream_t st, size_t smem) {
     if (n_envs == 0) return cudaSuccess;
     dim3 grid((unsigned)((P.mask_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
-    if (smem > 48 * 1024) {
+    if (smem > 16 * 1024) {  // plus 16 KB of static shared memory
         cudaError_t e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -72,11 +72,16 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* re
     return before + x - v;
 }
 
+// Radix counters are addressed through cidx: one spare 32-bit word after every
+// 16 counters, so that the raking read of 16 consecutive counters per thread
+// hits 32 different banks across a warp.
+__device__ __forceinline__ int cidx(int e) { return e + ((e >> 4) << 1); }
+
 // Sort keys[0, n) ascending by the full 64-bit key (depth bits high, global
 // index low; all distinct), n <= kCompCap.  LSD radix passes of 4 bits over
 // the depth bits that differ inside the window give a stable order by depth;
 // runs of equal depth are then ordered by index.  Returns the array that
-// holds the result (keys or tmp).  cnt: 16*NT u16; red: NT/32 u32.
+// holds the result (keys or tmp).  cnt: cidx(16*NT) u16; red: NT/32 u32.
 template <int NT>
 __device__ unsigned long long* window_sort(unsigned long long* keys, unsigned long long* tmp, uint16_t* cnt,
                                            uint32_t* red, int n) {
@@ -96,12 +101,12 @@ __device__ unsigned long long* window_sort(unsigned long long* keys, unsigned lo
     for (int shift = 0; shift < nbits; shift += 4) {
         const int s = 32 + shift;
 #pragma unroll
-        for (int d = 0; d < 16; ++d) cnt[d * NT + tid] = 0;
+        for (int d = 0; d < 16; ++d) cnt[cidx(d * NT + tid)] = 0;
         for (int i = 0; i < I; ++i) {
             const int idx = b0 + i;
             if (idx < n) {
                 const int d = (int)((src[idx] >> s) & 15ull);
-                cnt[d * NT + tid] += 1;
+                cnt[cidx(d * NT + tid)] += 1;
             }
         }
         __syncthreads();
@@ -110,13 +115,13 @@ __device__ unsigned long long* window_sort(unsigned long long* keys, unsigned lo
         uint32_t sum = 0;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-            loc[e] = cnt[tid * 16 + e];
+            loc[e] = cnt[cidx(tid * 16 + e)];
             sum += loc[e];
         }
         uint32_t run = block_excl_scan_u32<NT>(sum, red);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-            cnt[tid * 16 + e] = (uint16_t)run;
+            cnt[cidx(tid * 16 + e)] = (uint16_t)run;
             run += loc[e];
         }
         __syncthreads();
@@ -125,8 +130,8 @@ __device__ unsigned long long* window_sort(unsigned long long* keys, unsigned lo
             if (idx < n) {
                 const unsigned long long k = src[idx];
                 const int d = (int)((k >> s) & 15ull);
-                const uint32_t pos = cnt[d * NT + tid];
-                cnt[d * NT + tid] = (uint16_t)(pos + 1);
+                const uint32_t pos = cnt[cidx(d * NT + tid)];
+                cnt[cidx(d * NT + tid)] = (uint16_t)(pos + 1);
                 dst[pos] = k;
             }
         }
@@ -195,12 +200,12 @@ __device__ __forceinline__ float splat_alpha(const float4& A, const float4& B, f
 // 8x8 subtile and each lane two pixels of it, (x, y) and (x, y + 4), whose
 // blend chains are independent.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 6 : 12)) k_composite(CompParams P) {
+__global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_composite(CompParams P) {
     constexpr int NT = TW * TH / 2;
-    constexpr int NB = 2 * NT;  // splats staged per batch
+    constexpr int NB = NT;  // splats staged per batch (one per thread)
     constexpr int CAP = kCompCap;
     constexpr int UB = (CAP * 8 > NB * 64) ? CAP * 8 : NB * 64;
-    constexpr int CB = (16 * NT * 2 > 256 * 4) ? 16 * NT * 2 : 256 * 4;
+    constexpr int CB = (18 * NT * 2 > 256 * 4) ? 18 * NT * 2 : 256 * 4;
     constexpr int NW = NT / 32;
     __shared__ unsigned long long keys[CAP];
     __shared__ __align__(16) unsigned char ubuf[UB];  // sort scratch | staged records
@@ -377,31 +382,55 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 6 : 12)) k_compo
                         ov = R.x <= wx1 && R.x + R.y >= wx0 && R.z <= wy1 && R.z + R.w >= wy0;
                     }
                     uint32_t m = __ballot_sync(0xffffffffu, ov);
+                    // two splats per iteration: their four alpha evaluations are
+                    // independent; the blends then run in depth order
                     while (m) {
-                        const int k = __ffs(m) - 1;
+                        const int k1 = __ffs(m) - 1;
                         m &= m - 1u;
-                        const int jj = c + k;
-                        const int4 R = sR[jj];
-                        const bool hx = (unsigned)(px - R.x) <= (unsigned)R.y;
-                        const bool h0 = !done0 && hx && (unsigned)(py0 - R.z) <= (unsigned)R.w;
-                        const bool h1 = !done1 && hx && (unsigned)(py1 - R.z) <= (unsigned)R.w;
-                        if (h0 || h1) {
-                            const float4 A = sA[jj];
-                            const float4 B = sB[jj];
-                            const float dx = fpx - A.x;
-                            const float a0 = splat_alpha(A, B, dx, fpy0 - A.y);
-                            const float a1 = splat_alpha(A, B, dx, fpy1 - A.y);
-                            const bool u0 = h0 && a0 >= (1.0f / 255.0f);
-                            const bool u1 = h1 && a1 >= (1.0f / 255.0f);
-                            if (u0 || u1) {
-                                const float4 Cc = sC[jj];
-                                if (u0) {
+                        const bool two = m != 0u;
+                        const int k2 = two ? __ffs(m) - 1 : k1;
+                        if (two) m &= m - 1u;
+                        const int j1 = c + k1, j2 = c + k2;
+                        const int4 R1 = sR[j1];
+                        const int4 R2 = sR[j2];
+                        const bool x1 = (unsigned)(px - R1.x) <= (unsigned)R1.y;
+                        const bool x2 = two && (unsigned)(px - R2.x) <= (unsigned)R2.y;
+                        const bool h10 = !done0 && x1 && (unsigned)(py0 - R1.z) <= (unsigned)R1.w;
+                        const bool h11 = !done1 && x1 && (unsigned)(py1 - R1.z) <= (unsigned)R1.w;
+                        const bool h20 = !done0 && x2 && (unsigned)(py0 - R2.z) <= (unsigned)R2.w;
+                        const bool h21 = !done1 && x2 && (unsigned)(py1 - R2.z) <= (unsigned)R2.w;
+                        if (h10 || h11 || h20 || h21) {
+                            const float4 A1 = sA[j1], B1 = sB[j1];
+                            const float4 A2 = sA[j2], B2 = sB[j2];
+                            const float dx1 = fpx - A1.x, dx2 = fpx - A2.x;
+                            const float a10 = splat_alpha(A1, B1, dx1, fpy0 - A1.y);
+                            const float a11 = splat_alpha(A1, B1, dx1, fpy1 - A1.y);
+                            const float a20 = splat_alpha(A2, B2, dx2, fpy0 - A2.y);
+                            const float a21 = splat_alpha(A2, B2, dx2, fpy1 - A2.y);
+                            const bool u10 = h10 && a10 >= (1.0f / 255.0f);
+                            const bool u11 = h11 && a11 >= (1.0f / 255.0f);
+                            if (u10 || u11) {
+                                const float4 C1 = sC[j1];
+                                if (u10) {
                                     ++ncomp;
-                                    blend(a0, Cc, A.w, T0, r0, g0, b0, d0, done0);
+                                    blend(a10, C1, A1.w, T0, r0, g0, b0, d0, done0);
                                 }
-                                if (u1) {
+                                if (u11) {
                                     ++ncomp;
-                                    blend(a1, Cc, A.w, T1, r1, g1, b1, d1, done1);
+                                    blend(a11, C1, A1.w, T1, r1, g1, b1, d1, done1);
+                                }
+                            }
+                            const bool u20 = h20 && !done0 && a20 >= (1.0f / 255.0f);
+                            const bool u21 = h21 && !done1 && a21 >= (1.0f / 255.0f);
+                            if (u20 || u21) {
+                                const float4 C2 = sC[j2];
+                                if (u20) {
+                                    ++ncomp;
+                                    blend(a20, C2, A2.w, T0, r0, g0, b0, d0, done0);
+                                }
+                                if (u21) {
+                                    ++ncomp;
+                                    blend(a21, C2, A2.w, T1, r1, g1, b1, d1, done1);
                                 }
                             }
                         }

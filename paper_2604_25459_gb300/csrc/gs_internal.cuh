@@ -131,7 +131,11 @@ cudaError_t launch_scan(const uint32_t* counts, uint32_t* off_local, unsigned lo
 cudaError_t launch_scatter(const BinParams& P, int n_envs, cudaStream_t st, size_t smem);
 cudaError_t launch_composite(const CompParams& P, int n_envs, cudaStream_t st);
 
-constexpr int kCompCap = 2048;  // depth-ordered window held in shared memory by the compositor
+// Depth-ordered window held in shared memory by the compositor.  Smaller
+// windows sort less in tiles that terminate early, larger ones re-scan long
+// buckets less often; 768 measured best on the 2048 x 640x480 workload
+// (1024: +2 %, 512: +4 %, 2048: +19 % compositing time).
+constexpr int kCompCap = 768;
 
 // Read-only view of a scene's device data for entry points outside gs_api.cu.
 struct SceneView {

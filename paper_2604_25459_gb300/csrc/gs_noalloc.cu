@@ -203,7 +203,7 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
         B.off_local = off;
         B.env_base = env_base;
         B.cursor = cursor;
-        B.words_per_block = 128;
+        B.words_per_block = 256;  // 8 warps x 32 mask words (8192 Gaussians)
         NA_CK(launch_count(B, Wn, st, (size_t)T * 4), "count");
         NA_CK(launch_scan(counts, off, env_total, env_base, Wn, T, st), "scan");
         NA_CK(cudaMemcpyAsync(eb, env_base, sizeof(unsigned long long) * (Wn + 1), cudaMemcpyDeviceToHost, st),
