@@ -42,8 +42,8 @@ def test_c0_parity_independent_and_keyed():
     st_i, st_k, rec, proj = _keyed_check(w, 0, out)
     out["scene"].close()
     print("c0 independent", st_i, "keyed", st_k)
-    # the flag window (|alpha - 1/255| <= 1e-4/255) catches ~6e-4 sigma^2 px per splat
-    assert st_k["amb_frac"] < 0.02
+    # the alpha flag window (|alpha - 1/255| <= 1e-3/255) covers ~6e-3 sigma^2 px per splat
+    assert st_k["amb_frac"] < 0.1
 
 
 def test_c0_projection_records():
