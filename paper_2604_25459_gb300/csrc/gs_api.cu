@@ -70,7 +70,7 @@ struct DevBuf {
 struct gs_scene_s {
     int device = 0;
     DevGaussians D;
-    DevBuf g0, g1, g2, gsh;
+    DevBuf g0, g1, g2, g3, gsh;
     bool have_format = false;  // dtype / degree fixed by the first non-empty set
     uint32_t* status = nullptr;
     int tile_w = 16, tile_h = 16;
@@ -175,11 +175,13 @@ gs_status prep_view(gs_scene s, const gs_gaussians* g, int64_t dst, int link_mod
     return GS_OK;
 }
 
-gs_status alloc_gaussians(gs_scene s, int64_t n, DevBuf& a, DevBuf& b, DevBuf& c, DevBuf& sh, int planes) {
+gs_status alloc_gaussians(gs_scene s, int64_t n, DevBuf& a, DevBuf& b, DevBuf& c, DevBuf& d, DevBuf& sh,
+                          int planes) {
     const size_t m = (size_t)(n > 0 ? n : 1);
     CK(a.ensure(m * 16), "alloc p0");
     CK(b.ensure(m * 16), "alloc p1");
     CK(c.ensure(m * 16), "alloc p2");
+    CK(d.ensure(m * 16), "alloc p3");
     CK(sh.ensure(m * 16 * (size_t)(planes > 0 ? planes : 1)), "alloc sh");
     (void)s;
     return GS_OK;
@@ -322,6 +324,7 @@ gs_status render_wave(gs_scene s, const Plan& p, int e0, int We, const float* po
     P.p0 = s->D.p0;
     P.p1 = s->D.p1;
     P.p2 = s->D.p2;
+    P.p3 = s->D.p3;
     P.sh = s->D.sh;
     P.xf = s->xf.as<LinkXf>();
     P.cams = cams_dev;
@@ -580,11 +583,12 @@ gs_status gs_scene_create(const gs_gaussians* background, gs_scene* out) {
     s->D.dtype = background->dtype;
     s->D.sh_planes = sh_planes_for(s->D.sh_degree, s->D.dtype);
     s->have_format = background->n > 0;
-    gs_status r = alloc_gaussians(s, s->D.n, s->g0, s->g1, s->g2, s->gsh, s->D.sh_planes);
+    gs_status r = alloc_gaussians(s, s->D.n, s->g0, s->g1, s->g2, s->g3, s->gsh, s->D.sh_planes);
     if (r == GS_OK) {
         s->D.p0 = s->g0.as<float4>();
         s->D.p1 = s->g1.as<float4>();
         s->D.p2 = s->g2.as<float4>();
+        s->D.p3 = s->g3.as<float4>();
         s->D.sh = s->gsh.p;
         r = prep_view(s, background, 0, 0, nullptr, 0);
     }
@@ -636,15 +640,16 @@ gs_status gs_scene_attach_links(gs_scene s, int n_links, const int64_t* link_off
     }
     N.n = s->D.n_bg + lg->n;
     N.n_links = n_links;
-    DevBuf a, b, c, sh;
-    gs_status r = alloc_gaussians(s, N.n, a, b, c, sh, N.sh_planes);
+    DevBuf a, b, c, d, sh;
+    gs_status r = alloc_gaussians(s, N.n, a, b, c, d, sh, N.sh_planes);
     if (r != GS_OK) {
-        a.release(); b.release(); c.release(); sh.release();
+        a.release(); b.release(); c.release(); d.release(); sh.release();
         return r;
     }
     N.p0 = a.as<float4>();
     N.p1 = b.as<float4>();
     N.p2 = c.as<float4>();
+    N.p3 = d.as<float4>();
     N.sh = sh.p;
     const int64_t nb = s->D.n_bg;
     cudaError_t e = cudaSuccess;
@@ -652,12 +657,13 @@ gs_status gs_scene_attach_links(gs_scene s, int n_links, const int64_t* link_off
         e = cudaMemcpy(N.p0, s->D.p0, nb * 16, cudaMemcpyDeviceToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(N.p1, s->D.p1, nb * 16, cudaMemcpyDeviceToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(N.p2, s->D.p2, nb * 16, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(N.p3, s->D.p3, nb * 16, cudaMemcpyDeviceToDevice);
         for (int pl = 0; pl < N.sh_planes && e == cudaSuccess; ++pl)
             e = cudaMemcpy(static_cast<char*>(N.sh) + (size_t)pl * N.n * 16,
                            static_cast<char*>(s->D.sh) + (size_t)pl * s->D.n * 16, nb * 16, cudaMemcpyDeviceToDevice);
     }
     if (e != cudaSuccess) {
-        a.release(); b.release(); c.release(); sh.release();
+        a.release(); b.release(); c.release(); d.release(); sh.release();
         return cuda_fail(e, "copy background");
     }
     DevGaussians old = s->D;
@@ -665,11 +671,11 @@ gs_status gs_scene_attach_links(gs_scene s, int n_links, const int64_t* link_off
     r = prep_view(s, lg, nb, 1, link_offsets, n_links);
     if (r != GS_OK) {
         s->D = old;
-        a.release(); b.release(); c.release(); sh.release();
+        a.release(); b.release(); c.release(); d.release(); sh.release();
         return r;
     }
-    s->g0.release(); s->g1.release(); s->g2.release(); s->gsh.release();
-    s->g0 = a; s->g1 = b; s->g2 = c; s->gsh = sh;
+    s->g0.release(); s->g1.release(); s->g2.release(); s->g3.release(); s->gsh.release();
+    s->g0 = a; s->g1 = b; s->g2 = c; s->g3 = d; s->gsh = sh;
     if (lg->n > 0) s->have_format = true;
     s->stats.n_gaussians = s->D.n;
     return GS_OK;
@@ -821,10 +827,12 @@ gs_status gs_debug_copy_records(gs_scene s, int env, uint8_t* visible, float* u,
         if (v) v[g] = a[g].y;
         if (opacity) opacity[g] = a[g].z;
         if (z) z[g] = a[g].w;
-        if (conic) {
-            conic[3 * g] = b[g].x;
-            conic[3 * g + 1] = b[g].y;
-            conic[3 * g + 2] = b[g].z;
+        if (conic) {  // records hold L with L^T L = conic * 0.5 log2(e) (upper triangular)
+            const double k2 = 0.72134752044448170;
+            const double l00 = b[g].x, l01 = b[g].y, l11 = b[g].z;
+            conic[3 * g] = (float)(l00 * l00 / k2);
+            conic[3 * g + 1] = (float)(l00 * l01 / k2);
+            conic[3 * g + 2] = (float)((l01 * l01 + l11 * l11) / k2);
         }
         if (rgb) {
             rgb[3 * g] = c[g].x;
@@ -881,7 +889,7 @@ void gs_scene_destroy(gs_scene s) {
     if (!s) return;
     cudaSetDevice(s->device);
     cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&s->g0, &s->g1, &s->g2, &s->gsh, &s->xf, &s->cams, &s->poses, &s->r0, &s->r1, &s->r2,
+    DevBuf* bufs[] = {&s->g0, &s->g1, &s->g2, &s->g3, &s->gsh, &s->xf, &s->cams, &s->poses, &s->r0, &s->r1, &s->r2,
                       &s->r3, &s->mask, &s->counts, &s->off, &s->cursor, &s->env_total, &s->env_base, &s->pairs,
                       &s->dbg_hxy, &s->dbg_sorted, &s->stage_rgb[0], &s->stage_rgb[1], &s->stage_depth[0],
                       &s->stage_depth[1], &s->stage_alpha[0], &s->stage_alpha[1]};

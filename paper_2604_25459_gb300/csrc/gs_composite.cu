@@ -189,10 +189,13 @@ __device__ __forceinline__ void blend(float al, const float4& C, float z, float&
     }
 }
 
-// alpha = min(0.99, o 2^(a' dx^2 + b' dx dy + c' dy^2)) with the conic
-// prescaled by -log2(e) (1/2, 1, 1/2).
+// alpha = min(0.99, o exp(-q/2)) = min(0.99, o 2^-((l00 dx + l01 dy)^2 + (l11 dy)^2))
+// where B = (l00, l01, l11) is the conic's upper Cholesky factor scaled by
+// sqrt(log2(e)/2): q is evaluated as a sum of two squares.
 __device__ __forceinline__ float splat_alpha(const float4& A, const float4& B, float dx, float dy) {
-    const float pw = __fmaf_rn(__fmul_rn(B.z, dy), dy, __fmaf_rn(__fmul_rn(B.y, dx), dy, __fmul_rn(__fmul_rn(B.x, dx), dx)));
+    const float t = __fmaf_rn(B.y, dy, __fmul_rn(B.x, dx));
+    const float s = __fmul_rn(B.z, dy);
+    const float pw = -__fmaf_rn(t, t, __fmul_rn(s, s));
     return fminf(0.99f, __fmul_rn(A.z, ex2_approx(pw)));
 }
 
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_compo
     __shared__ int sel_state;
     unsigned long long* tmp = reinterpret_cast<unsigned long long*>(ubuf);
     float4* sA = reinterpret_cast<float4*>(ubuf);  // u, v, o, z
-    float4* sB = sA + NB;                          // conic * (-log2 e) / (1, 2, 1)
+    float4* sB = sA + NB;                          // scaled conic factor l00, l01, l11
     float4* sC = sB + NB;                          // r, g, b
     int4* sR = reinterpret_cast<int4*>(sC + NB);   // x0, x1 - x0, y0, y1 - y0
     uint16_t* cnt = reinterpret_cast<uint16_t*>(cbuf);
@@ -243,8 +246,6 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_compo
     const unsigned long long* Lk = P.pairs + start;
     const size_t recbase = (size_t)el * P.G;
     const bool dbg = P.dbg_sorted != nullptr;
-    constexpr float kA = -0.72134752044448170f;  // -0.5 log2(e)
-    constexpr float kB = -1.44269504088896341f;  // -log2(e)
 
     unsigned long long kmax = 0;
     if (n > (uint32_t)CAP) {
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_compo
                     const float4 q2 = P.r2[ri];
                     const uint32_t rx = __float_as_uint(q1.w), ry = __float_as_uint(q2.w);
                     sA[s] = q0;
-                    sB[s] = make_float4(q1.x * kA, q1.y * kB, q1.z * kA, 0.0f);
+                    sB[s] = make_float4(q1.x, q1.y, q1.z, 0.0f);
                     sC[s] = q2;
                     sR[s] = make_int4((int)(rx & 0xffffu), (int)((rx >> 16) - (rx & 0xffffu)), (int)(ry & 0xffffu),
                                       (int)((ry >> 16) - (ry & 0xffffu)));

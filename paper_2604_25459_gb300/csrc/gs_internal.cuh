@@ -3,11 +3,12 @@
 // Device data layout (all in HBM, owned by the scene):
 //   Gaussians, background first then link-major (global index g):
 //     p0[g] = {mean.x, mean.y, mean.z, opacity}
-//     p1[g] = {S00, S01, S02, S11}      3D covariance R diag(exp(2s)) R^T in the
-//     p2[g] = {S12, S22, qstar, link}   frame the mean lives in (world for the
-//                                       background, link frame for link Gaussians);
-//                                       qstar = 2 ln(255 o) (< 0 culls), link = 0 for
-//                                       the background, l+1 for link l (int bits)
+//     p1[g] = {F00, F01, F02, F10}      F = R diag(exp(s)), the factor of the 3D
+//     p2[g] = {F11, F12, F20, F21}      covariance F F^T in the frame the mean lives
+//     p3[g] = {F22, qstar, tr, link}    in (world for the background, link frame for
+//                                       link Gaussians); qstar = 2 ln(255 o) (< 0
+//                                       culls), tr = trace(F F^T), link = 0 for the
+//                                       background, l+1 for link l (int bits)
 //     sh plane-major: plane p holds values 4p..4p+3 (f32) or 8p..8p+7 (bf16/f16)
 //     of the flattened [coefficient][channel] vector, for every g: sh[p][g].
 //   Per wave of envs (local env index el, G Gaussians, T tiles):
@@ -53,6 +54,7 @@ struct DevGaussians {
     float4* p0 = nullptr;
     float4* p1 = nullptr;
     float4* p2 = nullptr;
+    float4* p3 = nullptr;
     void* sh = nullptr;  // sh_planes * n * 16 bytes
 };
 
@@ -67,6 +69,7 @@ struct ProjParams {
     const float4* p0;
     const float4* p1;
     const float4* p2;
+    const float4* p3;
     const void* sh;
     const LinkXf* xf;        // [We][L+1]
     const gs_camera* cams;   // [We]

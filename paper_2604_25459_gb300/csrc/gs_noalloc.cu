@@ -164,6 +164,7 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
         P.p0 = v.D.p0;
         P.p1 = v.D.p1;
         P.p2 = v.D.p2;
+        P.p3 = v.D.p3;
         P.sh = v.D.sh;
         P.xf = xf;
         P.cams = cams_dev;

@@ -39,8 +39,9 @@ __device__ __forceinline__ bool quat_rot(T w, T x, T y, T z, T* R) {
 }
 
 // ------------------------------------------------------------------ scene preparation
-// Sigma = R diag(exp(2 s)) R^T once per Gaussian (the 3DGS covariance), the
-// support threshold q* = 2 ln(255 o) and the link each Gaussian rides on.
+// Once per Gaussian: the factor F = R diag(exp(s)) of the 3DGS covariance
+// Sigma = F F^T (FP32), trace(Sigma), the support
+// threshold q* = 2 ln(255 o) and the link the Gaussian rides on.
 
 struct PrepArgs {
     const float* mean;
@@ -57,6 +58,7 @@ struct PrepArgs {
     float4* p0;
     float4* p1;
     float4* p2;
+    float4* p3;
     void* shp;
     int sh_values;
     int sh_planes;
@@ -68,20 +70,18 @@ __global__ void k_prep(PrepArgs A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     const int64_t g = A.dst + i;
-    double R[9];
-    bool ok = quat_rot<double>(A.quat[4 * i], A.quat[4 * i + 1], A.quat[4 * i + 2], A.quat[4 * i + 3], R);
-    double e2[3];
-    for (int k = 0; k < 3; ++k) e2[k] = exp(2.0 * (double)load_val<DT>(A.log_scale, 3 * i + k));
-    double S[6];  // 00 01 02 11 12 22
-    const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-    for (int m = 0; m < 6; ++m) {
-        const int a = ij[m][0], b = ij[m][1];
-        S[m] = R[3 * a] * R[3 * b] * e2[0] + R[3 * a + 1] * R[3 * b + 1] * e2[1] + R[3 * a + 2] * R[3 * b + 2] * e2[2];
-    }
+    float R[9];
+    bool ok = quat_rot<float>(A.quat[4 * i], A.quat[4 * i + 1], A.quat[4 * i + 2], A.quat[4 * i + 3], R);
+    float sc[3];
+    for (int k = 0; k < 3; ++k) sc[k] = expf(load_val<DT>(A.log_scale, 3 * i + k));
+    float F[9];  // F = R diag(exp(s)), covariance F F^T
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) F[3 * r + c] = R[3 * r + c] * sc[c];
+    const float tr = sc[0] * sc[0] + sc[1] * sc[1] + sc[2] * sc[2];
     const float o = load_val<DT>(A.opacity, i);
     float qstar = -1.0f;
-    if (o >= 1.0f / 255.0f && isfinite(o)) qstar = (float)(2.0 * log(255.0 * (double)o));
-    if (!ok || !isfinite(S[0] + S[3] + S[5])) {
+    if (o >= 1.0f / 255.0f && isfinite(o)) qstar = 2.0f * logf(255.0f * o);
+    if (!ok || !isfinite(tr)) {
         atomicOr(A.status, kStBadScene);
         qstar = -1.0f;
     }
@@ -95,8 +95,9 @@ __global__ void k_prep(PrepArgs A) {
         link = lo + 1;
     }
     A.p0[g] = make_float4(A.mean[3 * i], A.mean[3 * i + 1], A.mean[3 * i + 2], o);
-    A.p1[g] = make_float4((float)S[0], (float)S[1], (float)S[2], (float)S[3]);
-    A.p2[g] = make_float4((float)S[4], (float)S[5], qstar, __int_as_float(link));
+    A.p1[g] = make_float4(F[0], F[1], F[2], F[3]);
+    A.p2[g] = make_float4(F[4], F[5], F[6], F[7]);
+    A.p3[g] = make_float4(F[8], qstar, tr, __int_as_float(link));
     if constexpr (DT == GS_F32) {
         float* dst = static_cast<float*>(A.shp);
         for (int p = 0; p < A.sh_planes; ++p)
@@ -121,7 +122,7 @@ cudaError_t launch_prep(const float* mean, const float* quat, const void* log_sc
                         int n_links, const DevGaussians& D, uint32_t* status, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     PrepArgs A{mean, quat, log_scale, opacity, sh, n, dst_offset, link_mode, link_offsets, n_links, D.n,
-               D.p0, D.p1, D.p2, D.sh, sh_values(D.sh_degree), D.sh_planes, status};
+               D.p0, D.p1, D.p2, D.p3, D.sh, sh_values(D.sh_degree), D.sh_planes, status};
     dim3 grid((unsigned)((n + 255) / 256));
     switch (D.dtype) {
         case GS_F32: k_prep<GS_F32><<<grid, 256, 0, st>>>(A); break;
@@ -185,13 +186,16 @@ cudaError_t launch_link_table(const float* poses, const gs_camera* cams, int We,
 
 // ------------------------------------------------------------------ A2: projection
 
-// 2D covariance J W Sigma W^T J^T of one Gaussian (before the 0.3 px^2
-// low-pass), where W is the rotation part of X and J the EWA Jacobian at the
-// guard-band-clamped centre.
+// 2D covariance of one Gaussian before the 0.3 px^2 low-pass, in factored
+// form: M = J W F (2x3) with W the rotation part of X, J the EWA Jacobian at
+// the guard-band-clamped centre and F the Gaussian's covariance factor, so
+// Sigma_2 = M M^T.  Returns A = |m0|^2, B = m0.m1, C = |m1|^2 and
+// K = |m0 x m1|^2 = AC - B^2 (Lagrange's identity): computed as a cross
+// product, K carries no cancellation from A, B and C themselves.
 template <typename T>
-__device__ __forceinline__ void ewa_cov2d(const LinkXf& X, const float4& a0, const float4& a1, const float4& a2,
-                                          float fx, float fy, float limxn, float limxp, float limyn, float limyp,
-                                          T& A, T& B, T& C) {
+__device__ __forceinline__ void ewa_factor(const LinkXf& X, const float4& a0, const float4& a1, const float4& a2,
+                                           const float4& a3, float fx, float fy, float limxn, float limxp,
+                                           float limyn, float limyp, T& A, T& B, T& C, T& K) {
     const T mx = (T)X.r0.x * a0.x + (T)X.r0.y * a0.y + (T)X.r0.z * a0.z + (T)X.r0.w;
     const T my = (T)X.r1.x * a0.x + (T)X.r1.y * a0.y + (T)X.r1.z * a0.z + (T)X.r1.w;
     const T mz = (T)X.r2.x * a0.x + (T)X.r2.y * a0.y + (T)X.r2.z * a0.z + (T)X.r2.w;
@@ -203,16 +207,20 @@ __device__ __forceinline__ void ewa_cov2d(const LinkXf& X, const float4& a0, con
     const T j11 = (T)fy * iz, j12 = -(T)fy * ty * iz;
     const T w0x = j00 * X.r0.x + j02 * X.r2.x, w0y = j00 * X.r0.y + j02 * X.r2.y, w0z = j00 * X.r0.z + j02 * X.r2.z;
     const T w1x = j11 * X.r1.x + j12 * X.r2.x, w1y = j11 * X.r1.y + j12 * X.r2.y, w1z = j11 * X.r1.z + j12 * X.r2.z;
-    const T s00 = a1.x, s01 = a1.y, s02 = a1.z, s11 = a1.w, s12 = a2.x, s22 = a2.y;
-    const T v0x = s00 * w0x + s01 * w0y + s02 * w0z;
-    const T v0y = s01 * w0x + s11 * w0y + s12 * w0z;
-    const T v0z = s02 * w0x + s12 * w0y + s22 * w0z;
-    const T v1x = s00 * w1x + s01 * w1y + s02 * w1z;
-    const T v1y = s01 * w1x + s11 * w1y + s12 * w1z;
-    const T v1z = s02 * w1x + s12 * w1y + s22 * w1z;
-    A = w0x * v0x + w0y * v0y + w0z * v0z;
-    B = w1x * v0x + w1y * v0y + w1z * v0z;
-    C = w1x * v1x + w1y * v1y + w1z * v1z;
+    // F row-major: (F00 F01 F02 | F10 F11 F12 | F20 F21 F22)
+    const T f00 = a1.x, f01 = a1.y, f02 = a1.z, f10 = a1.w, f11 = a2.x, f12 = a2.y, f20 = a2.z, f21 = a2.w,
+            f22 = a3.x;
+    const T m0x = w0x * f00 + w0y * f10 + w0z * f20;
+    const T m0y = w0x * f01 + w0y * f11 + w0z * f21;
+    const T m0z = w0x * f02 + w0y * f12 + w0z * f22;
+    const T m1x = w1x * f00 + w1y * f10 + w1z * f20;
+    const T m1y = w1x * f01 + w1y * f11 + w1z * f21;
+    const T m1z = w1x * f02 + w1y * f12 + w1z * f22;
+    A = m0x * m0x + m0y * m0y + m0z * m0z;
+    B = m0x * m1x + m0y * m1y + m0z * m1z;
+    C = m1x * m1x + m1y * m1y + m1z * m1z;
+    const T kx = m0y * m1z - m0z * m1y, ky = m0z * m1x - m0x * m1z, kz = m0x * m1y - m0y * m1x;
+    K = kx * kx + ky * ky + kz * kz;
 }
 
 // Real SH basis through degree D in the 3DGS order (k = l*l + l + m), with the
@@ -316,16 +324,17 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
     const bool act = g < P.G;
     const int lane = threadIdx.x & 31;
     const int64_t gw = g - lane;
-    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
     if (act) {
         a0 = __ldg(P.p0 + g);
         a1 = __ldg(P.p1 + g);
         a2 = __ldg(P.p2 + g);
+        a3 = __ldg(P.p3 + g);
     }
-    const int li = __float_as_int(a2.w);
-    const float qstar = a2.z;
+    const int li = __float_as_int(a3.w);
+    const float qstar = a3.y;
     const bool live = act && qstar >= 0.0f;
-    const float trace = a1.x + a1.w + a2.y;  // >= largest eigenvalue of Sigma (rotation-invariant)
+    const float trace = a3.z;  // trace(Sigma) >= its largest eigenvalue (rotation-invariant)
     float sh[NV];
     const int e0 = blockIdx.y * P.env_group;
     const int e1 = min(P.We, e0 + P.env_group);
@@ -360,31 +369,38 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                 const bool maybe = (u + hxb >= 0.5f) && (u - hxb <= (float)W - 0.5f) && (v + hyb >= 0.5f) &&
                                    (v - hyb <= (float)H - 0.5f);
                 if (maybe) {
-                    float A, B, C;
-                    ewa_cov2d<float>(X, a0, a1, a2, fx, fy, limxn, limxp, limyn, limyp, A, B, C);
-                    float cA = A + 0.3f, cC = C + 0.3f;
-                    float det = cA * cC - B * B;
-                    float ca, cb, cc;
-                    bool ok = true;
-                    if (det > 0x1p-10f * cA * cC) {
-                        const float id = 1.0f / det;
-                        ca = cC * id;
-                        cb = -B * id;
-                        cc = cA * id;
+                    // Sigma_2 = M M^T + 0.3 I; det = K + 0.3 (A + C) + 0.09 is a sum of
+                    // non-negative terms.  The conic enters the compositor as its
+                    // upper Cholesky factor L (L^T L = conic, l11 = 1/sqrt(C + 0.3)),
+                    // scaled by sqrt(log2(e)/2) so that alpha = o 2^-(|L d|^2), a sum of
+                    // two squares with no cancellation for thin splats.
+                    constexpr float kS = 0.84932180028801907f;  // sqrt(0.5 log2(e))
+                    float A, B, C, K;
+                    ewa_factor<float>(X, a0, a1, a2, a3, fx, fy, limxn, limxp, limyn, limyp, A, B, C, K);
+                    float cA, cC, l00, l01, l11;
+                    if (K >= 0x1p-10f * A * C) {
+                        cA = A + 0.3f;
+                        cC = C + 0.3f;
+                        const float det = K + 0.3f * (A + C) + 0.09f;
+                        const float rc = 1.0f / sqrtf(cC);
+                        l00 = kS * sqrtf(cC / det);
+                        l01 = -kS * B * rc / sqrtf(det);
+                        l11 = kS * rc;
                     } else {
-                        // near-degenerate: the whole 2D covariance and its inverse in FP64
-                        double dA, dB, dC;
-                        ewa_cov2d<double>(X, a0, a1, a2, fx, fy, limxn, limxp, limyn, limyp, dA, dB, dC);
-                        dA += 0.3;
-                        dC += 0.3;
-                        const double ddet = dA * dC - dB * dB;
-                        ok = ddet > 0.0;
-                        ca = (float)(dC / ddet);
-                        cb = (float)(-dB / ddet);
-                        cc = (float)(dA / ddet);
-                        cA = (float)dA;
-                        cC = (float)dC;
+                        // near-degenerate 2D covariance (a thin Gaussian seen edge-on):
+                        // the factor, its products and the conic factor in FP64
+                        double dA, dB, dC, dK;
+                        ewa_factor<double>(X, a0, a1, a2, a3, fx, fy, limxn, limxp, limyn, limyp, dA, dB, dC, dK);
+                        const double eA = dA + 0.3, eC = dC + 0.3;
+                        const double det = dK + 0.3 * (dA + dC) + 0.09;
+                        const double rc = 1.0 / sqrt(eC);
+                        l00 = (float)((double)kS * sqrt(eC / det));
+                        l01 = (float)(-(double)kS * dB * rc / sqrt(det));
+                        l11 = (float)((double)kS * rc);
+                        cA = (float)eA;
+                        cC = (float)eC;
                     }
+                    const bool ok = true;
                     const float hx = sqrtf(qstar * cA) * 1.0001f;
                     const float hy = sqrtf(qstar * cC) * 1.0001f;
                     int i0, i1, j0, j1;
@@ -404,7 +420,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                         const uint32_t ry = (uint32_t)j0 | ((uint32_t)j1 << 16);
                         const size_t ri = (size_t)el * P.G + g;
                         P.r0[ri] = make_float4(u, v, a0.w, mz);
-                        P.r1[ri] = make_float4(ca, cb, cc, __uint_as_float(rx));
+                        P.r1[ri] = make_float4(l00, l01, l11, __uint_as_float(rx));
                         P.r2[ri] = make_float4(r, gg, b, __uint_as_float(ry));
                         P.r3[ri] = make_uint4(rx, ry, __float_as_uint(mz), 0u);
                         if (P.dbg_hxy) P.dbg_hxy[ri] = make_float2(hx, hy);
