@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-envs", type=int, default=2, help="envs in the CPU-baseline sample")
+    ap.add_argument("--workload", choices=["c1", "c3"], default="c1",
+                    help="c1: uniform 640x480 batch (headline); c3: batched uneven form through a plan")
+    ap.add_argument("--no-graph", action="store_true", help="c3: eager plan launches instead of a CUDA graph")
     return ap.parse_args()
 
 
@@ -330,6 +333,83 @@ def run_ours(a, rank, world, local_rank):
     scene.close()
 
 
+def run_c3(a, rank, world, local_rank):
+    """Batched uneven form: 4096 envs, per-env objects of 10k-200k Gaussians on a
+    shared 300k background, resolutions {64^2, 128^2, 320x240, 640x480} with
+    probabilities {.3, .3, .2, .2}; one plan (autotuned tile shape and claim
+    size, replayed from a captured CUDA graph); a step is one plan launch."""
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2604_25459_gb300 import gsbatch, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    E = a.envs if a.envs != 2048 else 4096
+    t0 = time.perf_counter()
+    w = synth.make_c3(n_envs=E, threads=os.cpu_count() or 8)
+    gen_s = time.perf_counter() - t0
+    scene = gsbatch.Scene(w.background)
+    scene.attach_links(w.link_offsets, w.links)
+    envs = gsbatch.make_envs(w.cams, link_ranges=np.stack([np.arange(E), np.arange(E) + 1], 1),
+                             pose_offsets=np.arange(E))
+    npx = int((w.cams["width"].astype(np.int64) * w.cams["height"]).sum())
+    rgb = torch.empty(npx * 3, device=dev)
+    depth = torch.empty(npx, device=dev)
+    poses = torch.from_numpy(w.link_poses).to(dev)
+    stream = torch.cuda.current_stream()
+    plan = scene.plan(envs, autotune=True, graph=not a.no_graph)
+    t0 = time.perf_counter()
+    plan.launch(poses, rgb, depth, stream=stream)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    for _ in range(a.warmup):
+        plan.launch(poses, rgb, depth, stream=stream)
+    torch.cuda.synchronize()
+    scene.sync_status()
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    evs[0].record(stream)
+    for k in range(a.steps):
+        plan.launch(poses, rgb, depth, stream=stream)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    scene.sync_status()
+    lat = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(a.steps))
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    info = plan.info()
+    if rank == 0:
+        value = world * E * a.steps / (total_ms / 1e3)
+        res, cnt = np.unique(w.cams["width"], return_counts=True)
+        line = {"metric": "env-frames/s, batched uneven RGB-D (4096 mixed-resolution envs)", "value": value,
+                "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"c3: {E} envs, 300k background + per-env objects log-uniform 10k-200k "
+                                       f"({w.links.n} object Gaussians), widths {dict(zip(res.tolist(), cnt.tolist()))}",
+                           "l2": f"{npx * 16 / 1e9:.2f} GB of outputs per step"},
+                "mpix_per_s": value * npx / E / 1e6,
+                "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+                "clocks": ck, "plan": info, "generate_s": gen_s, "first_launch_s": tune_s,
+                "gpu_launches": None, "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    scene.close()
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -347,6 +427,8 @@ def main():
             dist.init_process_group("gloo")
     if a.impl == "reference":
         run_reference(a, rank, world)
+    elif a.workload == "c3":
+        run_c3(a, rank, world, local_rank)
     else:
         run_ours(a, rank, world, local_rank)
     if world > 1:

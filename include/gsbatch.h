@@ -127,6 +127,58 @@ gs_status gs_render_batch(gs_scene s, int n_envs, const float* link_poses, const
 gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
                                float* depth, float* alpha, void* cuda_stream);
 
+/* One environment of an uneven batch (gs_render_batch_v, plans).  80 bytes. */
+typedef struct {
+    gs_camera cam;        /* its own camera, width and height */
+    int32_t link_begin;   /* renders the scene's links [link_begin, link_end) on top of the background */
+    int32_t link_end;
+    int64_t pose_offset;  /* index, in units of 7 floats, of the pose of link_begin in link_poses */
+    int64_t pixel_offset; /* first pixel of this env's image: rgb[3*pixel_offset..], depth[pixel_offset..] */
+} gs_env;
+
+/* Render environments of different resolutions and link subsets in one call
+ * (the batched uneven form; each env's (env, tile) work items run in the same
+ * persistent compositing launch).  envs: HOST array; link_poses, rgb, depth,
+ * alpha: DEVICE.  Images may be placed anywhere in the output buffers through
+ * pixel_offset (they must not overlap).  Results equal gs_render_batch for
+ * the same env.  Tile shape, budget and waves as for gs_render_batch.
+ * Errors: GS_ERR_INVALID (bad camera, link range outside the scene, negative
+ * offsets), GS_ERR_OOM, GS_ERR_CUDA. */
+gs_status gs_render_batch_v(gs_scene s, int n_envs, const gs_env* envs, const float* link_poses, float* rgb,
+                            float* depth, float* alpha, void* cuda_stream);
+
+/* A plan is a fixed batch (environments, resolutions, link subsets) rendered
+ * repeatedly with changing poses.  Its first launch runs eagerly: with
+ * GS_PLAN_AUTOTUNE it times every tile shape (8x8, 16x8, 16x16, 32x8) and
+ * compositor claim size (1 or 4 tiles per atomic) and keeps the fastest (the
+ * images do not depend on the choice); it sizes the intersection-key buffer at
+ * 1.25x what that launch needed.  With GS_PLAN_GRAPH the whole render (all
+ * waves) is then captured in a CUDA graph and later launches replay it with
+ * no host synchronisation (re-captured when the pose or output pointers
+ * change).  If poses later need more keys than the capacity, the extra keys
+ * are dropped, the scene's status word reports it (gs_scene_sync_status), and
+ * the next launch after that one completed re-measures the need with an eager
+ * pass (host-synchronising), resizes to 1.25x and re-captures.  The plan owns
+ * its scratch (separate from the scene's). */
+enum { GS_PLAN_AUTOTUNE = 1, GS_PLAN_GRAPH = 2 };
+typedef struct gs_plan_s* gs_plan;
+typedef struct {
+    int tile_w, tile_h;     /* chosen tile shape */
+    int chunk;              /* chosen compositor claim size */
+    int waves;              /* waves per launch */
+    int graph;              /* 1 once a CUDA graph is instantiated */
+    int tuned_candidates;   /* configurations timed by the autotuner */
+    double tuned_ms;        /* eager time of the chosen configuration */
+    int regrows;            /* capacity re-measurements after overflows */
+    int64_t key_capacity;   /* intersection keys, all waves */
+    int64_t scratch_bytes;  /* device scratch held by the plan */
+} gs_plan_info;
+gs_status gs_plan_create(gs_scene s, int n_envs, const gs_env* envs, int flags, gs_plan* out);
+gs_status gs_plan_launch(gs_plan p, const float* link_poses, float* rgb, float* depth, float* alpha,
+                         void* cuda_stream);
+gs_status gs_plan_get_info(gs_plan p, gs_plan_info* out);
+void gs_plan_destroy(gs_plan p);
+
 /* As gs_render_batch (same arguments, same kernels, same results), but it
  * allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The
  * paper has no counterpart; this is for callers that must not allocate device

@@ -1,11 +1,13 @@
-// C ABI of libgsbatch: scenes, batched rendering, status and debug hooks.
+// C ABI of libgsbatch: scenes, batched rendering (uniform, uneven, planned
+// under a CUDA graph), status, profiling and debug hooks.
 //
 // The call sequence follows the paper's loop (Sec. III-A "Data Flow"): poses
 // from the physics step -> RLGK (Sec. III-C) -> batch 3DGS renderer (Sec.
 // III-C "Throughput Scaling") -> RGB + depth per environment.  Every step of
 // the render runs in the kernels of gs_project.cu, gs_bin.cu and
-// gs_composite.cu; this file validates arguments, plans waves of
-// environments against the scratch budget and orders the launches.
+// gs_composite.cu; this file validates arguments, plans waves of environments
+// against the scratch budget and orders the launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -39,10 +41,15 @@ gs_status cuda_fail(cudaError_t e, const char* what) {
     return fail(GS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call, what)                                   \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
+#define CK(call, what)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+#define ST(call)                        \
+    do {                                \
+        gs_status s_ = (call);          \
+        if (s_ != GS_OK) return s_;     \
     } while (0)
 
 struct DevBuf {
@@ -54,6 +61,7 @@ struct DevBuf {
         bytes = 0;
     }
     cudaError_t ensure(size_t need) {
+        if (need == 0) need = 16;
         if (need <= bytes) return cudaSuccess;
         release();
         cudaError_t e = cudaMalloc(&p, need);
@@ -65,31 +73,50 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// Device scratch of a render: one set per scene (eager calls) and one per plan.
+struct Scratch {
+    DevBuf envs, blocks, cams, xf, r0, r1, r2, r3, mask, counts, off, cursor, env_total, env_base, pairs, dbg_hxy,
+        dbg_sorted, work;
+    DevBuf* all[18] = {&envs, &blocks, &cams, &xf, &r0, &r1, &r2, &r3, &mask, &counts,
+                       &off, &cursor, &env_total, &env_base, &pairs, &dbg_hxy, &dbg_sorted, &work};
+    void release() {
+        for (DevBuf* b : all) b->release();
+    }
+    int64_t bytes() const {
+        int64_t n = 0;
+        for (const DevBuf* b : all) n += (int64_t)b->bytes;
+        return n;
+    }
+};
+
+bool valid_tile(int tw, int th) {
+    return (tw == 8 && th == 8) || (tw == 16 && th == 8) || (tw == 16 && th == 16) || (tw == 32 && th == 8);
+}
+
 }  // namespace
 
 struct gs_scene_s {
     int device = 0;
     DevGaussians D;
     DevBuf g0, g1, g2, g3, gsh;
-    bool have_format = false;  // dtype / degree fixed by the first non-empty set
+    std::vector<int64_t> link_offsets{0};  // host copy, n_links + 1 entries
+    bool have_format = false;               // dtype / degree fixed by the first non-empty set
     uint32_t* status = nullptr;
     int tile_w = 16, tile_h = 16;
     int64_t budget = 64ll << 30;
     int max_wave = 0;
     int debug = 0;
-    // scratch
-    DevBuf xf, cams, poses, r0, r1, r2, r3, mask, counts, off, cursor, env_total, env_base, pairs, dbg_hxy,
-        dbg_sorted;
-    DevBuf stage_rgb[2], stage_depth[2], stage_alpha[2];
+    Scratch sc;
+    DevBuf stage_rgb[2], stage_depth[2], stage_alpha[2], poses;
     unsigned long long* pinned = nullptr;
     size_t pinned_n = 0;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_done[2] = {nullptr, nullptr};
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};
-    // what the last render left for the debug hooks
-    int last_e0 = -1, last_We = 0, last_ea = 0, last_eb = 0, last_W = 0, last_H = 0, last_T = 0;
+    // host tables of the last wave (debug hooks)
+    std::vector<EnvInfo> last_envs;
+    int last_e0 = -1, last_We = 0, last_ea = 0, last_eb = 0;
     unsigned long long last_pair_base = 0;
-    int64_t last_pairs = 0;
     gs_stats stats{};
     // profiling (per-phase CUDA events on the render stream) and counters
     int profile = 0;
@@ -104,14 +131,48 @@ struct gs_scene_s {
     int64_t prof_launches[GS_PHASES] = {0};
     int counters = 0;
     DevBuf neval;
+    // host staging of tables
+    std::vector<EnvInfo> h_envs;
+    std::vector<ProjBlock> h_blocks;
+    std::vector<gs_camera> h_cams;
+};
+
+struct gs_plan_s {
+    gs_scene s = nullptr;
+    std::vector<gs_env> envs;
+    std::vector<gs_camera> cams;
+    int flags = 0;
+    int tile_w = 16, tile_h = 16, chunk = 1;
+    Scratch sc;
+    struct Wave {
+        int e0, e1;
+        DevBuf envs, blocks, cams;
+        int n_blocks = 0, xf_items = 0, max_words = 0, max_T = 0;
+        unsigned long long recs = 0, words = 0, tiles = 0;
+        unsigned long long cap = 0;  // intersection-key capacity
+    };
+    std::vector<Wave> waves;
+    bool tuned = false;
+    int tuned_candidates = 0;
+    double tuned_ms = 0.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* cap_ptrs[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
+    uint32_t* pinned_status = nullptr;
+    cudaEvent_t done = nullptr;
+    bool launched = false;
+    int regrows = 0;
 };
 
 namespace {
 
+// ------------------------------------------------------------------ scene upload
+
 gs_status check_view(const gs_gaussians* g, const char* name) {
     if (!g) return fail(GS_ERR_INVALID, "%s: null gs_gaussians", name);
     if (g->n < 0) return fail(GS_ERR_INVALID, "%s: negative n", name);
-    if (g->n > 0xFFFFFFF0ll) return fail(GS_ERR_UNSUPPORTED, "%s: more than 2^32-16 Gaussians", name);
+    if (g->n > 0x7FFFFFF0ll) return fail(GS_ERR_UNSUPPORTED, "%s: more than 2^31-16 Gaussians", name);
     if (g->sh_degree < 0 || g->sh_degree > 3) return fail(GS_ERR_INVALID, "%s: sh_degree must be 0..3", name);
     if (g->dtype != GS_F32 && g->dtype != GS_BF16 && g->dtype != GS_F16)
         return fail(GS_ERR_INVALID, "%s: unknown dtype", name);
@@ -175,65 +236,119 @@ gs_status prep_view(gs_scene s, const gs_gaussians* g, int64_t dst, int link_mod
     return GS_OK;
 }
 
-gs_status alloc_gaussians(gs_scene s, int64_t n, DevBuf& a, DevBuf& b, DevBuf& c, DevBuf& d, DevBuf& sh,
-                          int planes) {
+gs_status alloc_gaussians(int64_t n, DevBuf& a, DevBuf& b, DevBuf& c, DevBuf& d, DevBuf& sh, int planes) {
     const size_t m = (size_t)(n > 0 ? n : 1);
     CK(a.ensure(m * 16), "alloc p0");
     CK(b.ensure(m * 16), "alloc p1");
     CK(c.ensure(m * 16), "alloc p2");
     CK(d.ensure(m * 16), "alloc p3");
     CK(sh.ensure(m * 16 * (size_t)(planes > 0 ? planes : 1)), "alloc sh");
-    (void)s;
     return GS_OK;
 }
 
-gs_status check_cams(const gs_camera* cams, int E, int* W, int* H) {
-    for (int e = 0; e < E; ++e) {
-        const gs_camera& c = cams[e];
-        if (e == 0) {
-            *W = c.width;
-            *H = c.height;
-        }
-        if (c.width != *W || c.height != *H)
-            return fail(GS_ERR_INVALID, "camera %d: resolution %dx%d differs from camera 0 (%dx%d)", e, c.width,
-                        c.height, *W, *H);
-        if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
-            return fail(GS_ERR_INVALID, "camera %d: width/height must be in [1, 16384]", e);
-        if (!(std::isfinite(c.fx) && std::isfinite(c.fy) && c.fx > 0 && c.fy > 0))
-            return fail(GS_ERR_INVALID, "camera %d: focal lengths must be finite and > 0", e);
-        if (!(std::isfinite(c.cx) && std::isfinite(c.cy)))
-            return fail(GS_ERR_INVALID, "camera %d: principal point must be finite", e);
-        if (!(std::isfinite(c.near_plane) && c.near_plane > 0))
-            return fail(GS_ERR_INVALID, "camera %d: near_plane must be finite and > 0", e);
-        double qn = 0;
-        for (int k = 0; k < 4; ++k) {
-            if (!std::isfinite(c.q_cw[k])) return fail(GS_ERR_INVALID, "camera %d: non-finite quaternion", e);
-            qn += (double)c.q_cw[k] * c.q_cw[k];
-        }
-        if (!(qn > 0)) return fail(GS_ERR_INVALID, "camera %d: zero quaternion", e);
-        for (int k = 0; k < 3; ++k)
-            if (!std::isfinite(c.t_cw[k])) return fail(GS_ERR_INVALID, "camera %d: non-finite translation", e);
+// ------------------------------------------------------------------ env validation
+
+gs_status check_cam(const gs_camera& c, int e) {
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
+        return fail(GS_ERR_INVALID, "env %d: width/height must be in [1, 16384]", e);
+    if (!(std::isfinite(c.fx) && std::isfinite(c.fy) && c.fx > 0 && c.fy > 0))
+        return fail(GS_ERR_INVALID, "env %d: focal lengths must be finite and > 0", e);
+    if (!(std::isfinite(c.cx) && std::isfinite(c.cy)))
+        return fail(GS_ERR_INVALID, "env %d: principal point must be finite", e);
+    if (!(std::isfinite(c.near_plane) && c.near_plane > 0))
+        return fail(GS_ERR_INVALID, "env %d: near_plane must be finite and > 0", e);
+    double qn = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (!std::isfinite(c.q_cw[k])) return fail(GS_ERR_INVALID, "env %d: non-finite camera quaternion", e);
+        qn += (double)c.q_cw[k] * c.q_cw[k];
+    }
+    if (!(qn > 0)) return fail(GS_ERR_INVALID, "env %d: zero camera quaternion", e);
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(c.t_cw[k])) return fail(GS_ERR_INVALID, "env %d: non-finite camera translation", e);
+    return GS_OK;
+}
+
+gs_status check_specs(gs_scene s, const std::vector<EnvSpec>& specs, int tw, int th) {
+    for (size_t e = 0; e < specs.size(); ++e) {
+        const EnvSpec& sp = specs[e];
+        ST(check_cam(*sp.cam, (int)e));
+        const int ntx = (sp.cam->width + tw - 1) / tw, nty = (sp.cam->height + th - 1) / th;
+        if (ntx * nty > 16384)
+            return fail(GS_ERR_UNSUPPORTED, "env %d: %d tiles exceed the 16384 supported (use larger tiles)", (int)e,
+                        ntx * nty);
+        if (sp.link_begin < 0 || sp.link_end < sp.link_begin || sp.link_end > s->D.n_links)
+            return fail(GS_ERR_INVALID, "env %d: link range [%d, %d) outside [0, %d]", (int)e, sp.link_begin,
+                        sp.link_end, s->D.n_links);
+        if (sp.link_end > sp.link_begin && sp.pose_offset < 0)
+            return fail(GS_ERR_INVALID, "env %d: negative pose_offset", (int)e);
+        if (sp.pixel_offset < 0) return fail(GS_ERR_INVALID, "env %d: negative pixel_offset", (int)e);
     }
     return GS_OK;
 }
 
-struct Plan {
-    int64_t G;
-    int L, W, H, ntx, nty, T;
-    int64_t mask_words;
-    size_t per_env;
-    int We;  // envs per wave
-};
+// Fixed scratch bytes of one env (records, visibility, tile counters, link table).
+size_t env_bytes(gs_scene s, const EnvSpec& sp, int tw, int th, bool debug) {
+    const int64_t nlg = s->link_offsets[sp.link_end] - s->link_offsets[sp.link_begin];
+    const int64_t n_local = bg_slots(s->D.n_bg) + nlg;
+    const int64_t T = (int64_t)((sp.cam->width + tw - 1) / tw) * ((sp.cam->height + th - 1) / th);
+    size_t b = (size_t)n_local * 64 + (size_t)((n_local + 31) / 32) * 4 + (size_t)T * 12 + 16 +
+               (size_t)(1 + sp.link_end - sp.link_begin) * sizeof(LinkXf) + sizeof(gs_camera) + sizeof(EnvInfo) + 64;
+    if (debug) b += (size_t)n_local * 8;
+    return b;
+}
+
+// Split envs into waves whose fixed scratch fits 60 % of the budget.
+gs_status plan_waves(gs_scene s, const std::vector<EnvSpec>& specs, int tw, int th, bool debug, int max_wave,
+                     size_t extra_per_env, std::vector<std::pair<int, int>>* waves) {
+    waves->clear();
+    const double cap = (double)s->budget * 0.6;
+    const int E = (int)specs.size();
+    // uniform batches: balanced waves of equal size
+    bool uniform = true;
+    for (int e = 1; e < E && uniform; ++e)
+        uniform = specs[e].cam->width == specs[0].cam->width && specs[e].cam->height == specs[0].cam->height &&
+                  specs[e].link_begin == specs[0].link_begin && specs[e].link_end == specs[0].link_end;
+    if (uniform && E > 0) {
+        const double per = (double)(env_bytes(s, specs[0], tw, th, debug) + extra_per_env);
+        int64_t wmax = (int64_t)(cap / per);
+        if (wmax < 1)
+            return fail(GS_ERR_OOM, "one environment needs %.0f bytes of scratch; budget is %lld", per,
+                        (long long)s->budget);
+        if (max_wave > 0 && wmax > max_wave) wmax = max_wave;
+        if (wmax > E) wmax = E;
+        const int64_t nw = (E + wmax - 1) / wmax;
+        const int We = (int)((E + nw - 1) / nw);
+        for (int e0 = 0; e0 < E; e0 += We) waves->push_back({e0, std::min(E, e0 + We)});
+        return GS_OK;
+    }
+    int e0 = 0;
+    double acc = 0;
+    for (int e = 0; e < E; ++e) {
+        const double b = (double)(env_bytes(s, specs[e], tw, th, debug) + extra_per_env);
+        if (b > cap) return fail(GS_ERR_OOM, "env %d needs %.0f bytes of scratch; budget is %lld", e, b,
+                                 (long long)s->budget);
+        if (e > e0 && (acc + b > cap || (max_wave > 0 && e - e0 >= max_wave))) {
+            waves->push_back({e0, e});
+            e0 = e;
+            acc = 0;
+        }
+        acc += b;
+    }
+    if (E > e0) waves->push_back({e0, E});
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------ one wave
 
 // Brackets one phase's launches with events on the render stream when
-// profiling is on.
+// profiling is on (eager renders only).
 struct PhaseTimer {
     gs_scene s;
     cudaStream_t st;
     int phase;
     cudaEvent_t a = nullptr;
-    PhaseTimer(gs_scene s_, cudaStream_t st_, int ph) : s(s_), st(st_), phase(ph) {
-        if (s->profile) {
+    PhaseTimer(gs_scene s_, cudaStream_t st_, int ph, bool on) : s(s_), st(st_), phase(ph) {
+        if (on && s->profile) {
             a = take();
             if (a) cudaEventRecord(a, st);
         }
@@ -258,299 +373,475 @@ struct PhaseTimer {
     }
 };
 
-gs_status make_plan(gs_scene s, int E, int W, int H, bool host_mode, Plan* p) {
-    p->G = s->D.n;
-    p->L = s->D.n_links;
-    p->W = W;
-    p->H = H;
-    p->ntx = (W + s->tile_w - 1) / s->tile_w;
-    p->nty = (H + s->tile_h - 1) / s->tile_h;
-    p->T = p->ntx * p->nty;
-    if (p->T > 16384)
-        return fail(GS_ERR_UNSUPPORTED, "%d tiles per image exceed the 16384 supported (use larger tiles)", p->T);
-    p->mask_words = (p->G + 31) / 32;
-    size_t per = (size_t)p->G * 64 + (size_t)p->mask_words * 4 + (size_t)p->T * 12 + 16 + (size_t)(p->L + 1) * 64;
-    if (s->debug) per += (size_t)p->G * 8;
-    if (host_mode) per += (size_t)W * H * 20 * 2;  // two staging sets of rgb + depth + alpha
-    p->per_env = per;
-    int64_t wmax = (int64_t)((double)s->budget * 0.6 / (double)per);
-    if (wmax < 1) return fail(GS_ERR_OOM, "one environment needs %zu bytes of scratch; budget is %lld", per,
-                              (long long)s->budget);
-    if (s->max_wave > 0 && wmax > s->max_wave) wmax = s->max_wave;
-    if (wmax > E) wmax = E;
-    const int64_t nw = (E + wmax - 1) / wmax;
-    p->We = (int)((E + nw - 1) / nw);
+struct WaveIO {
+    const float* poses;   // device, indexed by the specs' pose offsets
+    float* rgb;           // device outputs, indexed by pixel offsets minus pix_rebase
+    float* depth;
+    float* alpha;
+    long long pix_rebase;
+};
+
+struct WaveTables {       // device copies of one wave's tables
+    const EnvInfo* envs;
+    const ProjBlock* blocks;
+    const gs_camera* cams;
+    int We, n_blocks, xf_items, max_words, max_T;
+    unsigned long long recs, words, tiles;
+    const EnvInfo* host_envs;  // We + 1 host entries
+};
+
+// Build and upload the tables of specs[e0, e1) into the given device buffers.
+gs_status upload_tables(gs_scene s, const std::vector<EnvSpec>& specs, int e0, int e1, int tw, int th,
+                        long long pix_rebase, DevBuf& d_envs, DevBuf& d_blocks, DevBuf& d_cams, cudaStream_t st,
+                        bool sync_copy, WaveTables* wt) {
+    const int We = e1 - e0;
+    const EnvSpec* sp = specs.data() + e0;
+    const int nb = count_wave_blocks(s->D, s->link_offsets.data(), sp, We);
+    s->h_envs.resize((size_t)We + 1);
+    s->h_blocks.resize((size_t)std::max(nb, 1));
+    s->h_cams.resize((size_t)We);
+    int nb2 = 0;
+    build_wave_tables(s->D, s->link_offsets.data(), sp, We, tw, th, pix_rebase, s->h_envs.data(), s->h_blocks.data(),
+                      &nb2, nb);
+    int max_words = 0, max_T = 0;
+    for (int e = 0; e < We; ++e) {
+        s->h_cams[e] = *sp[e].cam;
+        max_words = std::max(max_words, (int)((s->h_envs[e].n_local + 31) / 32));
+        max_T = std::max(max_T, s->h_envs[e].T);
+    }
+    CK(d_envs.ensure(sizeof(EnvInfo) * ((size_t)We + 1)), "alloc env table");
+    CK(d_blocks.ensure(sizeof(ProjBlock) * (size_t)std::max(nb, 1)), "alloc block table");
+    CK(d_cams.ensure(sizeof(gs_camera) * (size_t)We), "alloc cameras");
+    if (sync_copy) {
+        CK(cudaMemcpy(d_envs.p, s->h_envs.data(), sizeof(EnvInfo) * ((size_t)We + 1), cudaMemcpyHostToDevice),
+           "copy env table");
+        CK(cudaMemcpy(d_blocks.p, s->h_blocks.data(), sizeof(ProjBlock) * (size_t)nb, cudaMemcpyHostToDevice),
+           "copy block table");
+        CK(cudaMemcpy(d_cams.p, s->h_cams.data(), sizeof(gs_camera) * (size_t)We, cudaMemcpyHostToDevice),
+           "copy cameras");
+    } else {  // pageable sources: the copies are staged before the calls return
+        CK(cudaMemcpyAsync(d_envs.p, s->h_envs.data(), sizeof(EnvInfo) * ((size_t)We + 1), cudaMemcpyHostToDevice,
+                           st),
+           "copy env table");
+        CK(cudaMemcpyAsync(d_blocks.p, s->h_blocks.data(), sizeof(ProjBlock) * (size_t)nb, cudaMemcpyHostToDevice,
+                           st),
+           "copy block table");
+        CK(cudaMemcpyAsync(d_cams.p, s->h_cams.data(), sizeof(gs_camera) * (size_t)We, cudaMemcpyHostToDevice, st),
+           "copy cameras");
+    }
+    const EnvInfo& sen = s->h_envs[We];
+    *wt = WaveTables{d_envs.as<EnvInfo>(), d_blocks.as<ProjBlock>(), d_cams.as<gs_camera>(), We, nb, sen.xf_base,
+                     max_words, max_T, sen.rec_base, sen.mask_base, sen.tile_base, s->h_envs.data()};
     return GS_OK;
 }
 
-}  // namespace
-
-namespace {
-
-// Render envs [e0, e0+We) whose poses/cams are already on the device; the
-// wave's outputs go to rgb/depth/alpha (device, wave-local env indexing).
-gs_status render_wave(gs_scene s, const Plan& p, int e0, int We, const float* poses_dev, const gs_camera* cams_dev,
-                      float* rgb, float* depth, float* alpha, cudaStream_t st, int64_t* launches) {
-    const int64_t G = p.G;
-    const size_t nrec = (size_t)We * (size_t)G;
-    CK(s->xf.ensure((size_t)We * (p.L + 1) * sizeof(LinkXf)), "alloc link table");
-    CK(s->r0.ensure(nrec * 16), "alloc records");
-    CK(s->r1.ensure(nrec * 16), "alloc records");
-    CK(s->r2.ensure(nrec * 16), "alloc records");
-    CK(s->r3.ensure(nrec * 16), "alloc records");
-    CK(s->mask.ensure((size_t)We * p.mask_words * 4), "alloc masks");
-    CK(s->counts.ensure((size_t)We * p.T * 4), "alloc counts");
-    CK(s->off.ensure((size_t)We * p.T * 4), "alloc offsets");
-    CK(s->cursor.ensure((size_t)We * p.T * 4), "alloc cursors");
-    CK(s->env_total.ensure((size_t)We * 8), "alloc totals");
-    CK(s->env_base.ensure((size_t)(We + 1) * 8), "alloc bases");
-    if (s->debug) CK(s->dbg_hxy.ensure(nrec * 8), "alloc debug");
-    if ((size_t)(We + 1) > s->pinned_n) {
-        if (s->pinned) cudaFreeHost(s->pinned);
-        s->pinned = nullptr;
-        s->pinned_n = 0;
-        CK(cudaMallocHost((void**)&s->pinned, sizeof(unsigned long long) * (We + 1)), "alloc pinned");
-        s->pinned_n = (size_t)We + 1;
-    }
+// Launch one wave.  Eager (cap == 0): reads the wave's intersection totals back
+// (host sync), grows the key buffer and splits the wave into sub-waves that
+// fit the budget.  Planned (cap > 0): no host sync; keys beyond cap are dropped
+// and flagged in the status word.
+gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& io, int tw, int th, int chunk,
+                   unsigned long long cap, cudaStream_t st, bool timers, int64_t* launches,
+                   unsigned long long* total_out) {
+    const int We = wt.We;
+    CK(sc.xf.ensure(sizeof(LinkXf) * (size_t)std::max(wt.xf_items, 1)), "alloc link table");
+    CK(sc.r0.ensure(wt.recs * 16), "alloc records");
+    CK(sc.r1.ensure(wt.recs * 16), "alloc records");
+    CK(sc.r2.ensure(wt.recs * 16), "alloc records");
+    CK(sc.r3.ensure(wt.recs * 16), "alloc records");
+    CK(sc.mask.ensure(wt.words * 4), "alloc masks");
+    CK(sc.counts.ensure(wt.tiles * 4), "alloc counts");
+    CK(sc.off.ensure(wt.tiles * 4), "alloc offsets");
+    CK(sc.cursor.ensure(wt.tiles * 4), "alloc cursors");
+    CK(sc.env_total.ensure((size_t)We * 8), "alloc totals");
+    CK(sc.env_base.ensure(((size_t)We + 1) * 8), "alloc bases");
+    CK(sc.work.ensure(16), "alloc work counter");
+    const bool debug = s->debug && cap == 0;
+    if (debug) CK(sc.dbg_hxy.ensure(wt.recs * 8), "alloc debug");
 
     // A1: link composition
-    PhaseTimer t1(s, st, GS_PHASE_LINK);
-    CK(launch_link_table(poses_dev, cams_dev, We, p.L, s->xf.as<LinkXf>(), s->status, st), "link table");
+    PhaseTimer t1(s, st, GS_PHASE_LINK, timers);
+    CK(launch_link_table(io.poses, wt.cams, wt.envs, We, wt.xf_items, sc.xf.as<LinkXf>(), s->status, st),
+       "link table");
     t1.done(1);
     ++*launches;
     // A2: projection
     ProjParams P{};
-    P.G = G;
+    P.n_gauss = s->D.n;
     P.p0 = s->D.p0;
     P.p1 = s->D.p1;
     P.p2 = s->D.p2;
     P.p3 = s->D.p3;
     P.sh = s->D.sh;
-    P.xf = s->xf.as<LinkXf>();
-    P.cams = cams_dev;
-    P.L1 = p.L + 1;
-    P.We = We;
-    P.r0 = s->r0.as<float4>();
-    P.r1 = s->r1.as<float4>();
-    P.r2 = s->r2.as<float4>();
-    P.r3 = s->r3.as<uint4>();
-    P.mask = s->mask.as<uint32_t>();
-    P.mask_words = p.mask_words;
-    P.dbg_hxy = s->debug ? s->dbg_hxy.as<float2>() : nullptr;
-    const unsigned gx = (unsigned)((G + 255) / 256);
-    int gy = (int)((4864 + gx - 1) / gx);
-    if (gy < 1) gy = 1;
-    if (gy > We) gy = We;
-    P.env_group = (We + gy - 1) / gy;
-    gy = (We + P.env_group - 1) / P.env_group;
-    PhaseTimer t2(s, st, GS_PHASE_PROJECT);
-    CK(launch_project(s->D, P, dim3(gx, (unsigned)gy), st), "projection");
+    P.blocks = wt.blocks;
+    P.envs = wt.envs;
+    P.cams = wt.cams;
+    P.xf = sc.xf.as<LinkXf>();
+    P.r0 = sc.r0.as<float4>();
+    P.r1 = sc.r1.as<float4>();
+    P.r2 = sc.r2.as<float4>();
+    P.r3 = sc.r3.as<uint4>();
+    P.mask = sc.mask.as<uint32_t>();
+    P.dbg_hxy = debug ? sc.dbg_hxy.as<float2>() : nullptr;
+    PhaseTimer t2(s, st, GS_PHASE_PROJECT, timers);
+    CK(launch_project(s->D, P, wt.n_blocks, st), "projection");
     t2.done(1);
     ++*launches;
     // A3: counts + scan
-    CK(cudaMemsetAsync(s->counts.p, 0, (size_t)We * p.T * 4, st), "memset counts");
+    CK(cudaMemsetAsync(sc.counts.p, 0, wt.tiles * 4, st), "memset counts");
     BinParams B{};
-    B.G = G;
-    B.mask_words = p.mask_words;
-    B.mask = s->mask.as<uint32_t>();
-    B.r3 = s->r3.as<uint4>();
+    B.envs = wt.envs;
+    B.mask = P.mask;
+    B.r3 = P.r3;
     B.e_begin = 0;
-    B.tile_w = s->tile_w;
-    B.tile_h = s->tile_h;
-    B.ntx = p.ntx;
-    B.T = p.T;
-    B.counts = s->counts.as<uint32_t>();
-    B.off_local = s->off.as<uint32_t>();
-    B.env_base = s->env_base.as<unsigned long long>();
-    B.cursor = s->cursor.as<uint32_t>();
-    B.words_per_block = 256;  // 8 warps x 32 mask words (8192 Gaussians)
-    const size_t smem1 = (size_t)p.T * 4, smem2 = (size_t)p.T * 8;
-    PhaseTimer t3(s, st, GS_PHASE_COUNT);
-    CK(launch_count(B, We, st, smem1), "count");
+    B.tile_w = tw;
+    B.tile_h = th;
+    B.words_per_block = kWordsPerBlock;
+    B.counts = sc.counts.as<uint32_t>();
+    B.off_local = sc.off.as<uint32_t>();
+    B.env_base = sc.env_base.as<unsigned long long>();
+    B.cursor = sc.cursor.as<uint32_t>();
+    B.status = s->status;
+    PhaseTimer t3(s, st, GS_PHASE_COUNT, timers);
+    CK(launch_count(B, We, wt.max_words, wt.max_T, st), "count");
     t3.done(1);
     ++*launches;
-    PhaseTimer t4(s, st, GS_PHASE_SCAN);
-    CK(launch_scan(s->counts.as<uint32_t>(), s->off.as<uint32_t>(), s->env_total.as<unsigned long long>(),
-                   s->env_base.as<unsigned long long>(), We, p.T, st),
+    PhaseTimer t4(s, st, GS_PHASE_SCAN, timers);
+    CK(launch_scan(wt.envs, sc.counts.as<uint32_t>(), sc.off.as<uint32_t>(), sc.env_total.as<unsigned long long>(),
+                   sc.env_base.as<unsigned long long>(), We, st),
        "scan");
     t4.done(2);
     *launches += 2;
-    CK(cudaMemcpyAsync(s->pinned, s->env_base.p, sizeof(unsigned long long) * (We + 1), cudaMemcpyDeviceToHost, st),
-       "read totals");
-    CK(cudaStreamSynchronize(st), "sync totals");
-    const unsigned long long* eb = s->pinned;
-    s->stats.intersections += (int64_t)eb[We];
-    CK(cudaMemsetAsync(s->cursor.p, 0, (size_t)We * p.T * 4, st), "memset cursors");
+    CK(cudaMemsetAsync(sc.cursor.p, 0, wt.tiles * 4, st), "memset cursors");
 
-    // A4 + A5 per sub-wave of envs whose intersection lists fit the budget
-    const double fixed = (double)p.per_env * We;
-    double cap_d = (double)s->budget - fixed;
-    if (cap_d < (double)s->budget * 0.25) cap_d = (double)s->budget * 0.25;
-    const size_t key_bytes = s->debug ? 16 : 8;
-    const unsigned long long cap_keys = (unsigned long long)(cap_d / key_bytes);
+    // sub-waves of envs whose keys fit (eager), or the whole wave (planned)
+    std::vector<unsigned long long> ebv;
+    const unsigned long long* eb = nullptr;
+    unsigned long long cap_keys = cap;
+    if (cap == 0) {
+        if ((size_t)(We + 1) > s->pinned_n) {
+            if (s->pinned) cudaFreeHost(s->pinned);
+            s->pinned = nullptr;
+            s->pinned_n = 0;
+            CK(cudaMallocHost((void**)&s->pinned, sizeof(unsigned long long) * (We + 1)), "alloc pinned");
+            s->pinned_n = (size_t)We + 1;
+        }
+        CK(cudaMemcpyAsync(s->pinned, sc.env_base.p, sizeof(unsigned long long) * (We + 1), cudaMemcpyDeviceToHost,
+                           st),
+           "read totals");
+        CK(cudaStreamSynchronize(st), "sync totals");
+        eb = s->pinned;
+        if (total_out) *total_out = eb[We];
+        s->stats.intersections += (int64_t)eb[We];
+        double cap_d = (double)s->budget * 0.4;
+        const size_t key_bytes = debug ? 16 : 8;
+        cap_keys = (unsigned long long)(cap_d / key_bytes);
+    } else {
+        ebv.assign(2, 0);
+        ebv[1] = cap;
+    }
     int ea = 0;
     while (ea < We) {
-        int ebd = ea + 1;
-        if (eb[ebd] - eb[ea] > cap_keys)
-            return fail(GS_ERR_OOM, "environment %d has %llu intersections, beyond the scratch budget", e0 + ea,
-                        (unsigned long long)(eb[ebd] - eb[ea]));
-        while (ebd < We && eb[ebd + 1] - eb[ea] <= cap_keys) ++ebd;
-        const unsigned long long npairs = eb[ebd] - eb[ea];
-        size_t want = (size_t)(npairs > 0 ? npairs : 1) * 8;
-        if (want > s->pairs.bytes) {
-            size_t grow = want + want / 4;
-            if (grow > (size_t)cap_keys * 8) grow = want;
-            CK(cudaStreamSynchronize(st), "sync before growth");
-            CK(s->pairs.ensure(grow), "alloc intersection keys");
+        int ebd = We;
+        unsigned long long npairs = cap;
+        unsigned long long base = 0;
+        if (cap == 0) {
+            ebd = ea + 1;
+            if (eb[ebd] - eb[ea] > cap_keys)
+                return fail(GS_ERR_OOM, "environment %d has %llu intersections, beyond the scratch budget", ea,
+                            (unsigned long long)(eb[ebd] - eb[ea]));
+            while (ebd < We && eb[ebd + 1] - eb[ea] <= cap_keys) ++ebd;
+            npairs = eb[ebd] - eb[ea];
+            base = eb[ea];
+            const size_t want = (size_t)(npairs > 0 ? npairs : 1) * 8;
+            if (want > sc.pairs.bytes) {
+                size_t grow = want + want / 4;
+                if (grow > (size_t)cap_keys * 8) grow = want;
+                CK(cudaStreamSynchronize(st), "sync before growth");
+                CK(sc.pairs.ensure(grow), "alloc intersection keys");
+            }
+            if (debug) CK(sc.dbg_sorted.ensure(sc.pairs.bytes), "alloc debug lists");
+        } else {
+            CK(sc.pairs.ensure((size_t)cap * 8), "alloc intersection keys");
         }
-        if (s->debug) CK(s->dbg_sorted.ensure(s->pairs.bytes), "alloc debug lists");
         B.e_begin = ea;
-        B.pair_base = eb[ea];
-        B.pairs = s->pairs.as<unsigned long long>();
-        PhaseTimer t5(s, st, GS_PHASE_SCATTER);
-        CK(launch_scatter(B, ebd - ea, st, smem2), "scatter");
+        B.pair_base = base;
+        B.pair_cap = cap == 0 ? (unsigned long long)(sc.pairs.bytes / 8) : cap;
+        B.pairs = sc.pairs.as<unsigned long long>();
+        PhaseTimer t5(s, st, GS_PHASE_SCATTER, timers);
+        CK(launch_scatter(B, ebd - ea, wt.max_words, wt.max_T, st), "scatter");
         t5.done(1);
         ++*launches;
         CompParams C{};
-        C.G = G;
-        C.r0 = s->r0.as<float4>();
-        C.r1 = s->r1.as<float4>();
-        C.r2 = s->r2.as<float4>();
-        C.counts = s->counts.as<uint32_t>();
-        C.off_local = s->off.as<uint32_t>();
-        C.env_base = s->env_base.as<unsigned long long>();
-        C.pair_base = eb[ea];
-        C.pairs = s->pairs.as<unsigned long long>();
-        C.dbg_sorted = s->debug ? s->dbg_sorted.as<unsigned long long>() : nullptr;
+        C.envs = wt.envs;
         C.e_begin = ea;
-        C.W = p.W;
-        C.H = p.H;
-        C.tile_w = s->tile_w;
-        C.tile_h = s->tile_h;
-        C.ntx = p.ntx;
-        C.T = p.T;
-        C.rgb = rgb;
-        C.depth = depth;
-        C.alpha = alpha;
+        C.e_end = ebd;
+        C.item_begin = wt.host_envs[ea].tile_base;
+        C.item_end = wt.host_envs[ebd].tile_base;
+        C.chunk = chunk;
+        C.work = sc.work.as<unsigned int>();
+        C.r0 = P.r0;
+        C.r1 = P.r1;
+        C.r2 = P.r2;
+        C.counts = sc.counts.as<uint32_t>();
+        C.off_local = sc.off.as<uint32_t>();
+        C.env_base = sc.env_base.as<unsigned long long>();
+        C.pair_base = base;
+        C.pair_cap = B.pair_cap;
+        C.pairs = B.pairs;
+        C.dbg_sorted = debug ? sc.dbg_sorted.as<unsigned long long>() : nullptr;
+        C.neval = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() : nullptr;
+        C.tile_w = tw;
+        C.tile_h = th;
+        C.rgb = io.rgb;
+        C.depth = io.depth;
+        C.alpha = io.alpha;
         C.status = s->status;
-        C.neval = s->counters ? s->neval.as<unsigned long long>() : nullptr;
-        PhaseTimer t6(s, st, GS_PHASE_COMPOSITE);
-        CK(launch_composite(C, ebd - ea, st), "composite");
+        CK(cudaMemsetAsync(sc.work.p, 0, 4, st), "memset work counter");
+        int ctas = 0;
+        PhaseTimer t6(s, st, GS_PHASE_COMPOSITE, timers);
+        CK(launch_composite(C, st, &ctas), "composite");
         t6.done(1);
         ++*launches;
-        s->last_ea = ea;
-        s->last_eb = ebd;
-        s->last_pair_base = eb[ea];
-        s->last_pairs = (int64_t)npairs;
+        if (cap == 0) {
+            s->last_ea = ea;
+            s->last_eb = ebd;
+            s->last_pair_base = base;
+        }
         ea = ebd;
     }
-    s->last_e0 = e0;
-    s->last_We = We;
-    s->last_W = p.W;
-    s->last_H = p.H;
-    s->last_T = p.T;
     return GS_OK;
 }
 
-gs_status render_common(gs_scene s, int E, const float* link_poses, const gs_camera* cams, float* rgb, float* depth,
-                        float* alpha, void* stream, bool host_mode) {
-    if (!s) return fail(GS_ERR_INVALID, "null scene");
-    if (E < 0) return fail(GS_ERR_INVALID, "negative n_envs");
-    if (E == 0) return GS_OK;
-    if (!cams) return fail(GS_ERR_INVALID, "null cams");
-    if (!rgb || !depth) return fail(GS_ERR_INVALID, "null rgb or depth output");
-    if (s->D.n_links > 0 && !link_poses) return fail(GS_ERR_INVALID, "null link_poses with %d links", s->D.n_links);
-    int W = 0, H = 0;
-    gs_status vs = check_cams(cams, E, &W, &H);
-    if (vs != GS_OK) return vs;
-    Plan p{};
-    vs = make_plan(s, E, W, H, host_mode, &p);
-    if (vs != GS_OK) return vs;
+// ------------------------------------------------------------------ eager renders
+
+enum class Out { Device, Host };
+
+gs_status render_specs(gs_scene s, const std::vector<EnvSpec>& specs, const float* poses_dev, float* rgb,
+                       float* depth, float* alpha, cudaStream_t st, Out mode, int64_t pix_per_env_host) {
+    const int tw = s->tile_w, th = s->tile_h;
+    ST(check_specs(s, specs, tw, th));
     CK(cudaSetDevice(s->device), "set device");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     s->stats.waves = 0;
     s->stats.kernel_launches = 0;
     s->stats.intersections = 0;
-    const size_t px = (size_t)W * H;
-    if (p.G == 0) {
-        // no Gaussians: black, transparent, depth 0
-        if (host_mode) {
-            memset(rgb, 0, (size_t)E * px * 12);
-            memset(depth, 0, (size_t)E * px * 4);
-            if (alpha) memset(alpha, 0, (size_t)E * px * 4);
-        } else {
-            CK(cudaMemsetAsync(rgb, 0, (size_t)E * px * 12, st), "clear rgb");
-            CK(cudaMemsetAsync(depth, 0, (size_t)E * px * 4, st), "clear depth");
-            if (alpha) CK(cudaMemsetAsync(alpha, 0, (size_t)E * px * 4, st), "clear alpha");
-        }
-        return GS_OK;
-    }
-    CK(s->cams.ensure((size_t)E * sizeof(gs_camera)), "alloc cams");
-    CK(cudaMemcpyAsync(s->cams.p, cams, (size_t)E * sizeof(gs_camera), cudaMemcpyHostToDevice, st), "copy cams");
-    const gs_camera* cams_dev = s->cams.as<gs_camera>();
-    const float* poses_dev = link_poses;
-    const size_t pose_floats = (size_t)p.L * 7;
-    if (host_mode && p.L > 0) {
-        CK(s->poses.ensure((size_t)E * pose_floats * 4), "alloc poses");
-        CK(cudaMemcpyAsync(s->poses.p, link_poses, (size_t)E * pose_floats * 4, cudaMemcpyHostToDevice, st),
-           "copy poses");
-        poses_dev = s->poses.as<float>();
-    }
+    const int E = (int)specs.size();
+    size_t extra = 0;
+    if (mode == Out::Host) extra = (size_t)pix_per_env_host * 20 * 2;
+    std::vector<std::pair<int, int>> waves;
+    ST(plan_waves(s, specs, tw, th, s->debug != 0, s->max_wave, extra, &waves));
     int64_t launches = 0;
-    if (!host_mode) {
-        for (int e0 = 0; e0 < E; e0 += p.We) {
-            const int We = E - e0 < p.We ? E - e0 : p.We;
-            gs_status r = render_wave(s, p, e0, We, poses_dev ? poses_dev + (size_t)e0 * pose_floats : nullptr,
-                                      cams_dev + e0, rgb + (size_t)e0 * px * 3, depth + (size_t)e0 * px,
-                                      alpha ? alpha + (size_t)e0 * px : nullptr, st, &launches);
-            if (r != GS_OK) return r;
+    if (mode == Out::Device) {
+        for (auto& w : waves) {
+            WaveTables wt{};
+            ST(upload_tables(s, specs, w.first, w.second, tw, th, 0, s->sc.envs, s->sc.blocks, s->sc.cams, st, false,
+                             &wt));
+            s->last_envs.assign(wt.host_envs, wt.host_envs + wt.We + 1);
+            ST(run_wave(s, s->sc, wt, WaveIO{poses_dev, rgb, depth, alpha, 0}, tw, th, 1, 0, st, true, &launches,
+                        nullptr));
+            s->last_e0 = w.first;
+            s->last_We = wt.We;
             s->stats.waves++;
         }
     } else {
+        // host buffers: wave outputs in device staging, copied out on a second
+        // stream while the next wave renders
         if (!s->copy_stream) CK(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking), "copy stream");
+        int maxw = 0;
+        for (auto& w : waves) maxw = std::max(maxw, w.second - w.first);
+        const size_t px = (size_t)pix_per_env_host;
         for (int k = 0; k < 2; ++k) {
             if (!s->ev_done[k]) CK(cudaEventCreateWithFlags(&s->ev_done[k], cudaEventDisableTiming), "event");
             if (!s->ev_copied[k]) CK(cudaEventCreateWithFlags(&s->ev_copied[k], cudaEventDisableTiming), "event");
-            CK(s->stage_rgb[k].ensure((size_t)p.We * px * 12), "alloc staging");
-            CK(s->stage_depth[k].ensure((size_t)p.We * px * 4), "alloc staging");
-            if (alpha) CK(s->stage_alpha[k].ensure((size_t)p.We * px * 4), "alloc staging");
+            CK(s->stage_rgb[k].ensure((size_t)maxw * px * 12), "alloc staging");
+            CK(s->stage_depth[k].ensure((size_t)maxw * px * 4), "alloc staging");
+            if (alpha) CK(s->stage_alpha[k].ensure((size_t)maxw * px * 4), "alloc staging");
         }
         int wave = 0;
-        for (int e0 = 0; e0 < E; e0 += p.We, ++wave) {
-            const int We = E - e0 < p.We ? E - e0 : p.We;
+        for (auto& w : waves) {
             const int k = wave & 1;
+            const int We = w.second - w.first;
+            const long long rebase = specs[w.first].pixel_offset;
             if (wave >= 2) CK(cudaStreamWaitEvent(st, s->ev_copied[k], 0), "wait copy");
-            gs_status r = render_wave(s, p, e0, We, poses_dev ? poses_dev + (size_t)e0 * pose_floats : nullptr,
-                                      cams_dev + e0, s->stage_rgb[k].as<float>(), s->stage_depth[k].as<float>(),
-                                      alpha ? s->stage_alpha[k].as<float>() : nullptr, st, &launches);
-            if (r != GS_OK) return r;
+            WaveTables wt{};
+            ST(upload_tables(s, specs, w.first, w.second, tw, th, rebase, s->sc.envs, s->sc.blocks, s->sc.cams, st,
+                             false, &wt));
+            s->last_envs.assign(wt.host_envs, wt.host_envs + wt.We + 1);
+            ST(run_wave(s, s->sc, wt,
+                        WaveIO{poses_dev, s->stage_rgb[k].as<float>(), s->stage_depth[k].as<float>(),
+                               alpha ? s->stage_alpha[k].as<float>() : nullptr, rebase},
+                        tw, th, 1, 0, st, true, &launches, nullptr));
+            s->last_e0 = w.first;
+            s->last_We = We;
             CK(cudaEventRecord(s->ev_done[k], st), "record");
             CK(cudaStreamWaitEvent(s->copy_stream, s->ev_done[k], 0), "wait render");
-            CK(cudaMemcpyAsync(rgb + (size_t)e0 * px * 3, s->stage_rgb[k].p, (size_t)We * px * 12,
+            CK(cudaMemcpyAsync(rgb + (size_t)rebase * 3, s->stage_rgb[k].p, (size_t)We * px * 12,
                                cudaMemcpyDeviceToHost, s->copy_stream),
                "copy rgb out");
-            CK(cudaMemcpyAsync(depth + (size_t)e0 * px, s->stage_depth[k].p, (size_t)We * px * 4,
-                               cudaMemcpyDeviceToHost, s->copy_stream),
+            CK(cudaMemcpyAsync(depth + rebase, s->stage_depth[k].p, (size_t)We * px * 4, cudaMemcpyDeviceToHost,
+                               s->copy_stream),
                "copy depth out");
             if (alpha)
-                CK(cudaMemcpyAsync(alpha + (size_t)e0 * px, s->stage_alpha[k].p, (size_t)We * px * 4,
-                                   cudaMemcpyDeviceToHost, s->copy_stream),
+                CK(cudaMemcpyAsync(alpha + rebase, s->stage_alpha[k].p, (size_t)We * px * 4, cudaMemcpyDeviceToHost,
+                                   s->copy_stream),
                    "copy alpha out");
             CK(cudaEventRecord(s->ev_copied[k], s->copy_stream), "record");
             s->stats.waves++;
+            ++wave;
         }
         CK(cudaStreamSynchronize(s->copy_stream), "sync copies");
         CK(cudaStreamSynchronize(st), "sync render");
     }
     s->stats.kernel_launches = launches;
+    (void)E;
+    return GS_OK;
+}
+
+gs_status clear_outputs(float* rgb, float* depth, float* alpha, size_t px, cudaStream_t st, bool host) {
+    if (host) {
+        memset(rgb, 0, px * 12);
+        memset(depth, 0, px * 4);
+        if (alpha) memset(alpha, 0, px * 4);
+        return GS_OK;
+    }
+    CK(cudaMemsetAsync(rgb, 0, px * 12, st), "clear rgb");
+    CK(cudaMemsetAsync(depth, 0, px * 4, st), "clear depth");
+    if (alpha) CK(cudaMemsetAsync(alpha, 0, px * 4, st), "clear alpha");
+    return GS_OK;
+}
+
+gs_status render_uniform(gs_scene s, int E, const float* link_poses, const gs_camera* cams, float* rgb, float* depth,
+                         float* alpha, void* stream, bool host_mode) {
+    if (!s) return fail(GS_ERR_INVALID, "null scene");
+    if (E < 0) return fail(GS_ERR_INVALID, "negative n_envs");
+    if (E == 0) return GS_OK;
+    if (!cams) return fail(GS_ERR_INVALID, "null cams");
+    if (!rgb || !depth) return fail(GS_ERR_INVALID, "null rgb or depth output");
+    const int L = s->D.n_links;
+    if (L > 0 && !link_poses) return fail(GS_ERR_INVALID, "null link_poses with %d links", L);
+    const int W = cams[0].width, H = cams[0].height;
+    for (int e = 0; e < E; ++e) {
+        if (cams[e].width != W || cams[e].height != H)
+            return fail(GS_ERR_INVALID, "camera %d: resolution %dx%d differs from camera 0 (%dx%d)", e,
+                        cams[e].width, cams[e].height, W, H);
+        ST(check_cam(cams[e], e));
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(s->device), "set device");
+    const long long px = (long long)W * H;
+    if (s->D.n == 0) return clear_outputs(rgb, depth, alpha, (size_t)E * px, st, host_mode);
+    std::vector<EnvSpec> specs((size_t)E);
+    for (int e = 0; e < E; ++e) specs[e] = EnvSpec{cams + e, 0, L, (long long)e * L, (long long)e * px};
+    const float* poses_dev = link_poses;
+    if (host_mode && L > 0) {
+        CK(s->poses.ensure((size_t)E * L * 28), "alloc poses");
+        CK(cudaMemcpyAsync(s->poses.p, link_poses, (size_t)E * L * 28, cudaMemcpyHostToDevice, st), "copy poses");
+        poses_dev = s->poses.as<float>();
+    }
+    return render_specs(s, specs, poses_dev, rgb, depth, alpha, st, host_mode ? Out::Host : Out::Device, px);
+}
+
+gs_status specs_from_envs(gs_scene s, int n, const gs_env* envs, std::vector<EnvSpec>* specs) {
+    specs->resize((size_t)n);
+    for (int e = 0; e < n; ++e) {
+        const gs_env& v = envs[e];
+        (*specs)[e] = EnvSpec{&v.cam, v.link_begin, v.link_end, (long long)v.pose_offset, (long long)v.pixel_offset};
+    }
+    (void)s;
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------ plans
+
+gs_status plan_release_graph(gs_plan p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+    return GS_OK;
+}
+
+// Build the plan's per-wave tables for the current tile shape (uploaded once).
+gs_status plan_tables(gs_plan p, const std::vector<EnvSpec>& specs) {
+    gs_scene s = p->s;
+    std::vector<std::pair<int, int>> ranges;
+    ST(plan_waves(s, specs, p->tile_w, p->tile_h, false, s->max_wave, 0, &ranges));
+    std::vector<unsigned long long> caps;
+    for (auto& w : p->waves) caps.push_back(w.cap);
+    for (auto& w : p->waves) {
+        w.envs.release();
+        w.blocks.release();
+        w.cams.release();
+    }
+    p->waves.clear();
+    p->waves.resize(ranges.size());
+    for (size_t i = 0; i < ranges.size(); ++i) {
+        auto& w = p->waves[i];
+        w.e0 = ranges[i].first;
+        w.e1 = ranges[i].second;
+        WaveTables wt{};
+        ST(upload_tables(s, specs, w.e0, w.e1, p->tile_w, p->tile_h, 0, w.envs, w.blocks, w.cams, nullptr, true, &wt));
+        w.n_blocks = wt.n_blocks;
+        w.xf_items = wt.xf_items;
+        w.max_words = wt.max_words;
+        w.max_T = wt.max_T;
+        w.recs = wt.recs;
+        w.words = wt.words;
+        w.tiles = wt.tiles;
+        w.cap = i < caps.size() ? caps[i] : 0;
+    }
+    return GS_OK;
+}
+
+WaveTables plan_wave_tables(gs_plan p, size_t i, std::vector<EnvInfo>& host) {
+    auto& w = p->waves[i];
+    return WaveTables{w.envs.as<EnvInfo>(), w.blocks.as<ProjBlock>(), w.cams.as<gs_camera>(), w.e1 - w.e0,
+                      w.n_blocks, w.xf_items, w.max_words, w.max_T, w.recs, w.words, w.tiles, host.data()};
+}
+
+// Eager pass over all waves (host syncs); records each wave's key total.
+gs_status plan_eager(gs_plan p, const std::vector<EnvSpec>& specs, const float* poses, float* rgb, float* depth,
+                     float* alpha, cudaStream_t st, std::vector<unsigned long long>* totals) {
+    gs_scene s = p->s;
+    totals->clear();
+    int64_t launches = 0;
+    for (size_t i = 0; i < p->waves.size(); ++i) {
+        auto& w = p->waves[i];
+        std::vector<EnvInfo> host((size_t)(w.e1 - w.e0) + 1);
+        int nb = 0;
+        std::vector<ProjBlock> dummy(1);
+        build_wave_tables(s->D, s->link_offsets.data(), specs.data() + w.e0, w.e1 - w.e0, p->tile_w, p->tile_h, 0,
+                          host.data(), dummy.data(), &nb, 0);
+        WaveTables wt = plan_wave_tables(p, i, host);
+        unsigned long long tot = 0;
+        ST(run_wave(s, p->sc, wt, WaveIO{poses, rgb, depth, alpha, 0}, p->tile_w, p->tile_h, p->chunk, 0, st, false,
+                    &launches, &tot));
+        totals->push_back(tot);
+    }
+    return GS_OK;
+}
+
+// Enqueue all waves in planned mode (no host sync) on st.
+gs_status plan_enqueue(gs_plan p, const std::vector<EnvSpec>& specs, const float* poses, float* rgb, float* depth,
+                       float* alpha, cudaStream_t st) {
+    gs_scene s = p->s;
+    int64_t launches = 0;
+    for (size_t i = 0; i < p->waves.size(); ++i) {
+        auto& w = p->waves[i];
+        std::vector<EnvInfo> host((size_t)(w.e1 - w.e0) + 1);
+        int nb = 0;
+        std::vector<ProjBlock> dummy(1);
+        build_wave_tables(s->D, s->link_offsets.data(), specs.data() + w.e0, w.e1 - w.e0, p->tile_w, p->tile_h, 0,
+                          host.data(), dummy.data(), &nb, 0);
+        WaveTables wt = plan_wave_tables(p, i, host);
+        ST(run_wave(s, p->sc, wt, WaveIO{poses, rgb, depth, alpha, 0}, p->tile_w, p->tile_h, p->chunk, w.cap, st,
+                    false, &launches, nullptr));
+    }
     return GS_OK;
 }
 
 }  // namespace
 
-gsb::SceneView gsb::scene_view(gs_scene s) {
-    return SceneView{s->device, s->D, s->status, s->tile_w, s->tile_h};
-}
+gsb::SceneView gsb::scene_view(gs_scene s) { return SceneView{s->device, s->D, s->status, s->tile_w, s->tile_h}; }
 
 gs_status gsb::report(gs_status st, const char* msg) {
     g_err = msg;
@@ -561,7 +852,7 @@ extern "C" {
 
 const char* gs_last_error(void) { return g_err.c_str(); }
 
-const char* gs_version(void) { return "gsbatch 0.1 (sm_103a)"; }
+const char* gs_version(void) { return "gsbatch 0.2 (sm_103a)"; }
 
 gs_status gs_scene_create(const gs_gaussians* background, gs_scene* out) {
     if (!out) return fail(GS_ERR_INVALID, "null output handle");
@@ -583,7 +874,7 @@ gs_status gs_scene_create(const gs_gaussians* background, gs_scene* out) {
     s->D.dtype = background->dtype;
     s->D.sh_planes = sh_planes_for(s->D.sh_degree, s->D.dtype);
     s->have_format = background->n > 0;
-    gs_status r = alloc_gaussians(s, s->D.n, s->g0, s->g1, s->g2, s->g3, s->gsh, s->D.sh_planes);
+    gs_status r = alloc_gaussians(s->D.n, s->g0, s->g1, s->g2, s->g3, s->gsh, s->D.sh_planes);
     if (r == GS_OK) {
         s->D.p0 = s->g0.as<float4>();
         s->D.p1 = s->g1.as<float4>();
@@ -626,7 +917,7 @@ gs_status gs_scene_attach_links(gs_scene s, int n_links, const int64_t* link_off
     } else if (lg->n != 0) {
         return fail(GS_ERR_INVALID, "link Gaussians given with n_links = 0");
     }
-    if (s->D.n_bg + lg->n > 0xFFFFFFF0ll) return fail(GS_ERR_UNSUPPORTED, "more than 2^32-16 Gaussians in total");
+    if (s->D.n_bg + lg->n > 0x7FFFFFF0ll) return fail(GS_ERR_UNSUPPORTED, "more than 2^31-16 Gaussians in total");
     if (lg->n > 0) {
         if (s->have_format && (lg->dtype != s->D.dtype || lg->sh_degree != s->D.sh_degree))
             return fail(GS_ERR_INVALID, "link Gaussians must use the background's dtype and sh_degree");
@@ -641,7 +932,7 @@ gs_status gs_scene_attach_links(gs_scene s, int n_links, const int64_t* link_off
     N.n = s->D.n_bg + lg->n;
     N.n_links = n_links;
     DevBuf a, b, c, d, sh;
-    gs_status r = alloc_gaussians(s, N.n, a, b, c, d, sh, N.sh_planes);
+    gs_status r = alloc_gaussians(N.n, a, b, c, d, sh, N.sh_planes);
     if (r != GS_OK) {
         a.release(); b.release(); c.release(); d.release(); sh.release();
         return r;
@@ -676,6 +967,8 @@ gs_status gs_scene_attach_links(gs_scene s, int n_links, const int64_t* link_off
     }
     s->g0.release(); s->g1.release(); s->g2.release(); s->g3.release(); s->gsh.release();
     s->g0 = a; s->g1 = b; s->g2 = c; s->g3 = d; s->gsh = sh;
+    s->link_offsets.assign(link_offsets ? link_offsets : nullptr, link_offsets ? link_offsets + n_links + 1 : nullptr);
+    if (s->link_offsets.empty()) s->link_offsets.assign(1, 0);
     if (lg->n > 0) s->have_format = true;
     s->stats.n_gaussians = s->D.n;
     return GS_OK;
@@ -683,18 +976,226 @@ gs_status gs_scene_attach_links(gs_scene s, int n_links, const int64_t* link_off
 
 gs_status gs_render_batch(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
                           float* depth, float* alpha, void* cuda_stream) {
-    return render_common(s, n_envs, link_poses, cams, rgb, depth, alpha, cuda_stream, false);
+    return render_uniform(s, n_envs, link_poses, cams, rgb, depth, alpha, cuda_stream, false);
 }
 
 gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
                                float* depth, float* alpha, void* cuda_stream) {
-    return render_common(s, n_envs, link_poses, cams, rgb, depth, alpha, cuda_stream, true);
+    return render_uniform(s, n_envs, link_poses, cams, rgb, depth, alpha, cuda_stream, true);
+}
+
+gs_status gs_render_batch_v(gs_scene s, int n_envs, const gs_env* envs, const float* link_poses, float* rgb,
+                            float* depth, float* alpha, void* cuda_stream) {
+    if (!s) return fail(GS_ERR_INVALID, "null scene");
+    if (n_envs < 0) return fail(GS_ERR_INVALID, "negative n_envs");
+    if (n_envs == 0) return GS_OK;
+    if (!envs || !rgb || !depth) return fail(GS_ERR_INVALID, "null envs, rgb or depth");
+    bool any_links = false;
+    for (int e = 0; e < n_envs; ++e) any_links |= envs[e].link_end > envs[e].link_begin;
+    if (any_links && !link_poses) return fail(GS_ERR_INVALID, "null link_poses");
+    std::vector<EnvSpec> specs;
+    ST(specs_from_envs(s, n_envs, envs, &specs));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    CK(cudaSetDevice(s->device), "set device");
+    if (s->D.n == 0) {
+        ST(check_specs(s, specs, s->tile_w, s->tile_h));
+        for (int e = 0; e < n_envs; ++e) {
+            const size_t px = (size_t)envs[e].cam.width * envs[e].cam.height;
+            ST(clear_outputs(rgb + envs[e].pixel_offset * 3, depth + envs[e].pixel_offset,
+                             alpha ? alpha + envs[e].pixel_offset : nullptr, px, st, false));
+        }
+        return GS_OK;
+    }
+    return render_specs(s, specs, link_poses, rgb, depth, alpha, st, Out::Device, 0);
+}
+
+gs_status gs_plan_create(gs_scene s, int n_envs, const gs_env* envs, int flags, gs_plan* out) {
+    if (!out) return fail(GS_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    if (!s) return fail(GS_ERR_INVALID, "null scene");
+    if (n_envs <= 0 || !envs) return fail(GS_ERR_INVALID, "a plan needs n_envs > 0 environments");
+    gs_plan p = new gs_plan_s();
+    p->s = s;
+    p->flags = flags;
+    p->envs.assign(envs, envs + n_envs);
+    p->tile_w = s->tile_w;
+    p->tile_h = s->tile_h;
+    std::vector<EnvSpec> specs;
+    specs_from_envs(s, n_envs, p->envs.data(), &specs);
+    gs_status r = check_specs(s, specs, 8, 8);
+    if (r == GS_OK) r = check_specs(s, specs, p->tile_w, p->tile_h);
+    if (r != GS_OK) {
+        delete p;
+        return r;
+    }
+    cudaSetDevice(s->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->pinned_status, 4);
+    if (e != cudaSuccess) {
+        gs_plan_destroy(p);
+        return cuda_fail(e, "plan create");
+    }
+    *p->pinned_status = 0;
+    *out = p;
+    return GS_OK;
+}
+
+gs_status gs_plan_launch(gs_plan p, const float* link_poses, float* rgb, float* depth, float* alpha,
+                         void* cuda_stream) {
+    if (!p) return fail(GS_ERR_INVALID, "null plan");
+    if (!rgb || !depth) return fail(GS_ERR_INVALID, "null rgb or depth");
+    gs_scene s = p->s;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    CK(cudaSetDevice(s->device), "set device");
+    std::vector<EnvSpec> specs;
+    specs_from_envs(s, (int)p->envs.size(), p->envs.data(), &specs);
+    bool any_links = false;
+    for (auto& v : p->envs) any_links |= v.link_end > v.link_begin;
+    if (any_links && !link_poses) return fail(GS_ERR_INVALID, "null link_poses");
+    if (s->D.n == 0) {
+        for (auto& v : p->envs)
+            ST(clear_outputs(rgb + v.pixel_offset * 3, depth + v.pixel_offset, alpha ? alpha + v.pixel_offset : nullptr,
+                             (size_t)v.cam.width * v.cam.height, st, false));
+        return GS_OK;
+    }
+    // a previous planned launch that overflowed its key capacity: regrow and re-plan
+    if (p->tuned && p->launched && cudaEventQuery(p->done) == cudaSuccess && (*p->pinned_status & kStOverflow)) {
+        // re-measure with the current poses (an eager, host-synchronising pass)
+        *p->pinned_status = 0;
+        CK(cudaMemsetAsync(s->status, 0, 4, st), "status clear");
+        std::vector<unsigned long long> tot;
+        ST(plan_eager(p, specs, link_poses, rgb, depth, alpha, st, &tot));
+        for (size_t i = 0; i < p->waves.size() && i < tot.size(); ++i)
+            p->waves[i].cap = std::max(p->waves[i].cap, tot[i] + tot[i] / 4 + 4096);
+        plan_release_graph(p);
+        p->regrows++;
+    }
+    if (!p->tuned) {
+        // eager warm-up: autotune (tile shape x claim size) and size the key capacity
+        struct Cand {
+            int tw, th, chunk;
+        };
+        std::vector<Cand> cands;
+        if (p->flags & GS_PLAN_AUTOTUNE) {
+            const int shapes[4][2] = {{16, 16}, {32, 8}, {16, 8}, {8, 8}};
+            for (auto& sh : shapes)
+                for (int ch : {1, 4}) cands.push_back({sh[0], sh[1], ch});
+        } else {
+            cands.push_back({p->tile_w, p->tile_h, 1});
+        }
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a), "event");
+        CK(cudaEventCreate(&b), "event");
+        double best = 1e30;
+        Cand bestc = cands[0];
+        std::vector<unsigned long long> best_tot;
+        for (const Cand& c : cands) {
+            if (check_specs(s, specs, c.tw, c.th) != GS_OK) continue;
+            p->tile_w = c.tw;
+            p->tile_h = c.th;
+            p->chunk = c.chunk;
+            ST(plan_tables(p, specs));
+            std::vector<unsigned long long> tot;
+            ST(plan_eager(p, specs, link_poses, rgb, depth, alpha, st, &tot));  // warm (sizes buffers)
+            CK(cudaEventRecord(a, st), "record");
+            ST(plan_eager(p, specs, link_poses, rgb, depth, alpha, st, &tot));
+            CK(cudaEventRecord(b, st), "record");
+            CK(cudaEventSynchronize(b), "sync");
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, a, b), "elapsed");
+            if (ms < best) {
+                best = ms;
+                bestc = c;
+                best_tot = tot;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        p->tile_w = bestc.tw;
+        p->tile_h = bestc.th;
+        p->chunk = bestc.chunk;
+        p->tuned_candidates = (int)cands.size();
+        p->tuned_ms = best;
+        ST(plan_tables(p, specs));
+        for (size_t i = 0; i < p->waves.size(); ++i) {
+            const unsigned long long t = i < best_tot.size() ? best_tot[i] : 0;
+            p->waves[i].cap = t + t / 4 + 4096;  // headroom for pose-dependent growth
+        }
+        p->sc.pairs.release();
+        p->tuned = true;
+        plan_release_graph(p);
+    }
+    const void* ptrs[4] = {link_poses, rgb, depth, alpha};
+    const bool same = memcmp(ptrs, p->cap_ptrs, sizeof ptrs) == 0;
+    if (!(p->flags & GS_PLAN_GRAPH)) {
+        ST(plan_enqueue(p, specs, link_poses, rgb, depth, alpha, st));
+        CK(cudaMemcpyAsync(p->pinned_status, s->status, 4, cudaMemcpyDeviceToHost, st), "status copy");
+    } else {
+        if (!p->exec || !same) {
+            plan_release_graph(p);
+            // grow every buffer the graph will reference before capturing it
+            ST(plan_enqueue(p, specs, link_poses, rgb, depth, alpha, st));
+            CK(cudaStreamSynchronize(st), "sync");
+            CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            gs_status r = plan_enqueue(p, specs, link_poses, rgb, depth, alpha, p->cap_stream);
+            cudaError_t ce = cudaMemcpyAsync(p->pinned_status, s->status, 4, cudaMemcpyDeviceToHost, p->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t ee = cudaStreamEndCapture(p->cap_stream, &g);
+            if (r != GS_OK) {
+                if (g) cudaGraphDestroy(g);
+                return r;
+            }
+            CK(ce, "status copy");
+            CK(ee, "end capture");
+            p->graph = g;
+            CK(cudaGraphInstantiate(&p->exec, g, 0), "instantiate graph");
+            memcpy(p->cap_ptrs, ptrs, sizeof ptrs);
+        }
+        CK(cudaGraphLaunch(p->exec, st), "graph launch");
+    }
+    CK(cudaEventRecord(p->done, st), "record");
+    p->launched = true;
+    return GS_OK;
+}
+
+gs_status gs_plan_get_info(gs_plan p, gs_plan_info* out) {
+    if (!p || !out) return fail(GS_ERR_INVALID, "null argument");
+    gs_plan_info i{};
+    i.tile_w = p->tile_w;
+    i.tile_h = p->tile_h;
+    i.chunk = p->chunk;
+    i.waves = (int)p->waves.size();
+    i.graph = p->exec != nullptr;
+    i.tuned_candidates = p->tuned_candidates;
+    i.tuned_ms = p->tuned_ms;
+    i.regrows = p->regrows;
+    for (auto& w : p->waves) i.key_capacity += (int64_t)w.cap;
+    i.scratch_bytes = p->sc.bytes();
+    *out = i;
+    return GS_OK;
+}
+
+void gs_plan_destroy(gs_plan p) {
+    if (!p) return;
+    if (p->s) cudaSetDevice(p->s->device);
+    cudaDeviceSynchronize();
+    plan_release_graph(p);
+    for (auto& w : p->waves) {
+        w.envs.release();
+        w.blocks.release();
+        w.cams.release();
+    }
+    p->sc.release();
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->done) cudaEventDestroy(p->done);
+    if (p->pinned_status) cudaFreeHost(p->pinned_status);
+    delete p;
 }
 
 gs_status gs_scene_set_tile(gs_scene s, int tw, int th) {
     if (!s) return fail(GS_ERR_INVALID, "null scene");
-    const bool ok = (tw == 8 && th == 8) || (tw == 16 && th == 8) || (tw == 16 && th == 16) || (tw == 32 && th == 8);
-    if (!ok) return fail(GS_ERR_INVALID, "tile %dx%d not one of 8x8, 16x8, 16x16, 32x8", tw, th);
+    if (!valid_tile(tw, th)) return fail(GS_ERR_INVALID, "tile %dx%d not one of 8x8, 16x8, 16x16, 32x8", tw, th);
     s->tile_w = tw;
     s->tile_h = th;
     return GS_OK;
@@ -731,31 +1232,9 @@ gs_status gs_scene_sync_status(gs_scene s, void* cuda_stream) {
     std::string m = "device status:";
     if (st & kStBadPose) m += " zero or non-finite link pose;";
     if (st & kStBadScene) m += " bad Gaussian quaternion;";
-    if (st & kStOverflow) m += " capacity overflow;";
+    if (st & kStOverflow) m += " intersection keys beyond capacity (planned launch) or corrupted bucket;";
     g_err = m;
     return GS_ERR_DEVICE;
-}
-
-gs_status gs_scene_get_stats(gs_scene s, gs_stats* out) {
-    if (!s || !out) return fail(GS_ERR_INVALID, "null argument");
-    s->stats.n_gaussians = s->D.n;
-    int64_t bytes = 0;
-    const DevBuf* bufs[] = {&s->xf, &s->cams, &s->poses, &s->r0, &s->r1, &s->r2, &s->r3, &s->mask, &s->counts,
-                            &s->off, &s->cursor, &s->env_total, &s->env_base, &s->pairs, &s->dbg_hxy,
-                            &s->dbg_sorted, &s->stage_rgb[0], &s->stage_rgb[1], &s->stage_depth[0],
-                            &s->stage_depth[1], &s->stage_alpha[0], &s->stage_alpha[1]};
-    for (const DevBuf* b : bufs) bytes += (int64_t)b->bytes;
-    s->stats.scratch_bytes = bytes;
-    s->stats.composited = 0;
-    if (s->counters && s->neval.p) {
-        CK(cudaSetDevice(s->device), "set device");
-        CK(cudaDeviceSynchronize(), "sync");
-        unsigned long long c = 0;
-        CK(cudaMemcpy(&c, s->neval.p, 8, cudaMemcpyDeviceToHost), "read counter");
-        s->stats.composited = (int64_t)c;
-    }
-    *out = s->stats;
-    return GS_OK;
 }
 
 gs_status gs_scene_set_counters(gs_scene s, int enable) {
@@ -799,51 +1278,74 @@ gs_status gs_scene_get_timings(gs_scene s, gs_timings* out, int reset) {
     return GS_OK;
 }
 
+gs_status gs_scene_get_stats(gs_scene s, gs_stats* out) {
+    if (!s || !out) return fail(GS_ERR_INVALID, "null argument");
+    s->stats.n_gaussians = s->D.n;
+    int64_t bytes = s->sc.bytes();
+    const DevBuf* bufs[] = {&s->stage_rgb[0], &s->stage_rgb[1], &s->stage_depth[0], &s->stage_depth[1],
+                            &s->stage_alpha[0], &s->stage_alpha[1], &s->poses};
+    for (const DevBuf* b : bufs) bytes += (int64_t)b->bytes;
+    s->stats.scratch_bytes = bytes;
+    s->stats.composited = 0;
+    if (s->counters && s->neval.p) {
+        CK(cudaSetDevice(s->device), "set device");
+        CK(cudaDeviceSynchronize(), "sync");
+        unsigned long long c = 0;
+        CK(cudaMemcpy(&c, s->neval.p, 8, cudaMemcpyDeviceToHost), "read counter");
+        s->stats.composited = (int64_t)c;
+    }
+    *out = s->stats;
+    return GS_OK;
+}
+
 gs_status gs_debug_copy_records(gs_scene s, int env, uint8_t* visible, float* u, float* v, float* hx, float* hy,
                                 float* z, float* opacity, float* conic, float* rgb, int32_t* range) {
     if (!s) return fail(GS_ERR_INVALID, "null scene");
     if (s->last_e0 < 0 || env < s->last_e0 || env >= s->last_e0 + s->last_We)
         return fail(GS_ERR_INVALID, "env %d is not in the last wave rendered", env);
-    if (!s->debug || !s->dbg_hxy.p) return fail(GS_ERR_INVALID, "debug was not enabled for the last render");
+    if (!s->debug || !s->sc.dbg_hxy.p) return fail(GS_ERR_INVALID, "debug was not enabled for the last render");
     CK(cudaSetDevice(s->device), "set device");
     CK(cudaDeviceSynchronize(), "sync");
-    const int el = env - s->last_e0;
-    const int64_t G = s->D.n;
-    const size_t base = (size_t)el * G;
-    std::vector<uint32_t> mask((G + 31) / 32);
-    std::vector<float4> a(G), b(G), c(G);
-    std::vector<float2> h(G);
-    CK(cudaMemcpy(mask.data(), s->mask.as<uint32_t>() + (size_t)el * mask.size(), mask.size() * 4,
-                  cudaMemcpyDeviceToHost), "copy");
-    CK(cudaMemcpy(a.data(), s->r0.as<float4>() + base, G * 16, cudaMemcpyDeviceToHost), "copy");
-    CK(cudaMemcpy(b.data(), s->r1.as<float4>() + base, G * 16, cudaMemcpyDeviceToHost), "copy");
-    CK(cudaMemcpy(c.data(), s->r2.as<float4>() + base, G * 16, cudaMemcpyDeviceToHost), "copy");
-    CK(cudaMemcpy(h.data(), s->dbg_hxy.as<float2>() + base, G * 8, cudaMemcpyDeviceToHost), "copy");
-    for (int64_t g = 0; g < G; ++g) {
-        const bool vis = (mask[g >> 5] >> (g & 31)) & 1u;
+    const EnvInfo& E = s->last_envs[env - s->last_e0];
+    const int64_t n_local = E.n_local, nbp = bg_slots(s->D.n_bg);
+    const int64_t lg0 = s->D.n_bg + s->link_offsets[E.link_begin];
+    std::vector<uint32_t> mask((n_local + 31) / 32);
+    std::vector<float4> a(n_local), b(n_local), c(n_local);
+    std::vector<float2> h(n_local);
+    CK(cudaMemcpy(mask.data(), s->sc.mask.as<uint32_t>() + E.mask_base, mask.size() * 4, cudaMemcpyDeviceToHost),
+       "copy");
+    CK(cudaMemcpy(a.data(), s->sc.r0.as<float4>() + E.rec_base, n_local * 16, cudaMemcpyDeviceToHost), "copy");
+    CK(cudaMemcpy(b.data(), s->sc.r1.as<float4>() + E.rec_base, n_local * 16, cudaMemcpyDeviceToHost), "copy");
+    CK(cudaMemcpy(c.data(), s->sc.r2.as<float4>() + E.rec_base, n_local * 16, cudaMemcpyDeviceToHost), "copy");
+    CK(cudaMemcpy(h.data(), s->sc.dbg_hxy.as<float2>() + E.rec_base, n_local * 8, cudaMemcpyDeviceToHost), "copy");
+    if (visible) memset(visible, 0, (size_t)s->D.n);
+    for (int64_t j = 0; j < n_local; ++j) {
+        if (j >= s->D.n_bg && j < nbp) continue;  // padding slots
+        const int64_t g = j < s->D.n_bg ? j : lg0 + (j - nbp);
+        const bool vis = (mask[j >> 5] >> (j & 31)) & 1u;
         if (visible) visible[g] = vis ? 1 : 0;
         if (!vis) continue;
-        if (u) u[g] = a[g].x;
-        if (v) v[g] = a[g].y;
-        if (opacity) opacity[g] = a[g].z;
-        if (z) z[g] = a[g].w;
+        if (u) u[g] = a[j].x;
+        if (v) v[g] = a[j].y;
+        if (opacity) opacity[g] = a[j].z;
+        if (z) z[g] = a[j].w;
         if (conic) {  // records hold L with L^T L = conic * 0.5 log2(e) (upper triangular)
             const double k2 = 0.72134752044448170;
-            const double l00 = b[g].x, l01 = b[g].y, l11 = b[g].z;
+            const double l00 = b[j].x, l01 = b[j].y, l11 = b[j].z;
             conic[3 * g] = (float)(l00 * l00 / k2);
             conic[3 * g + 1] = (float)(l00 * l01 / k2);
             conic[3 * g + 2] = (float)((l01 * l01 + l11 * l11) / k2);
         }
         if (rgb) {
-            rgb[3 * g] = c[g].x;
-            rgb[3 * g + 1] = c[g].y;
-            rgb[3 * g + 2] = c[g].z;
+            rgb[3 * g] = c[j].x;
+            rgb[3 * g + 1] = c[j].y;
+            rgb[3 * g + 2] = c[j].z;
         }
-        if (hx) hx[g] = h[g].x;
-        if (hy) hy[g] = h[g].y;
+        if (hx) hx[g] = h[j].x;
+        if (hy) hy[g] = h[j].y;
         if (range) {
             uint32_t rx, ry;
-            float fx = b[g].w, fy = c[g].w;
+            float fx = b[j].w, fy = c[j].w;
             memcpy(&rx, &fx, 4);
             memcpy(&ry, &fy, 4);
             range[4 * g] = (int32_t)(rx & 0xffffu);
@@ -861,27 +1363,32 @@ gs_status gs_debug_copy_tiles(gs_scene s, int env, uint32_t* counts, int64_t n_c
     if (s->last_e0 < 0 || env < s->last_e0 || env >= s->last_e0 + s->last_We)
         return fail(GS_ERR_INVALID, "env %d is not in the last wave rendered", env);
     const int el = env - s->last_e0;
-    if (n_counts < s->last_T) return fail(GS_ERR_INVALID, "counts holds %lld < %d tiles", (long long)n_counts,
-                                          s->last_T);
+    const EnvInfo& E = s->last_envs[el];
+    if (n_counts < E.T) return fail(GS_ERR_INVALID, "counts holds %lld < %d tiles", (long long)n_counts, E.T);
     CK(cudaSetDevice(s->device), "set device");
     CK(cudaDeviceSynchronize(), "sync");
-    CK(cudaMemcpy(counts, s->counts.as<uint32_t>() + (size_t)el * s->last_T, (size_t)s->last_T * 4,
-                  cudaMemcpyDeviceToHost), "copy counts");
+    CK(cudaMemcpy(counts, s->sc.counts.as<uint32_t>() + E.tile_base, (size_t)E.T * 4, cudaMemcpyDeviceToHost),
+       "copy counts");
     if (!lists) return GS_OK;
-    if (!s->debug || !s->dbg_sorted.p) return fail(GS_ERR_INVALID, "debug was not enabled for the last render");
+    if (!s->debug || !s->sc.dbg_sorted.p) return fail(GS_ERR_INVALID, "debug was not enabled for the last render");
     if (el < s->last_ea || el >= s->last_eb)
         return fail(GS_ERR_INVALID, "env %d is not in the last sub-wave rendered", env);
     unsigned long long base = 0, total = 0;
-    CK(cudaMemcpy(&base, s->env_base.as<unsigned long long>() + el, 8, cudaMemcpyDeviceToHost), "copy base");
-    CK(cudaMemcpy(&total, s->env_base.as<unsigned long long>() + el + 1, 8, cudaMemcpyDeviceToHost), "copy base");
+    CK(cudaMemcpy(&base, s->sc.env_base.as<unsigned long long>() + el, 8, cudaMemcpyDeviceToHost), "copy base");
+    CK(cudaMemcpy(&total, s->sc.env_base.as<unsigned long long>() + el + 1, 8, cudaMemcpyDeviceToHost), "copy base");
     total -= base;
-    if ((unsigned long long)n_lists < total) return fail(GS_ERR_INVALID, "lists holds %lld < %llu entries",
-                                                         (long long)n_lists, total);
+    if ((unsigned long long)n_lists < total)
+        return fail(GS_ERR_INVALID, "lists holds %lld < %llu entries", (long long)n_lists, total);
     std::vector<unsigned long long> keys(total > 0 ? total : 1);
     if (total > 0)
-        CK(cudaMemcpy(keys.data(), s->dbg_sorted.as<unsigned long long>() + (base - s->last_pair_base), total * 8,
-                      cudaMemcpyDeviceToHost), "copy lists");
-    for (unsigned long long i = 0; i < total; ++i) lists[i] = (uint32_t)(keys[i] & 0xffffffffull);
+        CK(cudaMemcpy(keys.data(), s->sc.dbg_sorted.as<unsigned long long>() + (base - s->last_pair_base), total * 8,
+                      cudaMemcpyDeviceToHost),
+           "copy lists");
+    const int64_t nbp = bg_slots(s->D.n_bg), lg0 = s->D.n_bg + s->link_offsets[E.link_begin];
+    for (unsigned long long i = 0; i < total; ++i) {
+        const int64_t j = (int64_t)(keys[i] & 0xffffffffull);
+        lists[i] = (uint32_t)(j < s->D.n_bg ? j : lg0 + (j - nbp));
+    }
     return GS_OK;
 }
 
@@ -889,12 +1396,11 @@ void gs_scene_destroy(gs_scene s) {
     if (!s) return;
     cudaSetDevice(s->device);
     cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&s->g0, &s->g1, &s->g2, &s->g3, &s->gsh, &s->xf, &s->cams, &s->poses, &s->r0, &s->r1, &s->r2,
-                      &s->r3, &s->mask, &s->counts, &s->off, &s->cursor, &s->env_total, &s->env_base, &s->pairs,
-                      &s->dbg_hxy, &s->dbg_sorted, &s->stage_rgb[0], &s->stage_rgb[1], &s->stage_depth[0],
-                      &s->stage_depth[1], &s->stage_alpha[0], &s->stage_alpha[1]};
+    DevBuf* bufs[] = {&s->g0, &s->g1, &s->g2, &s->g3, &s->gsh, &s->stage_rgb[0], &s->stage_rgb[1],
+                      &s->stage_depth[0], &s->stage_depth[1], &s->stage_alpha[0], &s->stage_alpha[1], &s->poses,
+                      &s->neval};
     for (DevBuf* b : bufs) b->release();
-    s->neval.release();
+    s->sc.release();
     for (auto& m : s->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);

@@ -53,39 +53,53 @@ __device__ __forceinline__ void for_each_visible(const uint32_t* mask, int64_t w
     }
 }
 
-// grid: (blocks over mask words, envs); block 256; dynamic smem T u32
+// Rebuilds a block's tile histogram of env el's visible records in hist[0, T).
+__device__ __forceinline__ void block_histogram(const BinParams& P, const EnvInfo& E, int64_t w0, int64_t w1,
+                                                uint16_t* wbuf, uint32_t* hist) {
+    const uint32_t* mask = P.mask + E.mask_base;
+    const uint4* r3 = P.r3 + E.rec_base;
+    for_each_visible(mask, w0, w1, wbuf, [&](int64_t j) {
+        const uint4 q = r3[j];
+        int tx0, tx1, ty0, ty1;
+        tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * E.ntx + tx], 1u);
+    });
+}
+
+// grid: (blocks over the largest env's visibility words, envs); block 256;
+// dynamic smem: max T u32.  Blocks past their env's words exit at once.
 __global__ void __launch_bounds__(256) k_count(BinParams P) {
     extern __shared__ uint32_t hist[];
     __shared__ uint16_t wbuf[8 * 1024];
     const int el = P.e_begin + blockIdx.y;
-    for (int t = threadIdx.x; t < P.T; t += blockDim.x) hist[t] = 0;
-    __syncthreads();
+    const EnvInfo E = P.envs[el];
+    const int64_t words = (E.n_local + 31) / 32;
     const int64_t w0 = (int64_t)blockIdx.x * P.words_per_block;
-    const int64_t w1 = min(w0 + (int64_t)P.words_per_block, P.mask_words);
-    const uint32_t* mask = P.mask + (size_t)el * P.mask_words;
-    const uint4* r3 = P.r3 + (size_t)el * P.G;
-    for_each_visible(mask, w0, w1, wbuf, [&](int64_t g) {
-        const uint4 q = r3[g];
-        int tx0, tx1, ty0, ty1;
-        tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * P.ntx + tx], 1u);
-    });
+    if (w0 >= words) return;
+    const int64_t w1 = min(w0 + (int64_t)P.words_per_block, words);
+    for (int t = threadIdx.x; t < E.T; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    uint32_t* cnt = P.counts + (size_t)el * P.T;
-    for (int t = threadIdx.x; t < P.T; t += blockDim.x) {
+    block_histogram(P, E, w0, w1, wbuf, hist);
+    __syncthreads();
+    uint32_t* cnt = P.counts + E.tile_base;
+    for (int t = threadIdx.x; t < E.T; t += blockDim.x) {
         const uint32_t h = hist[t];
         if (h) atomicAdd(cnt + t, h);
     }
 }
 
-cudaError_t launch_count(const BinParams& P, int n_envs, cudaStream_t st, size_t smem) {
-    if (n_envs == 0) return cudaSuccess;
-    dim3 grid((unsigned)((P.mask_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
-    if (smem > 16 * 1024) {  // plus 16 KB of static shared memory
-        cudaError_t e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+static cudaError_t opt_in_smem(const void* fn, size_t smem) {
+    if (smem <= 16 * 1024) return cudaSuccess;  // plus 16 KB of static shared memory
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_count(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st) {
+    if (n_envs == 0 || max_words == 0) return cudaSuccess;
+    const size_t smem = (size_t)max_T * 4;
+    cudaError_t e = opt_in_smem((const void*)k_count, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((max_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
     k_count<<<grid, 256, smem, st>>>(P);
     return cudaGetLastError();
 }
@@ -120,12 +134,13 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* warp_tot, T& block_tot
 }
 
 // per env: off_local[t] = sum_{t' < t} counts[t'], env_total = sum
-__global__ void __launch_bounds__(1024) k_scan_env(const uint32_t* counts, uint32_t* off_local,
-                                                   unsigned long long* env_total, int T) {
+__global__ void __launch_bounds__(1024) k_scan_env(const EnvInfo* envs, const uint32_t* counts, uint32_t* off_local,
+                                                   unsigned long long* env_total) {
     __shared__ uint32_t wt[32];
     const int el = blockIdx.x;
-    const uint32_t* c = counts + (size_t)el * T;
-    uint32_t* o = off_local + (size_t)el * T;
+    const int T = envs[el].T;
+    const uint32_t* c = counts + envs[el].tile_base;
+    uint32_t* o = off_local + envs[el].tile_base;
     uint32_t carry = 0;
     for (int base = 0; base < T; base += blockDim.x) {
         const int t = base + threadIdx.x;
@@ -154,69 +169,71 @@ __global__ void __launch_bounds__(1024) k_scan_base(const unsigned long long* en
     if (threadIdx.x == 0) env_base[We] = carry;
 }
 
-cudaError_t launch_scan(const uint32_t* counts, uint32_t* off_local, unsigned long long* env_total,
-                        unsigned long long* env_base, int We, int T, cudaStream_t st) {
+cudaError_t launch_scan(const EnvInfo* envs, const uint32_t* counts, uint32_t* off_local,
+                        unsigned long long* env_total, unsigned long long* env_base, int We, cudaStream_t st) {
     if (We == 0) return cudaSuccess;
-    k_scan_env<<<We, 1024, 0, st>>>(counts, off_local, env_total, T);
+    k_scan_env<<<We, 1024, 0, st>>>(envs, counts, off_local, env_total);
     k_scan_base<<<1, 1024, 0, st>>>(env_total, env_base, We);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- scatter
-// Same partition and visiting order as k_count.  Pass 1 rebuilds the block's histogram, then one
-// global atomic per touched tile reserves the block's range of that bucket;
-// pass 2 writes each key at (bucket start + block range + shared cursor).
+// Same partition and visiting order as k_count.  Pass 1 rebuilds the block's
+// histogram, then one global atomic per touched tile reserves the block's range
+// of that bucket; pass 2 writes each key at (bucket start + block range +
+// shared cursor).  A key past the pair buffer's capacity (possible only for a
+// launch planned with a fixed capacity) is dropped and flagged.
 
 __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
     extern __shared__ uint32_t sm[];
     __shared__ uint16_t wbuf[8 * 1024];
-    uint32_t* hist = sm;
-    uint32_t* base = sm + P.T;
     const int el = P.e_begin + blockIdx.y;
-    for (int t = threadIdx.x; t < P.T; t += blockDim.x) hist[t] = 0;
-    __syncthreads();
+    const EnvInfo E = P.envs[el];
+    const int64_t words = (E.n_local + 31) / 32;
     const int64_t w0 = (int64_t)blockIdx.x * P.words_per_block;
-    const int64_t w1 = min(w0 + (int64_t)P.words_per_block, P.mask_words);
-    const uint32_t* mask = P.mask + (size_t)el * P.mask_words;
-    const uint4* r3 = P.r3 + (size_t)el * P.G;
-    for_each_visible(mask, w0, w1, wbuf, [&](int64_t g) {
-        const uint4 q = r3[g];
-        int tx0, tx1, ty0, ty1;
-        tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * P.ntx + tx], 1u);
-    });
+    if (w0 >= words) return;
+    const int64_t w1 = min(w0 + (int64_t)P.words_per_block, words);
+    uint32_t* hist = sm;
+    uint32_t* base = sm + E.T;
+    for (int t = threadIdx.x; t < E.T; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    uint32_t* cur = P.cursor + (size_t)el * P.T;
-    const uint32_t* off = P.off_local + (size_t)el * P.T;
+    block_histogram(P, E, w0, w1, wbuf, hist);
+    __syncthreads();
+    uint32_t* cur = P.cursor + E.tile_base;
+    const uint32_t* off = P.off_local + E.tile_base;
     const unsigned long long eb = P.env_base[el] - P.pair_base;
-    for (int t = threadIdx.x; t < P.T; t += blockDim.x) {
+    for (int t = threadIdx.x; t < E.T; t += blockDim.x) {
         const uint32_t h = hist[t];
         if (h) base[t] = off[t] + atomicAdd(cur + t, h);
         hist[t] = 0;
     }
     __syncthreads();
-    for_each_visible(mask, w0, w1, wbuf, [&](int64_t g) {
-        const uint4 q = r3[g];
-        const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)(uint32_t)g;
+    const uint32_t* mask = P.mask + E.mask_base;
+    const uint4* r3 = P.r3 + E.rec_base;
+    bool dropped = false;
+    for_each_visible(mask, w0, w1, wbuf, [&](int64_t j) {
+        const uint4 q = r3[j];
+        const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)(uint32_t)j;
         int tx0, tx1, ty0, ty1;
         tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) {
-                const int t = ty * P.ntx + tx;
+                const int t = ty * E.ntx + tx;
                 const uint32_t k = atomicAdd(&hist[t], 1u);
-                P.pairs[eb + base[t] + k] = key;
+                const unsigned long long pos = eb + base[t] + k;
+                if (pos < P.pair_cap) P.pairs[pos] = key;
+                else dropped = true;
             }
     });
+    if (__syncthreads_or(dropped) && threadIdx.x == 0) atomicOr(P.status, kStOverflow);
 }
 
-cudaError_t launch_scatter(const BinParams& P, int n_envs, cudaStream_t st, size_t smem) {
-    if (n_envs == 0) return cudaSuccess;
-    dim3 grid((unsigned)((P.mask_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
-    if (smem > 16 * 1024) {  // plus 16 KB of static shared memory
-        cudaError_t e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+cudaError_t launch_scatter(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st) {
+    if (n_envs == 0 || max_words == 0) return cudaSuccess;
+    const size_t smem = (size_t)max_T * 8;
+    cudaError_t e = opt_in_smem((const void*)k_scatter, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((max_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
     k_scatter<<<grid, 256, smem, st>>>(P);
     return cudaGetLastError();
 }

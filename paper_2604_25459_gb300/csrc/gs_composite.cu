@@ -199,11 +199,13 @@ __device__ __forceinline__ float splat_alpha(const float4& A, const float4& B, f
     return fminf(0.99f, __fmul_rn(A.z, ex2_approx(pw)));
 }
 
-// CTA = one (env, tile) of TW x TH pixels with TW*TH/2 threads; warp w owns an
-// 8x8 subtile and each lane two pixels of it, (x, y) and (x, y + 4), whose
-// blend chains are independent.
+// Persistent CTAs of TW*TH/2 threads claim (env, tile) items from a work
+// counter, `chunk` consecutive items at a time (items run env-major, tiles
+// row-major, so envs of any resolution mix in one launch).  For an item the
+// CTA covers the TW x TH tile: warp w owns an 8x8 subtile and each lane two
+// pixels of it, (x, y) and (x, y + 4), whose blend chains are independent.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_composite(CompParams P) {
+__global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_composite(CompParams P) {
     constexpr int NT = TW * TH / 2;
     constexpr int NB = NT;  // splats staged per batch (one per thread)
     constexpr int CAP = kCompCap;
@@ -226,26 +228,54 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_compo
     uint16_t* cnt = reinterpret_cast<uint16_t*>(cbuf);
     uint32_t* hist = reinterpret_cast<uint32_t*>(cbuf);
 
+    __shared__ unsigned int s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int el = P.e_begin + blockIdx.y;
-    const int t = blockIdx.x;
-    const int tx = t % P.ntx, ty = t / P.ntx;
+    const bool dbg = P.dbg_sorted != nullptr;
+    int el = P.e_begin;  // env of the current item, cached across items (uniform in the CTA)
+    unsigned int e_lo = P.envs[el].tile_base, e_hi = e_lo + (unsigned)P.envs[el].T;
+    if (tid == 0) s_item = atomicAdd(P.work, (unsigned)P.chunk);
+    __syncthreads();
+    for (;;) {
+    const unsigned int first = P.item_begin + s_item;
+    if (first >= P.item_end) break;
+    const unsigned int last = min(first + (unsigned)P.chunk, P.item_end);
+    for (unsigned int item = first; item < last; ++item) {
+    if (item < e_lo || item >= e_hi) {
+        int lo = P.e_begin, hi = P.e_end - 1;  // env: last e with tile_base <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&P.envs[mid].tile_base) <= item) lo = mid; else hi = mid - 1;
+        }
+        el = lo;
+        e_lo = P.envs[el].tile_base;
+        e_hi = e_lo + (unsigned)P.envs[el].T;
+    }
+    const EnvInfo* Ep = P.envs + el;
+    const int W = __ldg(&Ep->W), H = __ldg(&Ep->H), ntx = __ldg(&Ep->ntx);
+    const unsigned int tile_base = e_lo;
+    const unsigned int n_local = __ldg(&Ep->n_local);
+    const unsigned long long pix_base = __ldg(&Ep->pix_base);
+    const int t = (int)(item - tile_base);
+    const int tx = t % ntx, ty = t / ntx;
     constexpr int SWX = TW / 8;
     const int wx0 = tx * TW + (warp % SWX) * 8, wy0 = ty * TH + (warp / SWX) * 8;
     const int wx1 = wx0 + 7, wy1 = wy0 + 7;
     const int px = wx0 + (lane & 7), py0 = wy0 + (lane >> 3), py1 = py0 + 4;
-    const bool in0 = px < P.W && py0 < P.H, in1 = px < P.W && py1 < P.H;
+    const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
     const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f, fpy1 = (float)py1 + 0.5f;
     bool done0 = !in0, done1 = !in1;
     float T0 = 1.0f, r0 = 0.0f, g0 = 0.0f, b0 = 0.0f, d0 = 0.0f;
     float T1 = 1.0f, r1 = 0.0f, g1 = 0.0f, b1 = 0.0f, d1 = 0.0f;
     uint32_t ncomp = 0;
 
-    const uint32_t n = P.counts[(size_t)el * P.T + t];
-    const unsigned long long start = P.env_base[el] - P.pair_base + P.off_local[(size_t)el * P.T + t];
+    uint32_t n = P.counts[tile_base + t];
+    const unsigned long long start = P.env_base[el] - P.pair_base + P.off_local[tile_base + t];
+    if (start + n > P.pair_cap) {  // keys past a planned capacity were dropped: render nothing
+        n = 0;
+        if (tid == 0) atomicOr(P.status, kStOverflow);
+    }
     const unsigned long long* Lk = P.pairs + start;
-    const size_t recbase = (size_t)el * P.G;
-    const bool dbg = P.dbg_sorted != nullptr;
+    const size_t recbase = (size_t)__ldg(&Ep->rec_base);
 
     unsigned long long kmax = 0;
     if (n > (uint32_t)CAP) {
@@ -354,7 +384,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_compo
             const int cnt_b = (int)min((uint32_t)NB, wn - b);
             for (int s = tid; s < cnt_b; s += NT) {
                 const uint32_t g = (uint32_t)(keys[b + s] & 0xffffffffull);
-                if (g < (uint64_t)P.G) {
+                if (g < n_local) {
                     const size_t ri = recbase + g;
                     const float4 q0 = P.r0[ri];
                     const float4 q1 = P.r1[ri];
@@ -454,9 +484,8 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_compo
         for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
         if (lane == 0 && c) atomicAdd(P.neval, (unsigned long long)c);
     }
-    const size_t plane = (size_t)P.H * P.W;
     if (in0) {
-        const size_t pix = (size_t)el * plane + (size_t)py0 * P.W + px;
+        const size_t pix = pix_base + (size_t)py0 * W + px;
         P.rgb[3 * pix] = fminf(fmaxf(r0, 0.0f), 1.0f);
         P.rgb[3 * pix + 1] = fminf(fmaxf(g0, 0.0f), 1.0f);
         P.rgb[3 * pix + 2] = fminf(fmaxf(b0, 0.0f), 1.0f);
@@ -465,7 +494,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_compo
         if (P.alpha) P.alpha[pix] = a;
     }
     if (in1) {
-        const size_t pix = (size_t)el * plane + (size_t)py1 * P.W + px;
+        const size_t pix = pix_base + (size_t)py1 * W + px;
         P.rgb[3 * pix] = fminf(fmaxf(r1, 0.0f), 1.0f);
         P.rgb[3 * pix + 1] = fminf(fmaxf(g1, 0.0f), 1.0f);
         P.rgb[3 * pix + 2] = fminf(fmaxf(b1, 0.0f), 1.0f);
@@ -473,20 +502,46 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 7 : 12)) k_compo
         P.depth[pix] = a > 0.0f ? d1 / a : 0.0f;
         if (P.alpha) P.alpha[pix] = a;
     }
+    __syncthreads();  // shared staging is reused by the next item
+    }  // items of the claim
+    if (tid == 0) s_item = atomicAdd(P.work, (unsigned)P.chunk);  // every thread has read the last claim
+    __syncthreads();
+    }  // claims
 }
 
-cudaError_t launch_composite(const CompParams& P, int n_envs, cudaStream_t st) {
-    if (n_envs == 0) return cudaSuccess;
-    dim3 grid((unsigned)P.T, (unsigned)n_envs);
-    if (P.tile_w == 16 && P.tile_h == 16)
-        k_composite<16, 16><<<grid, 128, 0, st>>>(P);
-    else if (P.tile_w == 8 && P.tile_h == 8)
-        k_composite<8, 8><<<grid, 32, 0, st>>>(P);
-    else if (P.tile_w == 16 && P.tile_h == 8)
-        k_composite<16, 8><<<grid, 64, 0, st>>>(P);
-    else
-        k_composite<32, 8><<<grid, 128, 0, st>>>(P);
+template <int TW, int TH>
+static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas) {
+    constexpr int NT = TW * TH / 2;
+    static int per_sm[64] = {0};  // resident CTAs per SM, per device
+    static int sms[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (per_sm[dev] == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[dev], k_composite<TW, TH>, NT, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (per_sm[dev] < 1) per_sm[dev] = 1;
+    }
+    const unsigned items = P.item_end - P.item_begin;
+    unsigned grid = (unsigned)(per_sm[dev] * sms[dev]);
+    const unsigned claims = (items + P.chunk - 1) / P.chunk;
+    if (grid > claims) grid = claims;
+    if (grid == 0) grid = 1;
+    *ctas = (int)grid;
+    k_composite<TW, TH><<<grid, NT, 0, st>>>(P);
     return cudaGetLastError();
+}
+
+cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
+    *ctas = 0;
+    if (P.item_end <= P.item_begin) return cudaSuccess;
+    if (P.tile_w == 16 && P.tile_h == 16) return launch_tiles<16, 16>(P, st, ctas);
+    if (P.tile_w == 8 && P.tile_h == 8) return launch_tiles<8, 8>(P, st, ctas);
+    if (P.tile_w == 16 && P.tile_h == 8) return launch_tiles<16, 8>(P, st, ctas);
+    return launch_tiles<32, 8>(P, st, ctas);
 }
 
 }  // namespace gsb

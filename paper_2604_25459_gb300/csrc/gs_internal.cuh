@@ -1,7 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libgsbatch.
 //
-// Device data layout (all in HBM, owned by the scene):
-//   Gaussians, background first then link-major (global index g):
+// Device data layout (all in HBM):
+//   Gaussians (scene-owned), background first then link-major (global index g):
 //     p0[g] = {mean.x, mean.y, mean.z, opacity}
 //     p1[g] = {F00, F01, F02, F10}      F = R diag(exp(s)), the factor of the 3D
 //     p2[g] = {F11, F12, F20, F21}      covariance F F^T in the frame the mean lives
@@ -11,14 +11,16 @@
 //                                       background, l+1 for link l (int bits)
 //     sh plane-major: plane p holds values 4p..4p+3 (f32) or 8p..8p+7 (bf16/f16)
 //     of the flattened [coefficient][channel] vector, for every g: sh[p][g].
-//   Per wave of envs (local env index el, G Gaussians, T tiles):
-//     xf[el][L+1]        link transforms composed with the camera (+ camera
-//                        centre in the link frame for the SH view direction)
-//     r0..r3[el*G + g]   projected record of (el, g), valid where the bit is set in
-//     mask[el][g/32]     (bit g%32)
-//     counts[el][t], off_local[el][t], cursor[el][t]   per (env, tile) intersections
-//     env_base[el]       exclusive scan of per-env intersection totals (+ total)
-//     pairs[...]         u64 keys (depth bits << 32 | g), bucketed by (env, tile)
+//   Per wave of envs (scratch), env el described by EnvInfo envs[el]:
+//     record slots: local index j = g for background Gaussians (padded to a
+//       multiple of 32), then the env's link Gaussians in global order; slot
+//       (el, j) is at envs[el].rec_base + j in r0..r3, valid where bit j%32 of
+//       mask[envs[el].mask_base + j/32] is set.  Local order = global order, so
+//       the key (depth bits << 32 | j) orders ties by global index.
+//     xf[envs[el].xf_base + f]  frame f = 0 background, f = 1 + (l - link_begin)
+//     counts/off_local/cursor[envs[el].tile_base + t]  per (env, tile)
+//     env_base[el]              exclusive scan of per-env intersection totals
+//     pairs[...]                u64 keys bucketed by (env, tile)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,7 +35,7 @@ namespace gsb {
 enum : uint32_t {
     kStBadPose = 1u,     // zero or non-finite link pose quaternion
     kStBadScene = 2u,    // zero or non-finite Gaussian quaternion at scene build
-    kStOverflow = 4u,    // a bucket exceeded what the kernels can address
+    kStOverflow = 4u,    // intersection keys beyond the capacity (planned launches) or a corrupted bucket
 };
 
 // Row-major rigid transform camera <- frame, plus the camera centre in that frame.
@@ -64,45 +66,74 @@ inline int sh_planes_for(int degree, gs_dtype dt) {
     return dt == GS_F32 ? (v + 3) / 4 : (v + 7) / 8;
 }
 
+// One environment of a wave.
+struct EnvInfo {
+    unsigned long long rec_base;   // first record slot
+    unsigned long long mask_base;  // first visibility word
+    unsigned long long pix_base;   // first pixel of the env's image in the outputs
+    long long pose_base;           // index (units of 7 floats) of the pose of link_begin
+    unsigned int tile_base;        // first (env, tile) counter of the wave
+    unsigned int n_local;          // record slots: padded background + the env's link Gaussians
+    int xf_base;                   // first link-table entry
+    int link_begin, n_links;       // links of the scene rendered in this env
+    int W, H, ntx, T;              // image and tile grid
+    int pad;
+};
+
+// A projection block: up to 256 consecutive Gaussians (thread t takes global
+// index g_first + t, record slot local_first + t) for envs [e0, e1) of a wave;
+// link frame of Gaussian with link field li is xf[envs[e].xf_base + li - lb].
+struct ProjBlock {
+    long long g_first;
+    unsigned int local_first;  // multiple of 32
+    int n;
+    int e0, e1;
+    int lb;
+    int pad;
+};
+
 struct ProjParams {
-    int64_t G;
+    int64_t n_gauss;  // SH plane stride
     const float4* p0;
     const float4* p1;
     const float4* p2;
     const float4* p3;
     const void* sh;
-    const LinkXf* xf;        // [We][L+1]
-    const gs_camera* cams;   // [We]
-    int L1;                  // n_links + 1
-    int We;
-    int env_group;
+    const ProjBlock* blocks;
+    const EnvInfo* envs;
+    const gs_camera* cams;  // per env of the wave
+    const LinkXf* xf;
     float4* r0;
     float4* r1;
     float4* r2;
     uint4* r3;
-    uint32_t* mask;          // [We][mask_words]
-    int64_t mask_words;
-    float2* dbg_hxy;         // nullable, [We][G]
+    uint32_t* mask;
+    float2* dbg_hxy;  // nullable, per record slot
 };
 
 struct BinParams {
-    int64_t G;
-    int64_t mask_words;
+    const EnvInfo* envs;
     const uint32_t* mask;
     const uint4* r3;
     int e_begin;             // first env (wave-local) handled by this launch
-    int tile_w, tile_h, ntx, T;
-    uint32_t* counts;        // [We][T]
+    int tile_w, tile_h;
+    int words_per_block;
+    uint32_t* counts;
     const uint32_t* off_local;
     const unsigned long long* env_base;
     unsigned long long pair_base;   // env_base[e_begin], subtracted from absolute offsets
-    uint32_t* cursor;        // [We][T]
+    unsigned long long pair_cap;    // keys the pair buffer holds
+    uint32_t* cursor;
     unsigned long long* pairs;
-    int words_per_block;
+    uint32_t* status;
 };
 
 struct CompParams {
-    int64_t G;
+    const EnvInfo* envs;
+    int e_begin, e_end;              // envs of this launch (wave-local)
+    unsigned int item_begin, item_end;  // (env, tile) items: envs[e_begin].tile_base .. envs[e_end].tile_base
+    int chunk;                       // items claimed per atomic
+    unsigned int* work;              // work counter (zeroed before the launch)
     const float4* r0;
     const float4* r1;
     const float4* r2;
@@ -110,12 +141,12 @@ struct CompParams {
     const uint32_t* off_local;
     const unsigned long long* env_base;
     unsigned long long pair_base;
+    unsigned long long pair_cap;
     const unsigned long long* pairs;
     unsigned long long* dbg_sorted;  // nullable: receives the full depth-ordered lists
     unsigned long long* neval;       // nullable: composited (pixel, Gaussian) pair counter
-    int e_begin;
-    int W, H, tile_w, tile_h, ntx, T;
-    float* rgb;     // [We][H][W][3] for the wave (env el at el*H*W*3)
+    int tile_w, tile_h;
+    float* rgb;     // images at envs[e].pix_base (x3 for rgb)
     float* depth;
     float* alpha;   // nullable
     uint32_t* status;
@@ -125,14 +156,19 @@ struct CompParams {
 cudaError_t launch_prep(const float* mean, const float* quat, const void* log_scale, const void* opacity,
                         const void* sh, int64_t n, int64_t dst_offset, int link_of_first, const int64_t* link_offsets,
                         int n_links, const DevGaussians& D, uint32_t* status, cudaStream_t st);
-cudaError_t launch_link_table(const float* poses, const gs_camera* cams, int We, int n_links, LinkXf* out,
-                              uint32_t* status, cudaStream_t st);
-cudaError_t launch_project(const DevGaussians& D, const ProjParams& P, dim3 grid, cudaStream_t st);
-cudaError_t launch_count(const BinParams& P, int n_envs, cudaStream_t st, size_t smem);
-cudaError_t launch_scan(const uint32_t* counts, uint32_t* off_local, unsigned long long* env_total,
-                        unsigned long long* env_base, int We, int T, cudaStream_t st);
-cudaError_t launch_scatter(const BinParams& P, int n_envs, cudaStream_t st, size_t smem);
-cudaError_t launch_composite(const CompParams& P, int n_envs, cudaStream_t st);
+// n_items = sum over envs of (1 + n_links); envs[We].xf_base must hold n_items.
+cudaError_t launch_link_table(const float* poses, const gs_camera* cams, const EnvInfo* envs, int We, int n_items,
+                              LinkXf* out, uint32_t* status, cudaStream_t st);
+cudaError_t launch_project(const DevGaussians& D, const ProjParams& P, int n_blocks, cudaStream_t st);
+// grid.x covers the largest env's mask words; max_T sizes the shared histogram
+cudaError_t launch_count(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st);
+cudaError_t launch_scan(const EnvInfo* envs, const uint32_t* counts, uint32_t* off_local,
+                        unsigned long long* env_total, unsigned long long* env_base, int We, cudaStream_t st);
+cudaError_t launch_scatter(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st);
+// grid = persistent CTAs; returns the grid size used through *ctas
+cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas);
+
+constexpr int kWordsPerBlock = 256;  // binning block: 8 warps x 32 visibility words (8192 slots)
 
 // Depth-ordered window held in shared memory by the compositor.  Smaller
 // windows sort less in tiles that terminate early, larger ones re-scan long
@@ -150,5 +186,21 @@ struct SceneView {
 SceneView scene_view(gs_scene s);
 // Set the thread-local message returned by gs_last_error and return st.
 gs_status report(gs_status st, const char* msg);
+
+// Host-side construction of a wave's tables (shared by all entry points).
+struct EnvSpec {        // one env as requested by the caller
+    const gs_camera* cam;
+    int link_begin, link_end;
+    long long pose_offset;    // pose index of link_begin
+    long long pixel_offset;   // first pixel of the image
+};
+int64_t bg_slots(int64_t n_bg);  // background slots padded to 32
+// Fills envs (n+1 entries; the last holds the totals in rec_base, mask_base,
+// tile_base and xf_base) and appends projection blocks; returns totals through
+// the EnvInfo sentinel.  link_offsets: host copy of the scene's link offsets.
+void build_wave_tables(const DevGaussians& D, const int64_t* link_offsets, const EnvSpec* specs, int n, int tile_w,
+                       int tile_h, long long pix_rebase, EnvInfo* envs, ProjBlock* blocks, int* n_blocks,
+                       int max_blocks);
+int count_wave_blocks(const DevGaussians& D, const int64_t* link_offsets, const EnvSpec* specs, int n);
 
 }  // namespace gsb

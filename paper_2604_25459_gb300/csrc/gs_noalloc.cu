@@ -61,27 +61,35 @@ gs_status scratch_on(int dev, unsigned char** out) {
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
+constexpr int kMaxBlocks = 16384;  // projection blocks per wave (host tables are static too)
+EnvSpec h_specs[kMaxWave];
+EnvInfo h_envs[kMaxWave + 1];
+ProjBlock h_blocks[kMaxBlocks];
+
 struct Layout {
-    size_t cams, xf, r0, r1, r2, r3, mask, counts, off, cursor, env_total, env_base, pairs, end_fixed;
+    size_t envs, blocks, cams, xf, r0, r1, r2, r3, mask, counts, off, cursor, env_total, env_base, work, pairs;
 };
 
-Layout layout(int We, int64_t G, int L, int64_t mask_words, int T) {
+Layout layout(int We, int nb, int xf_items, unsigned long long recs, unsigned long long words,
+              unsigned long long tiles) {
     Layout y{};
     size_t o = 0;
-    y.cams = o;      o = up256(o + (size_t)We * sizeof(gs_camera));
-    y.xf = o;        o = up256(o + (size_t)We * (L + 1) * sizeof(LinkXf));
-    y.r0 = o;        o = up256(o + (size_t)We * G * 16);
-    y.r1 = o;        o = up256(o + (size_t)We * G * 16);
-    y.r2 = o;        o = up256(o + (size_t)We * G * 16);
-    y.r3 = o;        o = up256(o + (size_t)We * G * 16);
-    y.mask = o;      o = up256(o + (size_t)We * mask_words * 4);
-    y.counts = o;    o = up256(o + (size_t)We * T * 4);
-    y.off = o;       o = up256(o + (size_t)We * T * 4);
-    y.cursor = o;    o = up256(o + (size_t)We * T * 4);
+    y.envs = o;      o = up256(o + sizeof(EnvInfo) * ((size_t)We + 1));
+    y.blocks = o;    o = up256(o + sizeof(ProjBlock) * (size_t)(nb > 0 ? nb : 1));
+    y.cams = o;      o = up256(o + sizeof(gs_camera) * (size_t)We);
+    y.xf = o;        o = up256(o + sizeof(LinkXf) * (size_t)xf_items);
+    y.r0 = o;        o = up256(o + recs * 16);
+    y.r1 = o;        o = up256(o + recs * 16);
+    y.r2 = o;        o = up256(o + recs * 16);
+    y.r3 = o;        o = up256(o + recs * 16);
+    y.mask = o;      o = up256(o + words * 4);
+    y.counts = o;    o = up256(o + tiles * 4);
+    y.off = o;       o = up256(o + tiles * 4);
+    y.cursor = o;    o = up256(o + tiles * 4);
     y.env_total = o; o = up256(o + (size_t)We * 8);
-    y.env_base = o;  o = up256(o + (size_t)(We + 1) * 8);
+    y.env_base = o;  o = up256(o + ((size_t)We + 1) * 8);
+    y.work = o;      o = up256(o + 16);
     y.pairs = o;
-    y.end_fixed = o;
     return y;
 }
 
@@ -123,7 +131,8 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
         if (!(qn > 0) || !isfinite(qn) || !isfinite(c.t_cw[0] + c.t_cw[1] + c.t_cw[2]))
             return failf(GS_ERR_INVALID, "camera %lld: pose invalid", e);
     }
-    const int ntx = (W + v.tile_w - 1) / v.tile_w, nty = (H + v.tile_h - 1) / v.tile_h, T = ntx * nty;
+    const int tw = v.tile_w, th = v.tile_h;
+    const int ntx = (W + tw - 1) / tw, nty = (H + th - 1) / th, T = ntx * nty;
     if (T > 16384) return failf(GS_ERR_UNSUPPORTED, "%lld tiles per image exceed 16384", T);
     NA_CK(cudaSetDevice(v.device), "set device");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -138,75 +147,97 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
     unsigned char* base = nullptr;
     gs_status r = scratch_on(v.device, &base);
     if (r != GS_OK) return r;
-    const int64_t mask_words = (G + 31) / 32;
+    std::lock_guard<std::mutex> lk(g_setup_mu);  // the static host tables below are shared too
+    const int64_t n_local = bg_slots(v.D.n_bg) + (v.D.n - v.D.n_bg);
+    const unsigned long long words1 = (unsigned long long)(n_local + 31) / 32;
     // largest wave whose fixed part leaves at least a quarter of the array for keys
     int We = n_envs < kMaxWave ? n_envs : kMaxWave;
-    while (We > 0 && layout(We, G, L, mask_words, T).end_fixed > kNoAllocBytes / 4 * 3) --We;
+    auto fixed = [&](int w) {
+        return layout(w, kMaxBlocks, w * (1 + L), (unsigned long long)w * n_local, words1 * w,
+                      (unsigned long long)w * T).pairs;
+    };
+    while (We > 0 && fixed(We) > kNoAllocBytes / 4 * 3) --We;
     if (We == 0)
         return failf(GS_ERR_UNSUPPORTED,
                      "scene too large for the no-allocation path: one env needs %lld bytes of records, the fixed "
                      "scratch holds %lld (use gs_render_batch)",
-                     (long long)layout(1, G, L, mask_words, T).end_fixed, (long long)kNoAllocBytes);
-    const Layout y = layout(We, G, L, mask_words, T);
-    const size_t pose_floats = (size_t)L * 7;
-    unsigned long long eb[kMaxWave + 1];
+                     (long long)fixed(1), (long long)kNoAllocBytes);
+    int64_t link_offs[2] = {0, v.D.n - v.D.n_bg};  // all links of a uniform batch, as one contiguous range
     for (int e0 = 0; e0 < n_envs; e0 += We) {
         const int Wn = n_envs - e0 < We ? n_envs - e0 : We;
-        gs_camera* cams_dev = reinterpret_cast<gs_camera*>(base + y.cams);
+        for (int e = 0; e < Wn; ++e)
+            h_specs[e] = EnvSpec{cams + e0 + e, 0, L, (long long)(e0 + e) * L, (long long)e * (long long)px};
+        // the link range [0, L) of every env maps to link Gaussians [0, n_link_gaussians)
+        DevGaussians D1 = v.D;
+        D1.n_links = L;
+        int nb = 0;
+        // build_wave_tables reads link_offsets[link_begin] and [link_end]; give it a
+        // table where index 0 is 0 and index L is the link Gaussian count
+        static int64_t lo_table[4097];
+        if (L > 4096) return report(GS_ERR_UNSUPPORTED, "more than 4096 links on the no-allocation path");
+        for (int l = 0; l <= L; ++l) lo_table[l] = l == L ? link_offs[1] : 0;
+        build_wave_tables(D1, lo_table, h_specs, Wn, tw, th, 0, h_envs, h_blocks, &nb, kMaxBlocks);
+        if (nb > kMaxBlocks)
+            return failf(GS_ERR_UNSUPPORTED, "%lld projection blocks exceed the no-allocation table of %lld", nb,
+                         kMaxBlocks);
+        const EnvInfo& sen = h_envs[Wn];
+        const Layout y = layout(Wn, nb, sen.xf_base, sen.rec_base, sen.mask_base, sen.tile_base);
+        int max_words = 0, max_T = 0;
+        for (int e = 0; e < Wn; ++e) {
+            max_words = max_words > (int)((h_envs[e].n_local + 31) / 32) ? max_words : (int)((h_envs[e].n_local + 31) / 32);
+            max_T = max_T > h_envs[e].T ? max_T : h_envs[e].T;
+        }
+        EnvInfo* d_envs = reinterpret_cast<EnvInfo*>(base + y.envs);
+        ProjBlock* d_blocks = reinterpret_cast<ProjBlock*>(base + y.blocks);
+        gs_camera* d_cams = reinterpret_cast<gs_camera*>(base + y.cams);
         LinkXf* xf = reinterpret_cast<LinkXf*>(base + y.xf);
-        NA_CK(cudaMemcpyAsync(cams_dev, cams + e0, (size_t)Wn * sizeof(gs_camera), cudaMemcpyHostToDevice, st),
+        NA_CK(cudaMemcpyAsync(d_envs, h_envs, sizeof(EnvInfo) * ((size_t)Wn + 1), cudaMemcpyHostToDevice, st),
+              "copy env table");
+        NA_CK(cudaMemcpyAsync(d_blocks, h_blocks, sizeof(ProjBlock) * (size_t)nb, cudaMemcpyHostToDevice, st),
+              "copy block table");
+        NA_CK(cudaMemcpyAsync(d_cams, cams + e0, sizeof(gs_camera) * (size_t)Wn, cudaMemcpyHostToDevice, st),
               "copy cams");
-        NA_CK(launch_link_table(L > 0 ? link_poses + (size_t)e0 * pose_floats : nullptr, cams_dev, Wn, L, xf,
-                                v.status, st),
-              "link table");
+        NA_CK(launch_link_table(link_poses, d_cams, d_envs, Wn, sen.xf_base, xf, v.status, st), "link table");
         ProjParams P{};
-        P.G = G;
+        P.n_gauss = v.D.n;
         P.p0 = v.D.p0;
         P.p1 = v.D.p1;
         P.p2 = v.D.p2;
         P.p3 = v.D.p3;
         P.sh = v.D.sh;
+        P.blocks = d_blocks;
+        P.envs = d_envs;
+        P.cams = d_cams;
         P.xf = xf;
-        P.cams = cams_dev;
-        P.L1 = L + 1;
-        P.We = Wn;
         P.r0 = reinterpret_cast<float4*>(base + y.r0);
         P.r1 = reinterpret_cast<float4*>(base + y.r1);
         P.r2 = reinterpret_cast<float4*>(base + y.r2);
         P.r3 = reinterpret_cast<uint4*>(base + y.r3);
         P.mask = reinterpret_cast<uint32_t*>(base + y.mask);
-        P.mask_words = mask_words;
         P.dbg_hxy = nullptr;
-        const unsigned gx = (unsigned)((G + 255) / 256);
-        int gy = (int)((4864 + gx - 1) / gx);
-        if (gy < 1) gy = 1;
-        if (gy > Wn) gy = Wn;
-        P.env_group = (Wn + gy - 1) / gy;
-        gy = (Wn + P.env_group - 1) / P.env_group;
-        NA_CK(launch_project(v.D, P, dim3(gx, (unsigned)gy), st), "projection");
+        NA_CK(launch_project(v.D, P, nb, st), "projection");
         uint32_t* counts = reinterpret_cast<uint32_t*>(base + y.counts);
         uint32_t* off = reinterpret_cast<uint32_t*>(base + y.off);
         uint32_t* cursor = reinterpret_cast<uint32_t*>(base + y.cursor);
         auto* env_total = reinterpret_cast<unsigned long long*>(base + y.env_total);
         auto* env_base = reinterpret_cast<unsigned long long*>(base + y.env_base);
-        NA_CK(cudaMemsetAsync(counts, 0, (size_t)Wn * T * 4, st), "clear counts");
+        NA_CK(cudaMemsetAsync(counts, 0, (size_t)sen.tile_base * 4, st), "clear counts");
         BinParams B{};
-        B.G = G;
-        B.mask_words = mask_words;
+        B.envs = d_envs;
         B.mask = P.mask;
         B.r3 = P.r3;
         B.e_begin = 0;
-        B.tile_w = v.tile_w;
-        B.tile_h = v.tile_h;
-        B.ntx = ntx;
-        B.T = T;
+        B.tile_w = tw;
+        B.tile_h = th;
+        B.words_per_block = kWordsPerBlock;
         B.counts = counts;
         B.off_local = off;
         B.env_base = env_base;
         B.cursor = cursor;
-        B.words_per_block = 256;  // 8 warps x 32 mask words (8192 Gaussians)
-        NA_CK(launch_count(B, Wn, st, (size_t)T * 4), "count");
-        NA_CK(launch_scan(counts, off, env_total, env_base, Wn, T, st), "scan");
+        B.status = v.status;
+        NA_CK(launch_count(B, Wn, max_words, max_T, st), "count");
+        NA_CK(launch_scan(d_envs, counts, off, env_total, env_base, Wn, st), "scan");
+        unsigned long long eb[kMaxWave + 1];
         NA_CK(cudaMemcpyAsync(eb, env_base, sizeof(unsigned long long) * (Wn + 1), cudaMemcpyDeviceToHost, st),
               "read totals");
         NA_CK(cudaStreamSynchronize(st), "sync totals");
@@ -216,12 +247,19 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
                          "no-allocation scratch too small: %lld intersection keys need %lld bytes, %lld are free "
                          "(use gs_render_batch)",
                          (long long)eb[Wn], (long long)need, (long long)(kNoAllocBytes - y.pairs));
-        NA_CK(cudaMemsetAsync(cursor, 0, (size_t)Wn * T * 4, st), "clear cursors");
+        NA_CK(cudaMemsetAsync(cursor, 0, (size_t)sen.tile_base * 4, st), "clear cursors");
         B.pair_base = 0;
+        B.pair_cap = (kNoAllocBytes - y.pairs) / 8;
         B.pairs = reinterpret_cast<unsigned long long*>(base + y.pairs);
-        NA_CK(launch_scatter(B, Wn, st, (size_t)T * 8), "scatter");
+        NA_CK(launch_scatter(B, Wn, max_words, max_T, st), "scatter");
         CompParams C{};
-        C.G = G;
+        C.envs = d_envs;
+        C.e_begin = 0;
+        C.e_end = Wn;
+        C.item_begin = 0;
+        C.item_end = sen.tile_base;
+        C.chunk = 1;
+        C.work = reinterpret_cast<unsigned int*>(base + y.work);
         C.r0 = P.r0;
         C.r1 = P.r1;
         C.r2 = P.r2;
@@ -229,21 +267,19 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
         C.off_local = off;
         C.env_base = env_base;
         C.pair_base = 0;
+        C.pair_cap = B.pair_cap;
         C.pairs = B.pairs;
         C.dbg_sorted = nullptr;
         C.neval = nullptr;
-        C.e_begin = 0;
-        C.W = W;
-        C.H = H;
-        C.tile_w = v.tile_w;
-        C.tile_h = v.tile_h;
-        C.ntx = ntx;
-        C.T = T;
+        C.tile_w = tw;
+        C.tile_h = th;
         C.rgb = rgb + (size_t)e0 * px * 3;
         C.depth = depth + (size_t)e0 * px;
         C.alpha = alpha ? alpha + (size_t)e0 * px : nullptr;
         C.status = v.status;
-        NA_CK(launch_composite(C, Wn, st), "composite");
+        NA_CK(cudaMemsetAsync(C.work, 0, 4, st), "clear work counter");
+        int ctas = 0;
+        NA_CK(launch_composite(C, st, &ctas), "composite");
     }
     return GS_OK;
 }

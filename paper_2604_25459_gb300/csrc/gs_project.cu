@@ -133,16 +133,21 @@ cudaError_t launch_prep(const float* mean, const float* quat, const void* log_sc
 }
 
 // ------------------------------------------------------------------ A1: link composition (RLGK)
-// For env e and frame f (f = 0: background/world, f = l+1: link l):
+// For env e and frame f (f = 0: background/world, f = 1 + l - link_begin: link l):
 //   M = [R_c R_l | R_c t_l + t_c]  (camera <- link), o = -M_R^T M_t (camera
 //   centre in the link frame, so that normalize(mu - o) is the view direction
 //   rotated into the link frame).
 
-__global__ void k_link_table(const float* poses, const gs_camera* cams, int We, int nl, LinkXf* out,
-                             uint32_t* status) {
+__global__ void k_link_table(const float* poses, const gs_camera* cams, const EnvInfo* envs, int We, int n_items,
+                             LinkXf* out, uint32_t* status) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= We * (nl + 1)) return;
-    const int e = idx / (nl + 1), f = idx % (nl + 1);
+    if (idx >= n_items) return;
+    int lo = 0, hi = We - 1;  // env: last e with envs[e].xf_base <= idx
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (envs[mid].xf_base <= idx) lo = mid; else hi = mid - 1;
+    }
+    const int e = lo, f = idx - envs[e].xf_base;
     const gs_camera& c = cams[e];
     float Rc[9];
     quat_rot<float>(c.q_cw[0], c.q_cw[1], c.q_cw[2], c.q_cw[3], Rc);
@@ -152,7 +157,7 @@ __global__ void k_link_table(const float* poses, const gs_camera* cams, int We, 
         for (int k = 0; k < 9; ++k) M[k] = Rc[k];
         for (int k = 0; k < 3; ++k) t[k] = tc[k];
     } else {
-        const float* P = poses + ((size_t)e * nl + (f - 1)) * 7;
+        const float* P = poses + (size_t)(envs[e].pose_base + (f - 1)) * 7;
         float Rl[9];
         bool ok = quat_rot<float>(P[0], P[1], P[2], P[3], Rl);
         float tl[3] = {P[4], P[5], P[6]};
@@ -176,11 +181,10 @@ __global__ void k_link_table(const float* poses, const gs_camera* cams, int We, 
     out[idx] = X;
 }
 
-cudaError_t launch_link_table(const float* poses, const gs_camera* cams, int We, int n_links, LinkXf* out,
-                              uint32_t* status, cudaStream_t st) {
-    const int n = We * (n_links + 1);
-    if (n == 0) return cudaSuccess;
-    k_link_table<<<(n + 127) / 128, 128, 0, st>>>(poses, cams, We, n_links, out, status);
+cudaError_t launch_link_table(const float* poses, const gs_camera* cams, const EnvInfo* envs, int We, int n_items,
+                              LinkXf* out, uint32_t* status, cudaStream_t st) {
+    if (n_items == 0 || We == 0) return cudaSuccess;
+    k_link_table<<<(n_items + 127) / 128, 128, 0, st>>>(poses, cams, envs, We, n_items, out, status);
     return cudaGetLastError();
 }
 
@@ -221,6 +225,26 @@ __device__ __forceinline__ void ewa_factor(const LinkXf& X, const float4& a0, co
     C = m1x * m1x + m1y * m1y + m1z * m1z;
     const T kx = m0y * m1z - m0z * m1y, ky = m0z * m1x - m0x * m1z, kz = m0x * m1y - m0y * m1x;
     K = kx * kx + ky * ky + kz * kz;
+}
+
+// Near-degenerate 2D covariance (a thin Gaussian seen edge-on): the factor,
+// its products and the scaled conic factor in FP64.  Kept out of line so the
+// common FP32 path does not carry its registers.
+__device__ __noinline__ void conic_factor_fp64(const LinkXf& X, const float4& a0, const float4& a1, const float4& a2,
+                                               const float4& a3, float fx, float fy, float limxn, float limxp,
+                                               float limyn, float limyp, float& l00, float& l01, float& l11, float& cA,
+                                               float& cC) {
+    constexpr double kS = 0.84932180028801907;  // sqrt(0.5 log2(e))
+    double dA, dB, dC, dK;
+    ewa_factor<double>(X, a0, a1, a2, a3, fx, fy, limxn, limxp, limyn, limyp, dA, dB, dC, dK);
+    const double eA = dA + 0.3, eC = dC + 0.3;
+    const double det = dK + 0.3 * (dA + dC) + 0.09;
+    const double rc = 1.0 / sqrt(eC);
+    l00 = (float)(kS * sqrt(eC / det));
+    l01 = (float)(-kS * dB * rc / sqrt(det));
+    l11 = (float)(kS * rc);
+    cA = (float)eA;
+    cC = (float)eC;
 }
 
 // Real SH basis through degree D in the 3DGS order (k = l*l + l + m), with the
@@ -320,10 +344,13 @@ __device__ __forceinline__ bool pixel_range(float c, float h, int n, int& lo, in
 template <int D, int DT>
 __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
     constexpr int NV = 3 * (D + 1) * (D + 1);
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool act = g < P.G;
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = g - lane;
+    const ProjBlock blk = P.blocks[blockIdx.x];
+    const int t = threadIdx.x;
+    const bool act = t < blk.n;
+    const int lane = t & 31;
+    const long long g = blk.g_first + t;
+    const unsigned int local = blk.local_first + (unsigned)t;
+    const bool warp_live = (t - lane) < blk.n;  // the warp owns visibility word local/32
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
     if (act) {
         a0 = __ldg(P.p0 + g);
@@ -331,25 +358,27 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
         a2 = __ldg(P.p2 + g);
         a3 = __ldg(P.p3 + g);
     }
-    const int li = __float_as_int(a3.w);
+    const int li = __float_as_int(a3.w) - blk.lb;  // frame offset within the env's link table
     const float qstar = a3.y;
     const bool live = act && qstar >= 0.0f;
     const float trace = a3.z;  // trace(Sigma) >= its largest eigenvalue (rotation-invariant)
     float sh[NV];
-    const int e0 = blockIdx.y * P.env_group;
-    const int e1 = min(P.We, e0 + P.env_group);
-    for (int el = e0; el < e1; ++el) {
+    for (int el = blk.e0; el < blk.e1; ++el) {
         bool vis = false;
+        const EnvInfo* E = P.envs + el;
+        const int xfb = __ldg(&E->xf_base);
         if (live) {
-            const LinkXf* Xp = P.xf + (size_t)el * P.L1 + li;
+            const LinkXf* Xp = P.xf + xfb + li;
+            // depth first: most (env, Gaussian) pairs stop at the near-plane test,
+            // so only the z row of the transform and the near plane are loaded here
             LinkXf X;
-            X.r0 = __ldg(&Xp->r0);
-            X.r1 = __ldg(&Xp->r1);
             X.r2 = __ldg(&Xp->r2);
             const gs_camera* cam = P.cams + el;
             const float near = __ldg(&cam->near_plane);
             const float mz = X.r2.x * a0.x + X.r2.y * a0.y + X.r2.z * a0.z + X.r2.w;
             if (mz > near) {
+                X.r0 = __ldg(&Xp->r0);
+                X.r1 = __ldg(&Xp->r1);
                 const float mx = X.r0.x * a0.x + X.r0.y * a0.y + X.r0.z * a0.z + X.r0.w;
                 const float my = X.r1.x * a0.x + X.r1.y * a0.y + X.r1.z * a0.z + X.r1.w;
                 const float fx = __ldg(&cam->fx), fy = __ldg(&cam->fy);
@@ -387,18 +416,8 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                         l01 = -kS * B * rc / sqrtf(det);
                         l11 = kS * rc;
                     } else {
-                        // near-degenerate 2D covariance (a thin Gaussian seen edge-on):
-                        // the factor, its products and the conic factor in FP64
-                        double dA, dB, dC, dK;
-                        ewa_factor<double>(X, a0, a1, a2, a3, fx, fy, limxn, limxp, limyn, limyp, dA, dB, dC, dK);
-                        const double eA = dA + 0.3, eC = dC + 0.3;
-                        const double det = dK + 0.3 * (dA + dC) + 0.09;
-                        const double rc = 1.0 / sqrt(eC);
-                        l00 = (float)((double)kS * sqrt(eC / det));
-                        l01 = (float)(-(double)kS * dB * rc / sqrt(det));
-                        l11 = (float)((double)kS * rc);
-                        cA = (float)eA;
-                        cC = (float)eC;
+                        conic_factor_fp64(X, a0, a1, a2, a3, fx, fy, limxn, limxp, limyn, limyp, l00, l01, l11, cA,
+                                          cC);
                     }
                     const bool ok = true;
                     const float hx = sqrtf(qstar * cA) * 1.0001f;
@@ -407,7 +426,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                     if (ok && pixel_range(u, hx, W, i0, i1) && pixel_range(v, hy, H, j0, j1)) {
                         // reloaded per visible env (L1/L2 hits): keeping all SH
                         // coefficients live across the env loop costs more occupancy
-                        load_sh<D, DT>(P.sh, P.G, g, sh);
+                        load_sh<D, DT>(P.sh, P.n_gauss, g, sh);
                         const float4 O = __ldg(&Xp->o);
                         float dx = a0.x - O.x, dy = a0.y - O.y, dz = a0.z - O.z;
                         const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
@@ -418,7 +437,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                         sh_colour<D>(sh, dx, dy, dz, r, gg, b);
                         const uint32_t rx = (uint32_t)i0 | ((uint32_t)i1 << 16);
                         const uint32_t ry = (uint32_t)j0 | ((uint32_t)j1 << 16);
-                        const size_t ri = (size_t)el * P.G + g;
+                        const size_t ri = (size_t)__ldg(&E->rec_base) + local;
                         P.r0[ri] = make_float4(u, v, a0.w, mz);
                         P.r1[ri] = make_float4(l00, l01, l11, __uint_as_float(rx));
                         P.r2[ri] = make_float4(r, gg, b, __uint_as_float(ry));
@@ -430,25 +449,26 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
             }
         }
         const uint32_t m = __ballot_sync(0xffffffffu, vis);
-        if (lane == 0 && gw < P.G) P.mask[(size_t)el * P.mask_words + (gw >> 5)] = m;
+        if (lane == 0 && warp_live) P.mask[(size_t)__ldg(&E->mask_base) + (local >> 5)] = m;
     }
 }
 
 template <int D>
-static void launch_project_d(const DevGaussians& Dg, const ProjParams& P, dim3 grid, cudaStream_t st) {
+static void launch_project_d(const DevGaussians& Dg, const ProjParams& P, int n_blocks, cudaStream_t st) {
     switch (Dg.dtype) {
-        case GS_F32: k_project<D, GS_F32><<<grid, 256, 0, st>>>(P); break;
-        case GS_BF16: k_project<D, GS_BF16><<<grid, 256, 0, st>>>(P); break;
-        default: k_project<D, GS_F16><<<grid, 256, 0, st>>>(P); break;
+        case GS_F32: k_project<D, GS_F32><<<n_blocks, 256, 0, st>>>(P); break;
+        case GS_BF16: k_project<D, GS_BF16><<<n_blocks, 256, 0, st>>>(P); break;
+        default: k_project<D, GS_F16><<<n_blocks, 256, 0, st>>>(P); break;
     }
 }
 
-cudaError_t launch_project(const DevGaussians& Dg, const ProjParams& P, dim3 grid, cudaStream_t st) {
+cudaError_t launch_project(const DevGaussians& Dg, const ProjParams& P, int n_blocks, cudaStream_t st) {
+    if (n_blocks == 0) return cudaSuccess;
     switch (Dg.sh_degree) {
-        case 0: launch_project_d<0>(Dg, P, grid, st); break;
-        case 1: launch_project_d<1>(Dg, P, grid, st); break;
-        case 2: launch_project_d<2>(Dg, P, grid, st); break;
-        default: launch_project_d<3>(Dg, P, grid, st); break;
+        case 0: launch_project_d<0>(Dg, P, n_blocks, st); break;
+        case 1: launch_project_d<1>(Dg, P, n_blocks, st); break;
+        case 2: launch_project_d<2>(Dg, P, n_blocks, st); break;
+        default: launch_project_d<3>(Dg, P, n_blocks, st); break;
     }
     return cudaGetLastError();
 }

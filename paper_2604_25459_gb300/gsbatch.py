@@ -48,6 +48,19 @@ class GsTimings(C.Structure):
     _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6)]
 
 
+class GsPlanInfo(C.Structure):
+    _fields_ = [("tile_w", C.c_int), ("tile_h", C.c_int), ("chunk", C.c_int), ("waves", C.c_int),
+                ("graph", C.c_int), ("tuned_candidates", C.c_int), ("tuned_ms", C.c_double), ("regrows", C.c_int),
+                ("key_capacity", C.c_int64), ("scratch_bytes", C.c_int64)]
+
+
+# gs_env in include/gsbatch.h: camera, link range, pose offset, pixel offset (80 bytes)
+ENV_DTYPE = np.dtype([("cam", CAMERA_DTYPE), ("link_begin", "<i4"), ("link_end", "<i4"), ("pose_offset", "<i8"),
+                      ("pixel_offset", "<i8")])
+assert ENV_DTYPE.itemsize == 80
+PLAN_AUTOTUNE, PLAN_GRAPH = 1, 2
+
+
 _lib = None
 
 # name -> (restype, argtypes); the exported C ABI declared in include/gsbatch.h
@@ -57,6 +70,11 @@ _SIGS = {
     "gs_render_batch": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_render_batch_host": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_render_batch_noalloc": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
+    "gs_render_batch_v": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
+    "gs_plan_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "gs_plan_launch": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
+    "gs_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(GsPlanInfo)]),
+    "gs_plan_destroy": (None, [C.c_void_p]),
     "gs_scene_set_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "gs_scene_set_budget": (C.c_int, [C.c_void_p, C.c_int64]),
     "gs_scene_set_wave": (C.c_int, [C.c_void_p, C.c_int]),
@@ -250,6 +268,20 @@ class Scene:
                                           _ptr(alpha), _stream_handle(stream)))
         return rgb, depth, alpha
 
+    def render_v(self, envs: np.ndarray, link_poses, rgb, depth, alpha=None, stream=None):
+        """Uneven batch (gs_render_batch_v): envs is a numpy ENV_DTYPE array (host);
+        outputs are flat CUDA tensors addressed by each env's pixel_offset."""
+        envs = np.ascontiguousarray(envs, dtype=ENV_DTYPE)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        _check(lib().gs_render_batch_v(self._h, int(envs.shape[0]), _ptr(envs), _ptr(link_poses), _ptr(rgb),
+                                       _ptr(depth), _ptr(alpha), _stream_handle(stream)))
+        return rgb, depth, alpha
+
+    def plan(self, envs: np.ndarray, autotune: bool = True, graph: bool = True) -> "Plan":
+        return Plan(self, envs, (PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0))
+
     def debug_records(self, env: int, n: int) -> dict:
         out = dict(visible=np.zeros(n, np.uint8), u=np.zeros(n, np.float32), v=np.zeros(n, np.float32),
                    hx=np.zeros(n, np.float32), hy=np.zeros(n, np.float32), z=np.zeros(n, np.float32),
@@ -285,6 +317,58 @@ class Scene:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Plan:
+    """A fixed uneven batch rendered repeatedly (gs_plan_*): autotuned on the
+    first launch, then replayed from a captured CUDA graph."""
+
+    def __init__(self, scene: Scene, envs: np.ndarray, flags: int):
+        self.scene = scene
+        self.envs = np.ascontiguousarray(envs, dtype=ENV_DTYPE)
+        self._h = C.c_void_p()
+        _check(lib().gs_plan_create(scene._h, int(self.envs.shape[0]), _ptr(self.envs), flags, C.byref(self._h)))
+        self._alive = True
+
+    def launch(self, link_poses, rgb, depth, alpha=None, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        _check(lib().gs_plan_launch(self._h, _ptr(link_poses), _ptr(rgb), _ptr(depth), _ptr(alpha),
+                                    _stream_handle(stream)))
+
+    def info(self) -> dict:
+        i = GsPlanInfo()
+        _check(lib().gs_plan_get_info(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in GsPlanInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_alive", False):
+            lib().gs_plan_destroy(self._h)
+            self._alive = False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_envs(cams: np.ndarray, link_ranges=None, pose_offsets=None) -> np.ndarray:
+    """ENV_DTYPE array for cameras of any resolutions, packed back to back in
+    the outputs; link_ranges [E,2] (default: no links), pose_offsets [E]."""
+    cams = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+    E = len(cams)
+    envs = np.zeros(E, dtype=ENV_DTYPE)
+    envs["cam"] = cams
+    if link_ranges is not None:
+        lr = np.asarray(link_ranges, dtype=np.int64).reshape(E, 2)
+        envs["link_begin"], envs["link_end"] = lr[:, 0], lr[:, 1]
+    if pose_offsets is not None:
+        envs["pose_offset"] = np.asarray(pose_offsets, dtype=np.int64)
+    px = cams["width"].astype(np.int64) * cams["height"].astype(np.int64)
+    envs["pixel_offset"] = np.concatenate([[0], np.cumsum(px)[:-1]])
+    return envs
 
 
 def scene_from_workload(w, dtype: str = "f32", sh_degree: int = 3) -> Scene:

@@ -353,3 +353,100 @@ def quantize(g: Gaussians, dtype: str) -> tuple:
     widened = Gaussians(g.mean, g.quat, from_half(stored["log_scale"], dtype),
                         from_half(stored["opacity"], dtype), from_half(stored["sh"], dtype))
     return stored, widened
+
+
+# ---------------------------------------------------------------- batched uneven workload (c3)
+
+C3_RESOLUTIONS = ((64, 64), (128, 128), (320, 240), (640, 480))
+C3_PROBS = (0.3, 0.3, 0.2, 0.2)
+
+
+def focal_for(width: int, height: int) -> float:
+    """Focal length keeping the c1/c2 field of view: f = 500 at 640 px width for
+    4:3 images, f = 100 at 128 px for square ones."""
+    return 500.0 * width / 640.0 if width != height else 100.0 * width / 128.0
+
+
+def c3_counts(n_envs: int, seed: int, lo: int = 10_000, hi: int = 200_000) -> np.ndarray:
+    """Per-env object Gaussian counts, log-uniform in [lo, hi]."""
+    rng = _rng(seed, 9)
+    return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), n_envs))).astype(np.int64).clip(lo, hi)
+
+
+def c3_resolutions(n_envs: int, seed: int) -> np.ndarray:
+    rng = _rng(seed, 10)
+    return rng.choice(len(C3_RESOLUTIONS), size=n_envs, p=C3_PROBS)
+
+
+def _c3_object(seed: int, e: int, n: int, sigma: float):
+    rng = _rng(seed, 8, e)
+    mean = rng.normal(0.0, sigma, size=(n, 3))
+    return (mean,) + _attributes(rng, n)
+
+
+@dataclasses.dataclass
+class UnevenWorkload:
+    """Envs of different resolutions, each rendering the shared background plus
+    its own object (link e of the scene, pose e)."""
+
+    name: str
+    background: Gaussians
+    link_offsets: np.ndarray  # int64 [E+1]: object of env e = links[off[e]:off[e+1]]
+    links: Gaussians
+    link_poses: np.ndarray  # f32 [E][7], object pose of env e (link -> world)
+    cams: np.ndarray  # CAMERA_DTYPE [E], mixed resolutions
+
+    @property
+    def n_envs(self) -> int:
+        return int(self.cams.shape[0])
+
+    def env(self, e: int) -> Workload:
+        """Env e alone, as a one-link workload (the same bytes)."""
+        a, b = int(self.link_offsets[e]), int(self.link_offsets[e + 1])
+        return Workload(f"{self.name}[{e}]", self.background, np.array([0, b - a], np.int64), self.links.slice(a, b),
+                        self.link_poses[e:e + 1, None, :].copy(), self.cams[e:e + 1].copy())
+
+
+def make_c3(n_envs: int = 4096, seed: int = 0, n_bg: int = 300_000, count_range=(10_000, 200_000),
+            sigma: float = 0.15, threads: int = 16) -> UnevenWorkload:
+    """The batched uneven form: a shared room-shell background of n_bg Gaussians;
+    env e has its own object of log-uniform size in count_range (means
+    N(0, sigma) in the object frame, the c0 attribute distributions) placed in
+    front of a jittered head camera, at a resolution drawn from {64x64, 128x128,
+    320x240, 640x480} with probabilities {.3, .3, .2, .2}.  Each env's object
+    comes from its own seeded stream, so env e can be regenerated alone."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    bg = make_room_shell(n_bg, seed)
+    counts = c3_counts(n_envs, seed, *count_range)
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    N = int(offsets[-1])
+    mean = np.empty((N, 3), np.float32)
+    quat = np.empty((N, 4), np.float32)
+    ls = np.empty((N, 3), np.float32)
+    op = np.empty(N, np.float32)
+    sh = np.empty((N, SH_COEFFS, 3), np.float32)
+
+    def fill(e):
+        a, b = offsets[e], offsets[e + 1]
+        m, q, l, o, s = _c3_object(seed, e, int(b - a), sigma)
+        mean[a:b], quat[a:b], ls[a:b], op[a:b], sh[a:b] = m, q, l, o, s
+
+    with ThreadPoolExecutor(max(1, threads)) as ex:
+        list(ex.map(fill, range(n_envs)))
+    links = Gaussians(mean, quat, ls, op, sh)
+    rng = _rng(seed, 11)
+    pos = np.stack([0.6 + rng.uniform(-0.2, 0.2, n_envs), rng.uniform(-0.3, 0.3, n_envs),
+                    0.6 + rng.uniform(0.0, 0.3, n_envs)], 1)
+    q = rng.normal(size=(n_envs, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    q *= np.where(q[:, :1] < 0, -1.0, 1.0)
+    poses = np.concatenate([q, pos], 1).astype(np.float32)
+    res = c3_resolutions(n_envs, seed)
+    cams = np.zeros(n_envs, dtype=CAMERA_DTYPE)
+    for k, (W, H) in enumerate(C3_RESOLUTIONS):
+        idx = np.nonzero(res == k)[0]
+        if len(idx):
+            c = head_cameras(n_envs, seed, W, H, focal_for(W, H))[idx]
+            cams[idx] = c
+    return UnevenWorkload("c3", bg, offsets, links, poses, cams)
