@@ -282,6 +282,94 @@ gs_status gs_debug_copy_tiles(gs_scene s, int env, uint32_t* counts, int64_t n_c
 /* Destroy a scene and free its device memory (NULL is a no-op). */
 void gs_scene_destroy(gs_scene s);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop over resident scenes.  The paper renders RGB-D for every
+ * environment as the simulator steps (Sec. III-A, Sec. III-C); here envs step at
+ * their own pace, each step is a render request, and a scheduler thread in
+ * the library batches them continuously:
+ *   - scenes (gs_scene, attached links) and per-env state (camera, link
+ *     range, the RGB and depth images) stay resident on the device;
+ *   - a request carries the env's link poses (host, copied at submit) and an
+ *     arrival time; requests that have arrived are admitted, oldest first,
+ *     into batches of one scene whose envs are idle (an env has at most one
+ *     request in flight, so its results come back in submission order);
+ *   - a batch is admitted when a stream slot is free and its estimated
+ *     device working set (records, tile tables and intersection keys, the
+ *     keys estimated from earlier batches of the same scene and resolution)
+ *     fits the HBM budget beside the batches in flight; one batch holds at
+ *     most budget / max_inflight (each slot keeps its scratch, so all slots
+ *     together stay within the budget); a request that alone exceeds the
+ *     budget still runs, alone, when nothing else is in flight;
+ *   - each batch runs the full render on its own CUDA stream and scratch, so
+ *     batches overlap on the device; a host callback on the stream records
+ *     its completion time.
+ * A request's output is bit-identical to rendering its env alone with
+ * gs_render_batch_v at the server's tile shape.  While a server runs, its
+ * scenes must not be rendered or destroyed by other calls.
+ * Times are seconds since gs_server_start (steady clock). */
+typedef struct gs_server_s* gs_server;
+
+typedef struct {
+    int64_t budget_bytes;  /* device working-set budget of the batches in flight (>= 1 MiB) */
+    int max_inflight;      /* stream slots, 1..64 */
+    int max_batch_envs;    /* requests per batch, >= 1 */
+    int tile_w, tile_h;    /* tile shape: 8x8, 16x8, 16x16 or 32x8 */
+} gs_server_config;
+
+typedef struct {
+    int64_t request_id;
+    int env_id;
+    int status;            /* 0 done; 1 cancelled; a negative gs_status on failure */
+    double arrival_s;      /* scheduled arrival */
+    double admit_s;        /* admitted into a batch (-1 if never) */
+    double done_s;         /* completed on the device (host callback), or cancelled */
+} gs_request_result;
+
+typedef struct {
+    int64_t submitted, completed, cancelled, batches;
+    int64_t peak_inflight_bytes;  /* largest estimated working set in flight */
+    int32_t max_concurrent;       /* most batches in flight at once */
+    int32_t max_batch;            /* most requests in one batch */
+} gs_server_stats;
+
+/* Create a server on the current device (stream slots created here; scratch
+ * grows on first use).  GS_ERR_INVALID for a bad config. */
+gs_status gs_server_create(const gs_server_config* cfg, gs_server* out);
+/* Register a scene (borrowed; must outlive the server).  Before start only. */
+gs_status gs_server_add_scene(gs_server sv, gs_scene scene, int* scene_id);
+/* Register an env instance of a scene: camera (copied), links [link_begin,
+ * link_end) of the scene.  Before start only. */
+gs_status gs_server_add_env(gs_server sv, int scene_id, const gs_camera* cam, int link_begin, int link_end,
+                            int* env_id);
+/* Allocate the resident outputs and start the scheduler thread. */
+gs_status gs_server_start(gs_server sv);
+/* Submit a render request for env_id: link_poses host f32 [link_end -
+ * link_begin][7] (copied; may be NULL for an env without links), arrival in
+ * seconds since start (< 0: now).  Requests may be submitted before start
+ * (open-loop arrival schedules).  request_id may be NULL. */
+gs_status gs_server_submit(gs_server sv, int env_id, const float* link_poses, double arrival_s,
+                           int64_t* request_id);
+/* Cancel a request that has not been admitted yet: it completes with status 1.
+ * GS_ERR_INVALID if it is unknown, admitted or finished. */
+gs_status gs_server_cancel(gs_server sv, int64_t request_id);
+/* Take up to max_results finished requests (completion order). */
+gs_status gs_server_poll(gs_server sv, gs_request_result* out, int max_results, int* n_out);
+/* Wait until every submitted request has finished (GS_ERR_TIMEOUT after
+ * timeout_s), then read the scenes' device status words (GS_ERR_DEVICE as
+ * gs_scene_sync_status).  A failed batch's CUDA error is returned here. */
+gs_status gs_server_drain(gs_server sv, double timeout_s);
+gs_status gs_server_get_stats(gs_server sv, gs_server_stats* out);
+/* Seconds since gs_server_start (0 before start, -1 for NULL): the clock of
+ * arrival_s, for scheduling arrivals relative to now. */
+double gs_server_now(gs_server sv);
+/* Device pointers to env_id's resident outputs: rgb f32 [H][W][3], depth f32
+ * [H][W] (owned by the server; valid until destroy).  After start only; read
+ * them when the env has no request in flight. */
+gs_status gs_server_env_output(gs_server sv, int env_id, float** rgb, float** depth);
+/* Stop the scheduler (requests not yet admitted are dropped), wait for the
+ * batches in flight and free everything the server owns (NULL is a no-op). */
+void gs_server_destroy(gs_server sv);
+
 /* Thread-local description of the last failure ("" if none). */
 const char* gs_last_error(void);
 

@@ -8,11 +8,20 @@
 // gs_composite.cu; this file validates arguments, plans waves of environments
 // against the scratch budget and orders the launches.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
+#include <tuple>
 #include <vector>
 
 #include "gs_internal.cuh"
@@ -1414,6 +1423,446 @@ void gs_scene_destroy(gs_scene s) {
         if (s->ev_copied[k]) cudaEventDestroy(s->ev_copied[k]);
     }
     delete s;
+}
+
+}  // extern "C"
+
+// ================================================================== serving
+// A request loop with continuous batching (the serving form of the renderer):
+// scenes and per-env state (camera, output image) stay resident; requests
+// carry poses and an arrival time; a scheduler thread admits arrived requests
+// into per-scene batches as stream slots and budget allow, launches each batch
+// on its own CUDA stream (so batches overlap on the device) and records the
+// completion time with a host callback on that stream.
+
+struct gs_server_s {
+    gs_server_config cfg{};
+    int device = 0;
+    struct SceneRec {
+        gs_scene s;
+        DevBuf rgb, depth;       // resident output images of the scene's envs
+        int64_t px = 0;          // pixels allocated so far
+    };
+    std::vector<std::unique_ptr<SceneRec>> scenes;
+    struct EnvRec {
+        int scene;
+        gs_camera cam;
+        int link_begin, link_end;
+        int64_t pix_off;
+        bool busy = false;
+    };
+    std::vector<EnvRec> envs;
+    struct Req {
+        int env;
+        double arrival;
+        std::vector<float> poses;
+        double admit = -1, done = -1;
+        int status = 0;
+    };
+    std::vector<Req> reqs;
+    std::deque<int64_t> scheduled;  // not yet arrived, by arrival time
+    std::deque<int64_t> pending;    // arrived, not admitted
+    std::deque<int64_t> completed;  // done, not yet polled
+    struct Slot {
+        cudaStream_t st = nullptr;
+        Scratch sc;
+        DevBuf poses;
+        float* h_poses = nullptr;   // pinned staging
+        size_t h_cap = 0;
+        bool busy = false;
+        std::vector<int64_t> batch;
+        double bytes = 0;
+        std::atomic<int> done{0};
+        double t_done = 0;
+        std::chrono::steady_clock::time_point t0;
+    };
+    std::vector<std::unique_ptr<Slot>> slots;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::atomic<bool> stop{false};
+    bool started = false;
+    std::chrono::steady_clock::time_point t0;
+    double inflight_bytes = 0;
+    gs_server_stats stats{};
+    std::map<std::tuple<int, int, int>, double> keys_ema;  // (scene, W, H) -> keys per env
+    std::string error;
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+void CUDART_CB server_slot_done(void* p) {
+    auto* sl = static_cast<gs_server_s::Slot*>(p);
+    sl->t_done = std::chrono::duration<double>(std::chrono::steady_clock::now() - sl->t0).count();
+    sl->done.store(1, std::memory_order_release);
+}
+
+double request_bytes(gs_server sv, const gs_server_s::EnvRec& ev) {
+    gs_scene s = sv->scenes[ev.scene]->s;
+    EnvSpec sp{&ev.cam, ev.link_begin, ev.link_end, 0, 0};
+    const int tw = sv->cfg.tile_w, th = sv->cfg.tile_h;
+    const double T = (double)((ev.cam.width + tw - 1) / tw) * ((ev.cam.height + th - 1) / th);
+    auto it = sv->keys_ema.find({ev.scene, ev.cam.width, ev.cam.height});
+    const double keys = it != sv->keys_ema.end() ? it->second : T * 2000.0;
+    return (double)env_bytes(s, sp, tw, th, false) + keys * 8.0 * 1.3;
+}
+
+// Launch one batch (requests of one scene) on a free slot.  Called by the
+// scheduler thread with the lock released.
+gs_status server_launch(gs_server sv, gs_server_s::Slot& sl, int scene, const std::vector<int64_t>& batch) {
+    auto& sr = *sv->scenes[scene];
+    gs_scene s = sr.s;
+    const int L = s->D.n_links;
+    const size_t n = batch.size();
+    const size_t pose_floats = std::max<size_t>(1, n * (size_t)L * 7);
+    if (pose_floats > sl.h_cap) {
+        if (sl.h_poses) cudaFreeHost(sl.h_poses);
+        sl.h_poses = nullptr;
+        CK(cudaMallocHost((void**)&sl.h_poses, pose_floats * 4), "alloc pinned poses");
+        sl.h_cap = pose_floats;
+    }
+    CK(sl.poses.ensure(pose_floats * 4), "alloc poses");
+    std::vector<EnvSpec> specs(n);
+    for (size_t i = 0; i < n; ++i) {
+        const auto& rq = sv->reqs[batch[i]];
+        const auto& ev = sv->envs[rq.env];
+        const int nl = ev.link_end - ev.link_begin;
+        if (nl > 0) memcpy(sl.h_poses + i * (size_t)L * 7, rq.poses.data(), sizeof(float) * nl * 7);
+        specs[i] = EnvSpec{&ev.cam, ev.link_begin, ev.link_end, (long long)i * L, (long long)ev.pix_off};
+    }
+    if (L > 0)
+        CK(cudaMemcpyAsync(sl.poses.p, sl.h_poses, n * (size_t)L * 28, cudaMemcpyHostToDevice, sl.st), "copy poses");
+    WaveTables wt{};
+    ST(upload_tables(s, specs, 0, (int)n, sv->cfg.tile_w, sv->cfg.tile_h, 0, sl.sc.envs, sl.sc.blocks, sl.sc.cams,
+                     sl.st, false, &wt));
+    int64_t launches = 0;
+    unsigned long long keys = 0;
+    ST(run_wave(s, sl.sc, wt, WaveIO{sl.poses.as<float>(), sr.rgb.as<float>(), sr.depth.as<float>(), nullptr, 0},
+                sv->cfg.tile_w, sv->cfg.tile_h, 1, 0, sl.st, false, &launches, &keys));
+    // keys per env of this resolution mix: running average per (scene, size)
+    std::map<std::tuple<int, int, int>, std::pair<double, int>> acc;
+    const double tiles_total = (double)wt.tiles;
+    for (size_t i = 0; i < n; ++i) {
+        const auto& ev = sv->envs[sv->reqs[batch[i]].env];
+        const double T = (double)wt.host_envs[i].T;
+        auto& a = acc[{ev.scene, ev.cam.width, ev.cam.height}];
+        a.first += tiles_total > 0 ? (double)keys * T / tiles_total : 0.0;
+        a.second += 1;
+    }
+    for (auto& kv : acc) {
+        const double per = kv.second.first / kv.second.second;
+        auto it = sv->keys_ema.find(kv.first);
+        if (it == sv->keys_ema.end()) sv->keys_ema[kv.first] = per;
+        else it->second = 0.8 * it->second + 0.2 * per;
+    }
+    sl.t0 = sv->t0;
+    CK(cudaLaunchHostFunc(sl.st, server_slot_done, &sl), "completion callback");
+    return GS_OK;
+}
+
+void server_loop(gs_server sv) {
+    cudaSetDevice(sv->device);
+    while (!sv->stop.load()) {
+        bool worked = false;
+        std::vector<std::pair<gs_server_s::Slot*, std::pair<int, std::vector<int64_t>>>> launch;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            const double t = sv->now();
+            while (!sv->scheduled.empty() && sv->reqs[sv->scheduled.front()].arrival <= t) {
+                sv->pending.push_back(sv->scheduled.front());
+                sv->scheduled.pop_front();
+            }
+            // completions
+            for (auto& sl : sv->slots) {
+                if (sl->busy && sl->done.load(std::memory_order_acquire)) {
+                    for (int64_t id : sl->batch) {
+                        auto& rq = sv->reqs[id];
+                        rq.done = sl->t_done;
+                        sv->envs[rq.env].busy = false;
+                        sv->completed.push_back(id);
+                        sv->stats.completed++;
+                    }
+                    sv->inflight_bytes -= sl->bytes;
+                    sl->busy = false;
+                    sl->batch.clear();
+                    worked = true;
+                }
+            }
+            // admission: per-scene batches of arrived requests whose env is idle
+            int inflight = 0;
+            for (auto& sl : sv->slots) inflight += sl->busy ? 1 : 0;
+            for (auto& slp : sv->slots) {
+                if (slp->busy || sv->pending.empty()) continue;
+                int scene = -1;
+                std::vector<int64_t> batch;
+                double bytes = 0;
+                std::deque<int64_t> keep;
+                std::vector<char> taken(sv->envs.size(), 0);
+                while (!sv->pending.empty()) {
+                    const int64_t id = sv->pending.front();
+                    sv->pending.pop_front();
+                    auto& rq = sv->reqs[id];
+                    auto& ev = sv->envs[rq.env];
+                    const bool fits_scene = scene < 0 || ev.scene == scene;
+                    const double b = request_bytes(sv, ev);
+                    // a batch holds at most budget / slots (a slot's scratch keeps its
+                    // high-water mark, so the slots together stay within the budget);
+                    // the batches in flight together at most the budget; a request
+                    // larger than that runs alone when nothing else is in flight
+                    const double budget = (double)sv->cfg.budget_bytes;
+                    const bool fits_budget =
+                        batch.empty() ? (sv->inflight_bytes + b <= budget || inflight == 0)
+                                      : (bytes + b <= budget / sv->cfg.max_inflight &&
+                                         sv->inflight_bytes + bytes + b <= budget);
+                    if (!ev.busy && !taken[rq.env] && fits_scene && fits_budget &&
+                        (int)batch.size() < sv->cfg.max_batch_envs) {
+                        scene = ev.scene;
+                        batch.push_back(id);
+                        bytes += b;
+                        taken[rq.env] = 1;
+                    } else {
+                        keep.push_back(id);
+                    }
+                }
+                sv->pending.swap(keep);
+                if (batch.empty()) break;
+                for (int64_t id : batch) {
+                    sv->reqs[id].admit = sv->now();
+                    sv->envs[sv->reqs[id].env].busy = true;
+                }
+                slp->busy = true;
+                slp->done.store(0);
+                slp->batch = batch;
+                slp->bytes = bytes;
+                sv->inflight_bytes += bytes;
+                sv->stats.batches++;
+                sv->stats.peak_inflight_bytes = std::max(sv->stats.peak_inflight_bytes, (int64_t)sv->inflight_bytes);
+                ++inflight;
+                sv->stats.max_concurrent = std::max(sv->stats.max_concurrent, inflight);
+                sv->stats.max_batch = std::max(sv->stats.max_batch, (int)batch.size());
+                launch.push_back({slp.get(), {scene, batch}});
+            }
+        }
+        for (auto& l : launch) {
+            gs_status st = server_launch(sv, *l.first, l.second.first, l.second.second);
+            worked = true;
+            if (st != GS_OK) {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                sv->error = g_err;
+                for (int64_t id : l.second.second) sv->reqs[id].status = (int)st;
+                // completes at once so the loop does not stall; the status tells
+                l.first->t_done = sv->now();
+                l.first->done.store(1);
+            }
+        }
+        if (!worked) {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait_for(lk, std::chrono::microseconds(20));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_server_create(const gs_server_config* cfg, gs_server* out) {
+    if (!out || !cfg) return fail(GS_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (cfg->budget_bytes < (1ll << 20)) return fail(GS_ERR_INVALID, "budget below 1 MiB");
+    if (cfg->max_inflight < 1 || cfg->max_inflight > 64) return fail(GS_ERR_INVALID, "max_inflight must be 1..64");
+    if (cfg->max_batch_envs < 1) return fail(GS_ERR_INVALID, "max_batch_envs must be >= 1");
+    if (!valid_tile(cfg->tile_w, cfg->tile_h)) return fail(GS_ERR_INVALID, "unsupported tile shape");
+    gs_server sv = new gs_server_s();
+    sv->cfg = *cfg;
+    cudaGetDevice(&sv->device);
+    for (int k = 0; k < cfg->max_inflight; ++k) {
+        auto sl = std::make_unique<gs_server_s::Slot>();
+        cudaError_t e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            gs_server_destroy(sv);
+            return cuda_fail(e, "server stream");
+        }
+        sv->slots.push_back(std::move(sl));
+    }
+    sv->t0 = std::chrono::steady_clock::now();
+    *out = sv;
+    return GS_OK;
+}
+
+gs_status gs_server_add_scene(gs_server sv, gs_scene s, int* scene_id) {
+    if (!sv || !s || !scene_id) return fail(GS_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->started) return fail(GS_ERR_INVALID, "scenes must be added before gs_server_start");
+    auto sr = std::make_unique<gs_server_s::SceneRec>();
+    sr->s = s;
+    sv->scenes.push_back(std::move(sr));
+    *scene_id = (int)sv->scenes.size() - 1;
+    return GS_OK;
+}
+
+gs_status gs_server_add_env(gs_server sv, int scene_id, const gs_camera* cam, int link_begin, int link_end,
+                            int* env_id) {
+    if (!sv || !cam || !env_id) return fail(GS_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->started) return fail(GS_ERR_INVALID, "envs must be added before gs_server_start");
+    if (scene_id < 0 || scene_id >= (int)sv->scenes.size()) return fail(GS_ERR_INVALID, "unknown scene %d", scene_id);
+    gs_scene s = sv->scenes[scene_id]->s;
+    ST(check_cam(*cam, (int)sv->envs.size()));
+    if (link_begin < 0 || link_end < link_begin || link_end > s->D.n_links)
+        return fail(GS_ERR_INVALID, "link range [%d, %d) outside [0, %d]", link_begin, link_end, s->D.n_links);
+    const int ntx = (cam->width + sv->cfg.tile_w - 1) / sv->cfg.tile_w;
+    const int nty = (cam->height + sv->cfg.tile_h - 1) / sv->cfg.tile_h;
+    if (ntx * nty > 16384) return fail(GS_ERR_UNSUPPORTED, "more than 16384 tiles");
+    gs_server_s::EnvRec ev{scene_id, *cam, link_begin, link_end, sv->scenes[scene_id]->px, false};
+    sv->scenes[scene_id]->px += (int64_t)cam->width * cam->height;
+    sv->envs.push_back(ev);
+    *env_id = (int)sv->envs.size() - 1;
+    return GS_OK;
+}
+
+gs_status gs_server_start(gs_server sv) {
+    if (!sv) return fail(GS_ERR_INVALID, "null server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->started) return GS_OK;
+    CK(cudaSetDevice(sv->device), "set device");
+    for (auto& sr : sv->scenes) {  // resident per-env outputs
+        CK(sr->rgb.ensure((size_t)std::max<int64_t>(sr->px, 1) * 12), "alloc env images");
+        CK(sr->depth.ensure((size_t)std::max<int64_t>(sr->px, 1) * 4), "alloc env depth");
+        CK(cudaMemset(sr->rgb.p, 0, sr->rgb.bytes), "clear");
+        CK(cudaMemset(sr->depth.p, 0, sr->depth.bytes), "clear");
+    }
+    sv->t0 = std::chrono::steady_clock::now();
+    std::sort(sv->scheduled.begin(), sv->scheduled.end(),
+              [&](int64_t a, int64_t b) { return sv->reqs[a].arrival < sv->reqs[b].arrival; });
+    sv->started = true;
+    sv->stop = false;
+    sv->worker = std::thread(server_loop, sv);
+    return GS_OK;
+}
+
+gs_status gs_server_submit(gs_server sv, int env_id, const float* poses, double arrival_s, int64_t* request_id) {
+    if (!sv) return fail(GS_ERR_INVALID, "null server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (env_id < 0 || env_id >= (int)sv->envs.size()) return fail(GS_ERR_INVALID, "unknown env %d", env_id);
+    const auto& ev = sv->envs[env_id];
+    const int nl = ev.link_end - ev.link_begin;
+    if (nl > 0 && !poses) return fail(GS_ERR_INVALID, "env %d renders %d links: poses required", env_id, nl);
+    gs_server_s::Req rq;
+    rq.env = env_id;
+    rq.arrival = arrival_s >= 0 ? arrival_s : (sv->started ? sv->now() : 0.0);
+    if (nl > 0) rq.poses.assign(poses, poses + (size_t)nl * 7);
+    sv->reqs.push_back(std::move(rq));
+    const int64_t id = (int64_t)sv->reqs.size() - 1;
+    // keep `scheduled` ordered by arrival (appends are usually in order)
+    auto pos = sv->scheduled.end();
+    while (pos != sv->scheduled.begin() && sv->reqs[*(pos - 1)].arrival > sv->reqs[id].arrival) --pos;
+    sv->scheduled.insert(pos, id);
+    sv->stats.submitted++;
+    if (request_id) *request_id = id;
+    sv->cv.notify_all();
+    return GS_OK;
+}
+
+gs_status gs_server_cancel(gs_server sv, int64_t request_id) {
+    if (!sv) return fail(GS_ERR_INVALID, "null server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (request_id < 0 || request_id >= (int64_t)sv->reqs.size())
+        return fail(GS_ERR_INVALID, "unknown request %lld", (long long)request_id);
+    for (std::deque<int64_t>* q : {&sv->scheduled, &sv->pending}) {
+        auto it = std::find(q->begin(), q->end(), request_id);
+        if (it == q->end()) continue;
+        q->erase(it);
+        auto& rq = sv->reqs[request_id];
+        rq.status = 1;
+        rq.done = sv->started ? sv->now() : 0.0;
+        sv->completed.push_back(request_id);
+        sv->stats.cancelled++;
+        return GS_OK;
+    }
+    return fail(GS_ERR_INVALID, "request %lld already admitted or finished", (long long)request_id);
+}
+
+gs_status gs_server_poll(gs_server sv, gs_request_result* out, int max_results, int* n_out) {
+    if (!sv || !n_out || (max_results > 0 && !out)) return fail(GS_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    int n = 0;
+    while (n < max_results && !sv->completed.empty()) {
+        const int64_t id = sv->completed.front();
+        sv->completed.pop_front();
+        const auto& rq = sv->reqs[id];
+        out[n++] = gs_request_result{id, rq.env, rq.status, rq.arrival, rq.admit, rq.done};
+    }
+    *n_out = n;
+    return GS_OK;
+}
+
+gs_status gs_server_drain(gs_server sv, double timeout_s) {
+    if (!sv) return fail(GS_ERR_INVALID, "null server");
+    const auto t_end = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (!sv->error.empty()) {
+                g_err = sv->error;
+                return GS_ERR_CUDA;
+            }
+            if (sv->stats.completed + sv->stats.cancelled >= sv->stats.submitted) break;
+        }
+        if (std::chrono::steady_clock::now() > t_end) return fail(GS_ERR_TIMEOUT, "requests still in flight");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    // every batch has completed: the scenes' device status words are final
+    for (auto& sr : sv->scenes) ST(gs_scene_sync_status(sr->s, nullptr));
+    return GS_OK;
+}
+
+double gs_server_now(gs_server sv) {
+    if (!sv) return -1.0;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    return sv->started ? sv->now() : 0.0;
+}
+
+gs_status gs_server_get_stats(gs_server sv, gs_server_stats* out) {
+    if (!sv || !out) return fail(GS_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *out = sv->stats;
+    return GS_OK;
+}
+
+gs_status gs_server_env_output(gs_server sv, int env_id, float** rgb, float** depth) {
+    if (!sv || !rgb || !depth) return fail(GS_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (env_id < 0 || env_id >= (int)sv->envs.size()) return fail(GS_ERR_INVALID, "unknown env %d", env_id);
+    if (!sv->started) return fail(GS_ERR_INVALID, "server not started");
+    const auto& ev = sv->envs[env_id];
+    auto& sr = *sv->scenes[ev.scene];
+    *rgb = sr.rgb.as<float>() + ev.pix_off * 3;
+    *depth = sr.depth.as<float>() + ev.pix_off;
+    return GS_OK;
+}
+
+void gs_server_destroy(gs_server sv) {
+    if (!sv) return;
+    sv->stop = true;
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    cudaSetDevice(sv->device);
+    for (auto& sl : sv->slots) {
+        if (sl->st) cudaStreamSynchronize(sl->st);
+        sl->sc.release();
+        sl->poses.release();
+        if (sl->h_poses) cudaFreeHost(sl->h_poses);
+        if (sl->st) cudaStreamDestroy(sl->st);
+    }
+    for (auto& sr : sv->scenes) {
+        sr->rgb.release();
+        sr->depth.release();
+    }
+    delete sv;
 }
 
 }  // extern "C"

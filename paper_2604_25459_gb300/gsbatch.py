@@ -61,6 +61,22 @@ assert ENV_DTYPE.itemsize == 80
 PLAN_AUTOTUNE, PLAN_GRAPH = 1, 2
 
 
+class GsServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("max_inflight", C.c_int), ("max_batch_envs", C.c_int),
+                ("tile_w", C.c_int), ("tile_h", C.c_int)]
+
+
+class GsRequestResult(C.Structure):
+    _fields_ = [("request_id", C.c_int64), ("env_id", C.c_int), ("status", C.c_int), ("arrival_s", C.c_double),
+                ("admit_s", C.c_double), ("done_s", C.c_double)]
+
+
+class GsServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("cancelled", C.c_int64),
+                ("batches", C.c_int64), ("peak_inflight_bytes", C.c_int64), ("max_concurrent", C.c_int32),
+                ("max_batch", C.c_int32)]
+
+
 _lib = None
 
 # name -> (restype, argtypes); the exported C ABI declared in include/gsbatch.h
@@ -87,6 +103,18 @@ _SIGS = {
     "gs_debug_copy_records": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 10),
     "gs_debug_copy_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
     "gs_scene_destroy": (None, [C.c_void_p]),
+    "gs_server_create": (C.c_int, [C.POINTER(GsServerConfig), C.POINTER(C.c_void_p)]),
+    "gs_server_add_scene": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+    "gs_server_add_env": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "gs_server_start": (C.c_int, [C.c_void_p]),
+    "gs_server_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.POINTER(C.c_int64)]),
+    "gs_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
+    "gs_server_poll": (C.c_int, [C.c_void_p, C.POINTER(GsRequestResult), C.c_int, C.POINTER(C.c_int)]),
+    "gs_server_drain": (C.c_int, [C.c_void_p, C.c_double]),
+    "gs_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(GsServerStats)]),
+    "gs_server_env_output": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "gs_server_now": (C.c_double, [C.c_void_p]),
+    "gs_server_destroy": (None, [C.c_void_p]),
     "gs_last_error": (C.c_char_p, []),
     "gs_version": (C.c_char_p, []),
 }
@@ -352,6 +380,105 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class _DevView:
+    """A borrowed device array exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Server:
+    """The request loop (gs_server_*): resident scenes and env instances,
+    requests batched continuously on a pool of CUDA streams under an HBM
+    budget."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 4, max_batch_envs: int = 512, tile=(16, 16)):
+        cfg = GsServerConfig(int(budget_bytes), int(max_inflight), int(max_batch_envs), int(tile[0]), int(tile[1]))
+        self._h = C.c_void_p()
+        _check(lib().gs_server_create(C.byref(cfg), C.byref(self._h)))
+        self._alive = True
+        self._scenes = []
+        self._env_shape = []
+        self._env_links = []
+
+    def add_scene(self, scene: Scene) -> int:
+        sid = C.c_int()
+        _check(lib().gs_server_add_scene(self._h, scene._h, C.byref(sid)))
+        self._scenes.append(scene)  # the scene must outlive the server
+        return sid.value
+
+    def add_env(self, scene_id: int, cam, link_begin: int = 0, link_end: int = 0) -> int:
+        cam = np.ascontiguousarray(np.asarray(cam, dtype=CAMERA_DTYPE).reshape(1))
+        eid = C.c_int()
+        _check(lib().gs_server_add_env(self._h, int(scene_id), _ptr(cam), int(link_begin), int(link_end),
+                                       C.byref(eid)))
+        self._env_shape.append((int(cam["height"][0]), int(cam["width"][0])))
+        self._env_links.append(int(link_end) - int(link_begin))
+        return eid.value
+
+    def start(self):
+        _check(lib().gs_server_start(self._h))
+
+    def submit(self, env_id: int, link_poses=None, arrival_s: float = -1.0) -> int:
+        p = None
+        if self._env_links[env_id] > 0:
+            link_poses = np.ascontiguousarray(link_poses, dtype=np.float32)
+            if link_poses.size != self._env_links[env_id] * 7:
+                raise ValueError("link_poses must hold 7 floats per link of the env")
+            p = _ptr(link_poses)
+        rid = C.c_int64()
+        _check(lib().gs_server_submit(self._h, int(env_id), p, float(arrival_s), C.byref(rid)))
+        return rid.value
+
+    def cancel(self, request_id: int):
+        _check(lib().gs_server_cancel(self._h, int(request_id)))
+
+    def poll(self, max_results: int = 4096) -> list:
+        buf = (GsRequestResult * max_results)()
+        n = C.c_int()
+        _check(lib().gs_server_poll(self._h, buf, max_results, C.byref(n)))
+        return [{k: getattr(buf[i], k) for k, _ in GsRequestResult._fields_} for i in range(n.value)]
+
+    def drain(self, timeout_s: float = 600.0):
+        _check(lib().gs_server_drain(self._h, float(timeout_s)))
+
+    def now(self) -> float:
+        """Seconds since start: the clock of arrival times."""
+        return float(lib().gs_server_now(self._h))
+
+    def stats(self) -> dict:
+        st = GsServerStats()
+        _check(lib().gs_server_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in GsServerStats._fields_}
+
+    def env_output(self, env_id: int):
+        """(rgb [H,W,3], depth [H,W]) torch views of the env's resident outputs."""
+        import torch
+        rgb, depth = C.c_void_p(), C.c_void_p()
+        _check(lib().gs_server_env_output(self._h, int(env_id), C.byref(rgb), C.byref(depth)))
+        H, W = self._env_shape[env_id]
+        return (torch.as_tensor(_DevView(rgb.value, (H, W, 3)), device="cuda"),
+                torch.as_tensor(_DevView(depth.value, (H, W)), device="cuda"))
+
+    def close(self):
+        if getattr(self, "_alive", False):
+            lib().gs_server_destroy(self._h)
+            self._alive = False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def make_envs(cams: np.ndarray, link_ranges=None, pose_offsets=None) -> np.ndarray:

@@ -450,3 +450,67 @@ def make_c3(n_envs: int = 4096, seed: int = 0, n_bg: int = 300_000, count_range=
             c = head_cameras(n_envs, seed, W, H, focal_for(W, H))[idx]
             cams[idx] = c
     return UnevenWorkload("c3", bg, offsets, links, poses, cams)
+
+
+# ---------------------------------------------------------------- served workload (c4)
+
+@dataclasses.dataclass
+class ServedWorkload:
+    """Resident scenes and env instances of the request loop: scene k is a
+    room-shell background of its own size plus the c1 robot (20 links x 5k
+    Gaussians); env i belongs to scene ``env_scene[i]`` and has its own camera
+    (c3 resolution mix).  Request poses come from ``request_poses``."""
+
+    name: str
+    backgrounds: list          # [n_scenes] Gaussians
+    link_offsets: np.ndarray   # int64 [L+1], shared robot
+    links: Gaussians
+    env_scene: np.ndarray      # int32 [E]
+    cams: np.ndarray           # CAMERA_DTYPE [E]
+    seed: int
+
+    @property
+    def n_envs(self) -> int:
+        return int(self.cams.shape[0])
+
+    @property
+    def n_links(self) -> int:
+        return int(self.link_offsets.shape[0] - 1)
+
+    def request_poses(self, n: int, stream: int = 0) -> np.ndarray:
+        """f32 [n][L][7]: link poses of n requests (joint angles U(-1,1) on the
+        c1 chain), from stream ``stream`` of this workload's seed."""
+        rng = _rng(self.seed, 12, stream)
+        return chain_link_poses(rng.uniform(-1.0, 1.0, size=(n, self.n_links)))
+
+    def scene_workload(self, k: int, env_ids, poses: np.ndarray) -> Workload:
+        """Envs ``env_ids`` (all of scene k, one resolution) with the given
+        poses [len(env_ids)][L][7], as a plain workload."""
+        env_ids = np.asarray(env_ids)
+        return Workload(f"{self.name}[{k}]", self.backgrounds[k], self.link_offsets, self.links,
+                        np.ascontiguousarray(poses, np.float32), self.cams[env_ids].copy())
+
+
+def c4_background_sizes(n_scenes: int, lo: int = 200_000, hi: int = 1_000_000) -> np.ndarray:
+    """Background sizes of the served scenes, evenly spaced from lo to hi."""
+    return np.linspace(lo, hi, n_scenes).round().astype(np.int64)
+
+
+def make_c4(n_scenes: int = 8, n_envs: int = 4096, seed: int = 0, bg_range=(200_000, 1_000_000),
+            n_links: int = 20, per_link: int = 5000) -> ServedWorkload:
+    """The served form: n_scenes room-shell backgrounds (sizes evenly spaced
+    over bg_range, each from its own seed 1000*seed + k + 1, the c0 attribute
+    distributions), the c1 robot shared by all, and n_envs env instances
+    assigned to scenes round robin, with jittered head cameras at the c3
+    resolution mix."""
+    sizes = c4_background_sizes(n_scenes, *bg_range)
+    bgs = [make_room_shell(int(n), 1000 * seed + k + 1) for k, n in enumerate(sizes)]
+    offsets, robot = make_robot(n_links, per_link, seed)
+    res = c3_resolutions(n_envs, seed)
+    cams = np.zeros(n_envs, dtype=CAMERA_DTYPE)
+    for k, (W, H) in enumerate(C3_RESOLUTIONS):
+        idx = np.nonzero(res == k)[0]
+        if len(idx):
+            cams[idx] = head_cameras(n_envs, seed, W, H, focal_for(W, H))[idx]
+    env_scene = (np.arange(n_envs) % n_scenes).astype(np.int32)
+    return ServedWorkload("c4", bgs, offsets, robot, env_scene, cams, seed)

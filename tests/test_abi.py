@@ -45,3 +45,16 @@ def test_argument_checks_without_gpu(lib):
     assert lib.gs_scene_set_tile(None, 16, 16) == gsbatch.GS_ERR_INVALID
     assert lib.gs_render_batch(None, 1, None, None, None, None, None, None) == gsbatch.GS_ERR_INVALID
     assert lib.gs_version().startswith(b"gsbatch")
+
+
+def test_server_config_checks_without_gpu(lib):
+    h = C.c_void_p()
+    assert lib.gs_server_create(None, C.byref(h)) == gsbatch.GS_ERR_INVALID
+    for cfg in [(0, 2, 8, 16, 16), (1 << 30, 0, 8, 16, 16), (1 << 30, 65, 8, 16, 16), (1 << 30, 2, 0, 16, 16),
+                (1 << 30, 2, 8, 12, 16)]:
+        c = gsbatch.GsServerConfig(*cfg)
+        assert lib.gs_server_create(C.byref(c), C.byref(h)) == gsbatch.GS_ERR_INVALID, cfg
+        assert not h.value
+    assert lib.gs_server_submit(None, 0, None, 0.0, None) == gsbatch.GS_ERR_INVALID
+    assert lib.gs_server_poll(None, None, 0, None) == gsbatch.GS_ERR_INVALID
+    lib.gs_server_destroy(None)
