@@ -302,7 +302,11 @@ void gs_scene_destroy(gs_scene s);
  *     budget still runs, alone, when nothing else is in flight;
  *   - each batch runs the full render on its own CUDA stream and scratch, so
  *     batches overlap on the device; a host callback on the stream records
- *     its completion time.
+ *     its completion time.  Its intersection keys get a capacity from the
+ *     running per-(scene, resolution) estimate, so the scheduler never waits
+ *     on the device; a batch whose keys overflowed it (flagged on the device)
+ *     is rendered again with exact sizing before it completes, and the first
+ *     batch of each kind is sized exactly;
  * A request's output is bit-identical to rendering its env alone with
  * gs_render_batch_v at the server's tile shape.  While a server runs, its
  * scenes must not be rendered or destroyed by other calls.
@@ -330,6 +334,7 @@ typedef struct {
     int64_t peak_inflight_bytes;  /* largest estimated working set in flight */
     int32_t max_concurrent;       /* most batches in flight at once */
     int32_t max_batch;            /* most requests in one batch */
+    int64_t retried;              /* batches rendered again after their keys overflowed the estimate */
 } gs_server_stats;
 
 /* Create a server on the current device (stream slots created here; scratch

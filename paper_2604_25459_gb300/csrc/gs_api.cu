@@ -85,9 +85,9 @@ struct DevBuf {
 // Device scratch of a render: one set per scene (eager calls) and one per plan.
 struct Scratch {
     DevBuf envs, blocks, cams, xf, r0, r1, r2, r3, mask, counts, off, cursor, env_total, env_base, pairs, dbg_hxy,
-        dbg_sorted, work;
-    DevBuf* all[18] = {&envs, &blocks, &cams, &xf, &r0, &r1, &r2, &r3, &mask, &counts,
-                       &off, &cursor, &env_total, &env_base, &pairs, &dbg_hxy, &dbg_sorted, &work};
+        dbg_sorted, work, spill;
+    DevBuf* all[19] = {&envs, &blocks, &cams, &xf,        &r0,       &r1,         &r2,    &r3,   &mask,  &counts,
+                       &off,  &cursor, &env_total, &env_base, &pairs, &dbg_hxy, &dbg_sorted, &work, &spill};
     void release() {
         for (DevBuf* b : all) b->release();
     }
@@ -388,6 +388,7 @@ struct WaveIO {
     float* depth;
     float* alpha;
     long long pix_rebase;
+    uint32_t* status = nullptr;  // device status word of this wave (NULL: the scene's)
 };
 
 struct WaveTables {       // device copies of one wave's tables
@@ -464,12 +465,16 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     CK(sc.env_total.ensure((size_t)We * 8), "alloc totals");
     CK(sc.env_base.ensure(((size_t)We + 1) * 8), "alloc bases");
     CK(sc.work.ensure(16), "alloc work counter");
+    int spill_ctas = 0;  // per-CTA regions for partitioning long buckets
+    CK(composite_max_ctas(tw, th, &spill_ctas), "compositor occupancy");
+    CK(sc.spill.ensure((size_t)spill_ctas * kSpillMax * 8), "alloc spill");
     const bool debug = s->debug && cap == 0;
     if (debug) CK(sc.dbg_hxy.ensure(wt.recs * 8), "alloc debug");
+    uint32_t* const status = io.status ? io.status : s->status;
 
     // A1: link composition
     PhaseTimer t1(s, st, GS_PHASE_LINK, timers);
-    CK(launch_link_table(io.poses, wt.cams, wt.envs, We, wt.xf_items, sc.xf.as<LinkXf>(), s->status, st),
+    CK(launch_link_table(io.poses, wt.cams, wt.envs, We, wt.xf_items, sc.xf.as<LinkXf>(), status, st),
        "link table");
     t1.done(1);
     ++*launches;
@@ -509,7 +514,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     B.off_local = sc.off.as<uint32_t>();
     B.env_base = sc.env_base.as<unsigned long long>();
     B.cursor = sc.cursor.as<uint32_t>();
-    B.status = s->status;
+    B.status = status;
     PhaseTimer t3(s, st, GS_PHASE_COUNT, timers);
     CK(launch_count(B, We, wt.max_words, wt.max_T, st), "count");
     t3.done(1);
@@ -597,6 +602,9 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.pair_base = base;
         C.pair_cap = B.pair_cap;
         C.pairs = B.pairs;
+        C.spill = sc.spill.as<unsigned long long>();
+        C.spill_cap = kSpillMax;
+        C.spill_ctas = (unsigned)spill_ctas;
         C.dbg_sorted = debug ? sc.dbg_sorted.as<unsigned long long>() : nullptr;
         C.neval = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() : nullptr;
         C.tile_w = tw;
@@ -604,7 +612,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.rgb = io.rgb;
         C.depth = io.depth;
         C.alpha = io.alpha;
-        C.status = s->status;
+        C.status = status;
         CK(cudaMemsetAsync(sc.work.p, 0, 4, st), "memset work counter");
         int ctas = 0;
         PhaseTimer t6(s, st, GS_PHASE_COMPOSITE, timers);
@@ -1466,11 +1474,16 @@ struct gs_server_s {
     struct Slot {
         cudaStream_t st = nullptr;
         Scratch sc;
-        DevBuf poses;
-        float* h_poses = nullptr;   // pinned staging
+        DevBuf poses, dstat;          // link poses; the batch's device status word
+        float* h_poses = nullptr;     // pinned staging of the poses
         size_t h_cap = 0;
+        unsigned long long* h_meta = nullptr;  // pinned: [0] status word, [1..n+1] key offsets per env
+        size_t meta_cap = 0;
         bool busy = false;
-        std::vector<int64_t> batch;
+        bool eager = false;           // the batch in flight sizes its keys exactly (host sync)
+        bool failed = false;          // its launch failed (requests carry the status)
+        int scene = -1;
+        std::vector<int64_t> batch;   // request ids, in launch order
         double bytes = 0;
         std::atomic<int> done{0};
         double t_done = 0;
@@ -1485,7 +1498,7 @@ struct gs_server_s {
     std::chrono::steady_clock::time_point t0;
     double inflight_bytes = 0;
     gs_server_stats stats{};
-    std::map<std::tuple<int, int, int>, double> keys_ema;  // (scene, W, H) -> keys per env
+    std::map<std::tuple<int, int, int>, double> keys_ema;  // (scene, W, H) -> intersections per env
     std::string error;
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1500,74 +1513,111 @@ void CUDART_CB server_slot_done(void* p) {
     sl->done.store(1, std::memory_order_release);
 }
 
+// Estimated intersections of an env (running average for its scene and
+// resolution), or -1 before any batch of that kind has run.
+double keys_estimate(gs_server sv, const gs_server_s::EnvRec& ev) {
+    auto it = sv->keys_ema.find({ev.scene, ev.cam.width, ev.cam.height});
+    return it != sv->keys_ema.end() ? it->second : -1.0;
+}
+
 double request_bytes(gs_server sv, const gs_server_s::EnvRec& ev) {
     gs_scene s = sv->scenes[ev.scene]->s;
     EnvSpec sp{&ev.cam, ev.link_begin, ev.link_end, 0, 0};
     const int tw = sv->cfg.tile_w, th = sv->cfg.tile_h;
-    const double T = (double)((ev.cam.width + tw - 1) / tw) * ((ev.cam.height + th - 1) / th);
-    auto it = sv->keys_ema.find({ev.scene, ev.cam.width, ev.cam.height});
-    const double keys = it != sv->keys_ema.end() ? it->second : T * 2000.0;
+    double keys = keys_estimate(sv, ev);
+    if (keys < 0) keys = (double)(sv->scenes[ev.scene]->s->D.n);  // first of its kind: about one key per Gaussian
     return (double)env_bytes(s, sp, tw, th, false) + keys * 8.0 * 1.3;
 }
 
-// Launch one batch (requests of one scene) on a free slot.  Called by the
-// scheduler thread with the lock released.
-gs_status server_launch(gs_server sv, gs_server_s::Slot& sl, int scene, const std::vector<int64_t>& batch) {
-    auto& sr = *sv->scenes[scene];
+// Launch one batch (requests of one scene, in sl.batch) on its slot.  Called
+// by the scheduler thread with the lock released.  The batch is ordered by
+// ascending pixel count: low-resolution envs have the longest tile buckets,
+// so their tiles are claimed first.  Planned mode (keys capacity from the
+// running estimates, no host sync) unless the batch has an env of a kind not
+// seen before or sl.eager is set; a planned batch whose keys overflowed is
+// relaunched eagerly by the scheduler.
+gs_status server_launch(gs_server sv, gs_server_s::Slot& sl) {
+    auto& sr = *sv->scenes[sl.scene];
     gs_scene s = sr.s;
     const int L = s->D.n_links;
+    auto& batch = sl.batch;
     const size_t n = batch.size();
+    std::stable_sort(batch.begin(), batch.end(), [&](int64_t x, int64_t y) {
+        const gs_camera& a = sv->envs[sv->reqs[x].env].cam;
+        const gs_camera& b = sv->envs[sv->reqs[y].env].cam;
+        return (int64_t)a.width * a.height < (int64_t)b.width * b.height;
+    });
     const size_t pose_floats = std::max<size_t>(1, n * (size_t)L * 7);
     if (pose_floats > sl.h_cap) {
         if (sl.h_poses) cudaFreeHost(sl.h_poses);
         sl.h_poses = nullptr;
+        sl.h_cap = 0;
         CK(cudaMallocHost((void**)&sl.h_poses, pose_floats * 4), "alloc pinned poses");
         sl.h_cap = pose_floats;
     }
+    if (n + 2 > sl.meta_cap) {
+        if (sl.h_meta) cudaFreeHost(sl.h_meta);
+        sl.h_meta = nullptr;
+        sl.meta_cap = 0;
+        CK(cudaMallocHost((void**)&sl.h_meta, (n + 2) * 8), "alloc pinned batch info");
+        sl.meta_cap = n + 2;
+    }
     CK(sl.poses.ensure(pose_floats * 4), "alloc poses");
+    CK(sl.dstat.ensure(8), "alloc status");
     std::vector<EnvSpec> specs(n);
+    double est = 0;
+    bool known = true;
     for (size_t i = 0; i < n; ++i) {
         const auto& rq = sv->reqs[batch[i]];
         const auto& ev = sv->envs[rq.env];
         const int nl = ev.link_end - ev.link_begin;
         if (nl > 0) memcpy(sl.h_poses + i * (size_t)L * 7, rq.poses.data(), sizeof(float) * nl * 7);
         specs[i] = EnvSpec{&ev.cam, ev.link_begin, ev.link_end, (long long)i * L, (long long)ev.pix_off};
+        const double k = keys_estimate(sv, ev);
+        if (k < 0) known = false;
+        est += k;
     }
+    const bool eager = sl.eager || !known;
+    sl.eager = eager;
     if (L > 0)
         CK(cudaMemcpyAsync(sl.poses.p, sl.h_poses, n * (size_t)L * 28, cudaMemcpyHostToDevice, sl.st), "copy poses");
+    CK(cudaMemsetAsync(sl.dstat.p, 0, 4, sl.st), "clear status");
     WaveTables wt{};
     ST(upload_tables(s, specs, 0, (int)n, sv->cfg.tile_w, sv->cfg.tile_h, 0, sl.sc.envs, sl.sc.blocks, sl.sc.cams,
                      sl.st, false, &wt));
     int64_t launches = 0;
     unsigned long long keys = 0;
-    ST(run_wave(s, sl.sc, wt, WaveIO{sl.poses.as<float>(), sr.rgb.as<float>(), sr.depth.as<float>(), nullptr, 0},
-                sv->cfg.tile_w, sv->cfg.tile_h, 1, 0, sl.st, false, &launches, &keys));
-    // keys per env of this resolution mix: running average per (scene, size)
-    std::map<std::tuple<int, int, int>, std::pair<double, int>> acc;
-    const double tiles_total = (double)wt.tiles;
-    for (size_t i = 0; i < n; ++i) {
-        const auto& ev = sv->envs[sv->reqs[batch[i]].env];
-        const double T = (double)wt.host_envs[i].T;
-        auto& a = acc[{ev.scene, ev.cam.width, ev.cam.height}];
-        a.first += tiles_total > 0 ? (double)keys * T / tiles_total : 0.0;
-        a.second += 1;
-    }
-    for (auto& kv : acc) {
-        const double per = kv.second.first / kv.second.second;
-        auto it = sv->keys_ema.find(kv.first);
-        if (it == sv->keys_ema.end()) sv->keys_ema[kv.first] = per;
-        else it->second = 0.8 * it->second + 0.2 * per;
-    }
+    const unsigned long long cap = eager ? 0ull : (unsigned long long)(est * 1.25) + 65536ull;
+    WaveIO io{sl.poses.as<float>(), sr.rgb.as<float>(), sr.depth.as<float>(), nullptr, 0, sl.dstat.as<uint32_t>()};
+    ST(run_wave(s, sl.sc, wt, io, sv->cfg.tile_w, sv->cfg.tile_h, 1, cap, sl.st, false, &launches, &keys));
+    CK(cudaMemcpyAsync(sl.h_meta, sl.dstat.p, 4, cudaMemcpyDeviceToHost, sl.st), "read status");
+    CK(cudaMemcpyAsync(sl.h_meta + 1, sl.sc.env_base.p, (n + 1) * 8, cudaMemcpyDeviceToHost, sl.st), "read keys");
     sl.t0 = sv->t0;
     CK(cudaLaunchHostFunc(sl.st, server_slot_done, &sl), "completion callback");
     return GS_OK;
+}
+
+// A finished batch (lock held): update the key estimates from its exact
+// per-env intersection counts; true if it must be relaunched eagerly.
+bool server_batch_done(gs_server sv, gs_server_s::Slot& sl, uint32_t* status_out) {
+    const uint32_t st = (uint32_t)(sl.h_meta[0] & 0xffffffffu);
+    const unsigned long long* base = sl.h_meta + 1;
+    for (size_t i = 0; i < sl.batch.size(); ++i) {
+        const auto& ev = sv->envs[sv->reqs[sl.batch[i]].env];
+        const double k = (double)(base[i + 1] - base[i]);
+        auto it = sv->keys_ema.find({ev.scene, ev.cam.width, ev.cam.height});
+        if (it == sv->keys_ema.end()) sv->keys_ema[{ev.scene, ev.cam.width, ev.cam.height}] = k;
+        else it->second = 0.9 * it->second + 0.1 * k;
+    }
+    *status_out = st;
+    return (st & kStOverflow) && !sl.eager;
 }
 
 void server_loop(gs_server sv) {
     cudaSetDevice(sv->device);
     while (!sv->stop.load()) {
         bool worked = false;
-        std::vector<std::pair<gs_server_s::Slot*, std::pair<int, std::vector<int64_t>>>> launch;
+        std::vector<gs_server_s::Slot*> launch, relaunch;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             const double t = sv->now();
@@ -1578,9 +1628,21 @@ void server_loop(gs_server sv) {
             // completions
             for (auto& sl : sv->slots) {
                 if (sl->busy && sl->done.load(std::memory_order_acquire)) {
+                    uint32_t dst = 0;
+                    if (sl->failed) {
+                        dst = 0;  // the requests already carry the launch's status
+                    } else if (server_batch_done(sv, *sl, &dst)) {
+                        sl->done.store(0);  // keys overflowed the estimate: render it again, exactly
+                        sl->eager = true;
+                        sv->stats.retried++;
+                        relaunch.push_back(sl.get());
+                        worked = true;
+                        continue;
+                    }
                     for (int64_t id : sl->batch) {
                         auto& rq = sv->reqs[id];
                         rq.done = sl->t_done;
+                        if (rq.status == 0 && dst != 0) rq.status = (int)GS_ERR_DEVICE;
                         sv->envs[rq.env].busy = false;
                         sv->completed.push_back(id);
                         sv->stats.completed++;
@@ -1635,6 +1697,9 @@ void server_loop(gs_server sv) {
                 }
                 slp->busy = true;
                 slp->done.store(0);
+                slp->eager = false;
+                slp->failed = false;
+                slp->scene = scene;
                 slp->batch = batch;
                 slp->bytes = bytes;
                 sv->inflight_bytes += bytes;
@@ -1643,19 +1708,23 @@ void server_loop(gs_server sv) {
                 ++inflight;
                 sv->stats.max_concurrent = std::max(sv->stats.max_concurrent, inflight);
                 sv->stats.max_batch = std::max(sv->stats.max_batch, (int)batch.size());
-                launch.push_back({slp.get(), {scene, batch}});
+                launch.push_back(slp.get());
             }
         }
-        for (auto& l : launch) {
-            gs_status st = server_launch(sv, *l.first, l.second.first, l.second.second);
+        for (auto* l : relaunch) launch.push_back(l);
+        for (auto* l : launch) {
+            gs_status st = server_launch(sv, *l);
             worked = true;
             if (st != GS_OK) {
                 std::lock_guard<std::mutex> lk(sv->mu);
                 sv->error = g_err;
-                for (int64_t id : l.second.second) sv->reqs[id].status = (int)st;
-                // completes at once so the loop does not stall; the status tells
-                l.first->t_done = sv->now();
-                l.first->done.store(1);
+                for (int64_t id : l->batch) sv->reqs[id].status = (int)st;
+                // completes once the stream has drained, so the loop does not stall;
+                // the requests carry the status
+                cudaStreamSynchronize(l->st);
+                l->failed = true;
+                l->t_done = sv->now();
+                l->done.store(1);
             }
         }
         if (!worked) {
@@ -1855,7 +1924,9 @@ void gs_server_destroy(gs_server sv) {
         if (sl->st) cudaStreamSynchronize(sl->st);
         sl->sc.release();
         sl->poses.release();
+        sl->dstat.release();
         if (sl->h_poses) cudaFreeHost(sl->h_poses);
+        if (sl->h_meta) cudaFreeHost(sl->h_meta);
         if (sl->st) cudaStreamDestroy(sl->st);
     }
     for (auto& sr : sv->scenes) {

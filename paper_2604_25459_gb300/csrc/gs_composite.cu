@@ -204,22 +204,36 @@ __device__ __forceinline__ float splat_alpha(const float4& A, const float4& B, f
 // row-major, so envs of any resolution mix in one launch).  For an item the
 // CTA covers the TW x TH tile: warp w owns an 8x8 subtile and each lane two
 // pixels of it, (x, y) and (x, y + 4), whose blend chains are independent.
+//
+// A bucket of at most kCompCap keys is sorted in shared memory at once.  A
+// longer bucket is first partitioned, in one counting pass, into kBins equal
+// key ranges written in range order to the CTA's spill region (spill_cap
+// keys); window w then holds the bins that start in [w H, (w+1) H) with
+// H = kCompCap / 2, so every window is at most kCompCap keys unless one bin is
+// larger than H; such a window (and a bucket longer than spill_cap, or any
+// long bucket when there is no spill region) is cut into windows by radix
+// selection over its keys instead.
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_composite(CompParams P) {
     constexpr int NT = TW * TH / 2;
     constexpr int NB = NT;  // splats staged per batch (one per thread)
     constexpr int CAP = kCompCap;
+    constexpr int HALF = kCompCap / 2;
     constexpr int UB = (CAP * 8 > NB * 64) ? CAP * 8 : NB * 64;
     constexpr int CB = (18 * NT * 2 > 256 * 4) ? 18 * NT * 2 : 256 * 4;
     constexpr int NW = NT / 32;
-    __shared__ unsigned long long keys[CAP];
-    __shared__ __align__(16) unsigned char ubuf[UB];  // sort scratch | staged records
-    __shared__ __align__(16) unsigned char cbuf[CB];  // radix counters | selection histogram
+    static_assert(CAP * 8 + UB >= kBins * 4, "bin counters alias the key and staging buffers");
+    static_assert(kBins % NT == 0, "bins per thread");
+    __shared__ __align__(16) unsigned char kbuf[CAP * 8 + UB];  // window keys | sort scratch, staged records
+    __shared__ __align__(16) unsigned char cbuf[CB];            // radix counters | selection histogram
     __shared__ uint32_t red[32];
-    __shared__ unsigned long long redl[NW > 0 ? NW : 1];
+    __shared__ unsigned long long redl[2 * (NW > 0 ? NW : 1)];
     __shared__ unsigned long long sel_lo, sel_hi, sel_khi;
     __shared__ uint32_t sel_wn, sel_cnt;
     __shared__ int sel_state;
+    __shared__ uint32_t s_ws[kSpillMax / (kCompCap / 2) + 2];  // window starts in the spill region
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(kbuf);
+    unsigned char* ubuf = kbuf + CAP * 8;
     unsigned long long* tmp = reinterpret_cast<unsigned long long*>(ubuf);
     float4* sA = reinterpret_cast<float4*>(ubuf);  // u, v, o, z
     float4* sB = sA + NB;                          // scaled conic factor l00, l01, l11
@@ -227,10 +241,13 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_compo
     int4* sR = reinterpret_cast<int4*>(sC + NB);   // x0, x1 - x0, y0, y1 - y0
     uint16_t* cnt = reinterpret_cast<uint16_t*>(cbuf);
     uint32_t* hist = reinterpret_cast<uint32_t*>(cbuf);
+    uint32_t* bins = reinterpret_cast<uint32_t*>(kbuf);  // partition counters (between windows only)
 
     __shared__ unsigned int s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool dbg = P.dbg_sorted != nullptr;
+    unsigned long long* spill =
+        P.spill ? P.spill + (size_t)blockIdx.x * P.spill_cap : nullptr;  // this CTA's region
     int el = P.e_begin;  // env of the current item, cached across items (uniform in the CTA)
     unsigned int e_lo = P.envs[el].tile_base, e_hi = e_lo + (unsigned)P.envs[el].T;
     if (tid == 0) s_item = atomicAdd(P.work, (unsigned)P.chunk);
@@ -276,109 +293,19 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_compo
     }
     const unsigned long long* Lk = P.pairs + start;
     const size_t recbase = (size_t)__ldg(&Ep->rec_base);
-
-    unsigned long long kmax = 0;
-    if (n > (uint32_t)CAP) {
-        unsigned long long m = 0;
-        for (uint32_t i = tid; i < n; i += NT) {
-            const unsigned long long k = Lk[i];
-            m = k > m ? k : m;
-        }
-        kmax = block_max_u64<NT>(m, redl);
-    }
-
-    unsigned long long klo = 0;
-    uint32_t processed = 0;
     bool finished = false;
-    while (processed < n && !finished) {
-        uint32_t wn;
-        unsigned long long khi;
-        if (n - processed <= (uint32_t)CAP) {
-            wn = n - processed;
-            khi = ~0ull;
-        } else {
-            // radix-select a window [klo, khi) of at most CAP keys
-            if (tid == 0) {
-                sel_lo = klo;
-                sel_hi = kmax;
-                sel_state = 0;
-            }
-            __syncthreads();
-            for (int level = 0; level < 10; ++level) {
-                const unsigned long long lo = sel_lo, hi = sel_hi;
-                const unsigned long long x = lo ^ hi;
-                const int hb = x ? 63 - __clzll((long long)x) : 0;
-                const int shift = hb > 7 ? hb - 7 : 0;
-                for (int i = tid; i < 256; i += NT) hist[i] = 0;
-                __syncthreads();
-                for (uint32_t i = tid; i < n; i += NT) {
-                    const unsigned long long k = Lk[i];
-                    if (k >= lo && k <= hi) atomicAdd(&hist[(k >> shift) & 255u], 1u);
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    const unsigned long long pre = (lo >> (shift + 8)) << (shift + 8);
-                    int d = 0;
-                    while (d < 255 && hist[d] == 0) ++d;
-                    if (hist[d] > (uint32_t)CAP) {
-                        const unsigned long long blo = pre | ((unsigned long long)d << shift);
-                        const unsigned long long bhi = blo | ((1ull << shift) - 1ull);
-                        sel_lo = blo > lo ? blo : lo;
-                        sel_hi = bhi < hi ? bhi : hi;
-                    } else {
-                        uint32_t cum = 0;
-                        while (d < 256 && cum + hist[d] <= (uint32_t)CAP) {
-                            cum += hist[d];
-                            ++d;
-                        }
-                        // window ends just before digit d (or after hi when all digits fit)
-                        unsigned long long kh;
-                        if (d >= 256) {
-                            kh = hi + 1ull;
-                        } else {
-                            kh = pre | ((unsigned long long)d << shift);
-                            if (kh > hi + 1ull) kh = hi + 1ull;
-                        }
-                        sel_khi = kh;
-                        sel_wn = cum;
-                        sel_state = 1;
-                    }
-                }
-                __syncthreads();
-                if (sel_state) break;
-            }
-            // keys are unique, so eight 8-bit levels always isolate a window; anything
-            // else means a corrupted bucket: flag it and stop instead of spinning
-            khi = sel_state ? sel_khi : klo;
-            wn = sel_state ? sel_wn : 0u;
-        }
-        if (wn == 0) {
-            if (tid == 0) atomicOr(P.status, kStOverflow);
-            break;
-        }
-        // gather the window into shared memory
-        if (processed == 0 && n <= (uint32_t)CAP) {
-            for (uint32_t i = tid; i < n; i += NT) keys[i] = Lk[i];
-            __syncthreads();
-        } else {
-            if (tid == 0) sel_cnt = 0;
-            __syncthreads();
-            for (uint32_t i = tid; i < n; i += NT) {
-                const unsigned long long k = Lk[i];
-                if (k >= klo && k < khi) {
-                    const uint32_t slot = atomicAdd(&sel_cnt, 1u);
-                    if (slot < (uint32_t)CAP) keys[slot] = k;
-                }
-            }
-            __syncthreads();
-        }
+
+    // Sort keys[0, wn) (the next wn keys in depth order) and composite them;
+    // `before` keys of the bucket precede them.  Sets `finished` once every
+    // pixel of the tile has terminated.
+    auto run_window = [&](uint32_t wn, uint32_t before) {
         const unsigned long long* sorted = window_sort<NT>(keys, tmp, cnt, red, (int)wn);
         if (sorted != keys) {  // the sorted window sits in the scratch half: move it home
             for (uint32_t i = tid; i < wn; i += NT) keys[i] = sorted[i];
             __syncthreads();
         }
         if (dbg)
-            for (uint32_t i = tid; i < wn; i += NT) P.dbg_sorted[start + processed + i] = keys[i];
+            for (uint32_t i = tid; i < wn; i += NT) P.dbg_sorted[start + before + i] = keys[i];
 
         for (uint32_t b = 0; b < wn; b += NB) {
             const int cnt_b = (int)min((uint32_t)NB, wn - b);
@@ -475,8 +402,241 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_compo
                 break;
             }
         }
-        processed += wn;
-        klo = khi;
+    };
+
+    // Smallest and largest of the keys L[0, len) (block-wide).
+    auto key_range = [&](const unsigned long long* L, uint32_t len, unsigned long long& mn,
+                         unsigned long long& mx) {
+        unsigned long long a = ~0ull, b = 0;
+        for (uint32_t i = tid; i < len; i += NT) {
+            const unsigned long long k = L[i];
+            a = k < a ? k : a;
+            b = k > b ? k : b;
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long oa = __shfl_xor_sync(0xffffffffu, a, d);
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, d);
+            a = oa < a ? oa : a;
+            b = ob > b ? ob : b;
+        }
+        if (lane == 0) {
+            redl[warp] = a;
+            redl[NW + warp] = b;
+        }
+        __syncthreads();
+        mn = redl[0];
+        mx = redl[NW];
+        for (int w = 1; w < NW; ++w) {
+            mn = redl[w] < mn ? redl[w] : mn;
+            mx = redl[NW + w] > mx ? redl[NW + w] : mx;
+        }
+        __syncthreads();
+    };
+
+    // Radix-select, among the keys of L[0, len) inside [lo, hi], the smallest
+    // ones: on success khi is such that the keys in [lo, khi) number wn, with
+    // 0 < wn <= cap (8-bit digits of the key range; distinct keys are always
+    // isolated within eight levels).  False means a corrupted bucket.
+    auto select = [&](const unsigned long long* L, uint32_t len, unsigned long long lo0, unsigned long long hi0,
+                      uint32_t cap, unsigned long long& khi, uint32_t& wn) -> bool {
+        if (tid == 0) {
+            sel_lo = lo0;
+            sel_hi = hi0;
+            sel_state = 0;
+        }
+        __syncthreads();
+        for (int level = 0; level < 10; ++level) {
+            const unsigned long long lo = sel_lo, hi = sel_hi;
+            const unsigned long long x = lo ^ hi;
+            const int hb = x ? 63 - __clzll((long long)x) : 0;
+            const int shift = hb > 7 ? hb - 7 : 0;
+            for (int i = tid; i < 256; i += NT) hist[i] = 0;
+            __syncthreads();
+            for (uint32_t i = tid; i < len; i += NT) {
+                const unsigned long long k = L[i];
+                if (k >= lo && k <= hi) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const unsigned long long pre = (lo >> (shift + 8)) << (shift + 8);
+                int d = 0;
+                while (d < 255 && hist[d] == 0) ++d;
+                if (hist[d] > cap) {
+                    const unsigned long long blo = pre | ((unsigned long long)d << shift);
+                    const unsigned long long bhi = blo | ((1ull << shift) - 1ull);
+                    sel_lo = blo > lo ? blo : lo;
+                    sel_hi = bhi < hi ? bhi : hi;
+                } else {
+                    uint32_t cum = 0;
+                    while (d < 256 && cum + hist[d] <= cap) {
+                        cum += hist[d];
+                        ++d;
+                    }
+                    // window ends just before digit d (or after hi when all digits fit)
+                    unsigned long long kh;
+                    if (d >= 256) {
+                        kh = hi + 1ull;
+                    } else {
+                        kh = pre | ((unsigned long long)d << shift);
+                        if (kh > hi + 1ull) kh = hi + 1ull;
+                    }
+                    sel_khi = kh;
+                    sel_wn = cum;
+                    sel_state = 1;
+                }
+            }
+            __syncthreads();
+            if (sel_state) break;
+        }
+        const bool ok = sel_state != 0 && sel_wn > 0;
+        khi = sel_khi;
+        wn = sel_wn;
+        __syncthreads();  // the shared selection state is rewritten by the next call
+        return ok;
+    };
+
+    // Window producer: fills keys[0, wn) with the next wn keys of the bucket
+    // in depth order (unsorted) and returns wn, 0 when the bucket is done.
+    // Short buckets are one window; long ones are partitioned run by run into
+    // the spill region (see above), and a segment that needs it (an oversized
+    // window, or the whole bucket without a spill region) is cut by selection.
+    unsigned long long klo = 0, kmax = 0;
+    uint32_t processed = 0;  // keys of the bucket in runs started so far
+    int w = 0, nw = 0;       // next window of the current run
+    const unsigned long long* seg = nullptr;
+    uint32_t seg_len = 0, seg_used = 0;
+    unsigned long long seg_lo = 0, seg_hi = 0;
+    bool started = false;
+    auto next_window = [&]() -> uint32_t {
+        if (n <= (uint32_t)CAP) {
+            if (started || n == 0) return 0u;
+            started = true;
+            for (uint32_t i = tid; i < n; i += NT) keys[i] = Lk[i];
+            __syncthreads();
+            return n;
+        }
+        if (!started) {
+            started = true;
+            key_range(Lk, n, klo, kmax);
+            if (!spill) {
+                seg = Lk;
+                seg_len = n;
+                seg_lo = klo;
+                seg_hi = kmax;
+                processed = n;
+            }
+        }
+        for (;;) {
+            if (seg_used < seg_len) {  // cut the segment by selection
+                unsigned long long kh;
+                uint32_t wn;
+                if (seg_len - seg_used <= (uint32_t)CAP) {
+                    kh = seg_hi + 1ull;
+                    wn = seg_len - seg_used;
+                } else if (!select(seg, seg_len, seg_lo, seg_hi, CAP, kh, wn)) {
+                    if (tid == 0) atomicOr(P.status, kStOverflow);
+                    return 0u;
+                }
+                if (tid == 0) sel_cnt = 0;
+                __syncthreads();
+                for (uint32_t i = tid; i < seg_len; i += NT) {
+                    const unsigned long long k = seg[i];
+                    if (k >= seg_lo && k < kh) {
+                        const uint32_t slot = atomicAdd(&sel_cnt, 1u);
+                        if (slot < (uint32_t)CAP) keys[slot] = k;
+                    }
+                }
+                __syncthreads();
+                seg_used += wn;
+                seg_lo = kh;
+                return wn;
+            }
+            if (w < nw) {  // the next window of the partitioned run
+                const uint32_t a = s_ws[w], b = s_ws[w + 1];
+                ++w;
+                if (b <= a) continue;
+                if (b - a <= (uint32_t)CAP) {
+                    for (uint32_t i = tid; i < b - a; i += NT) keys[i] = spill[a + i];
+                    __syncthreads();
+                    return b - a;
+                }
+                seg = spill + a;  // a bin of more than HALF keys
+                seg_len = b - a;
+                seg_used = 0;
+                key_range(seg, seg_len, seg_lo, seg_hi);
+                continue;
+            }
+            if (processed >= n) return 0u;
+            // the next run of at most spill_cap keys, [klo, kh), partitioned
+            // into kBins key ranges in the spill region
+            unsigned long long kh;
+            uint32_t m;
+            if (n - processed <= P.spill_cap) {
+                kh = kmax + 1ull;
+                m = n - processed;
+            } else if (!select(Lk, n, klo, kmax, P.spill_cap, kh, m)) {
+                if (tid == 0) atomicOr(P.status, kStOverflow);
+                return 0u;
+            }
+            const unsigned long long span = kh - 1ull - klo;
+            const int shift = (span >> 11) ? 53 - __clzll((long long)span) : 0;  // span >> shift < kBins
+            for (int i = tid; i < kBins; i += NT) bins[i] = 0;
+            __syncthreads();
+            for (uint32_t i = tid; i < n; i += NT) {
+                const unsigned long long k = Lk[i];
+                if (k >= klo && k < kh) atomicAdd(&bins[(uint32_t)((k - klo) >> shift)], 1u);
+            }
+            __syncthreads();
+            constexpr int PER = kBins / NT;
+            uint32_t loc = 0;
+#pragma unroll 4
+            for (int j = 0; j < PER; ++j) loc += bins[tid * PER + j];
+            uint32_t run = block_excl_scan_u32<NT>(loc, red);
+#pragma unroll 4
+            for (int j = 0; j < PER; ++j) {
+                const uint32_t c = bins[tid * PER + j];
+                bins[tid * PER + j] = run;
+                run += c;
+            }
+            __syncthreads();
+            // window v: the bins that start in [v HALF, (v+1) HALF)
+            nw = (int)((m + HALF - 1) / HALF);
+            for (int v = tid; v <= nw; v += NT) {
+                uint32_t x = m;
+                if (v == 0) {
+                    x = 0;
+                } else if (v < nw) {
+                    const uint32_t target = (uint32_t)v * HALF;
+                    int lo = 0, hi = kBins;  // first bin whose start >= target
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (bins[mid] >= target) hi = mid; else lo = mid + 1;
+                    }
+                    x = lo < kBins ? bins[lo] : m;
+                }
+                s_ws[v] = x;
+            }
+            __syncthreads();
+            for (uint32_t i = tid; i < n; i += NT) {
+                const unsigned long long k = Lk[i];
+                if (k >= klo && k < kh) {
+                    const uint32_t pos = atomicAdd(&bins[(uint32_t)((k - klo) >> shift)], 1u);
+                    spill[pos] = k;
+                }
+            }
+            __syncthreads();
+            w = 0;
+            processed += m;
+            klo = kh;
+        }
+    };
+
+    uint32_t before = 0;  // keys of the bucket composited so far (windows come in depth order)
+    while (!finished) {
+        const uint32_t wn = next_window();
+        if (wn == 0) break;
+        run_window(wn, before);
+        before += wn;
     }
 
     if (P.neval) {
@@ -510,7 +670,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_compo
 }
 
 template <int TW, int TH>
-static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas) {
+static cudaError_t resident_ctas(int* out) {
     constexpr int NT = TW * TH / 2;
     static int per_sm[64] = {0};  // resident CTAs per SM, per device
     static int sms[64] = {0};
@@ -519,16 +679,29 @@ static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (per_sm[dev] == 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[dev], k_composite<TW, TH>, NT, 0);
+        int ps = 0, n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_composite<TW, TH>, NT, 0);
         if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        if (per_sm[dev] < 1) per_sm[dev] = 1;
+        sms[dev] = n;
+        per_sm[dev] = ps < 1 ? 1 : ps;
     }
+    *out = per_sm[dev] * sms[dev];
+    return cudaSuccess;
+}
+
+template <int TW, int TH>
+static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas) {
+    constexpr int NT = TW * TH / 2;
+    int full = 0;
+    cudaError_t e = resident_ctas<TW, TH>(&full);
+    if (e != cudaSuccess) return e;
     const unsigned items = P.item_end - P.item_begin;
-    unsigned grid = (unsigned)(per_sm[dev] * sms[dev]);
+    unsigned grid = (unsigned)full;
     const unsigned claims = (items + P.chunk - 1) / P.chunk;
     if (grid > claims) grid = claims;
+    if (P.spill && grid > P.spill_ctas) grid = P.spill_ctas;
     if (grid == 0) grid = 1;
     *ctas = (int)grid;
     k_composite<TW, TH><<<grid, NT, 0, st>>>(P);
@@ -538,10 +711,19 @@ static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas)
 cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
     *ctas = 0;
     if (P.item_end <= P.item_begin) return cudaSuccess;
+    if (P.spill && (P.spill_cap < (unsigned)kCompCap || P.spill_cap > (unsigned)kSpillMax || P.spill_ctas == 0))
+        return cudaErrorInvalidValue;
     if (P.tile_w == 16 && P.tile_h == 16) return launch_tiles<16, 16>(P, st, ctas);
     if (P.tile_w == 8 && P.tile_h == 8) return launch_tiles<8, 8>(P, st, ctas);
     if (P.tile_w == 16 && P.tile_h == 8) return launch_tiles<16, 8>(P, st, ctas);
     return launch_tiles<32, 8>(P, st, ctas);
+}
+
+cudaError_t composite_max_ctas(int tile_w, int tile_h, int* ctas) {
+    if (tile_w == 16 && tile_h == 16) return resident_ctas<16, 16>(ctas);
+    if (tile_w == 8 && tile_h == 8) return resident_ctas<8, 8>(ctas);
+    if (tile_w == 16 && tile_h == 8) return resident_ctas<16, 8>(ctas);
+    return resident_ctas<32, 8>(ctas);
 }
 
 }  // namespace gsb

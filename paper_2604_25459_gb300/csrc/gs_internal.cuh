@@ -143,6 +143,9 @@ struct CompParams {
     unsigned long long pair_base;
     unsigned long long pair_cap;
     const unsigned long long* pairs;
+    unsigned long long* spill;       // nullable: spill_cap keys per CTA for partitioning long buckets
+    unsigned int spill_cap;          // kCompCap <= spill_cap <= kSpillMax
+    unsigned int spill_ctas;         // regions in spill: the launch uses at most this many CTAs
     unsigned long long* dbg_sorted;  // nullable: receives the full depth-ordered lists
     unsigned long long* neval;       // nullable: composited (pixel, Gaussian) pair counter
     int tile_w, tile_h;
@@ -167,6 +170,9 @@ cudaError_t launch_scan(const EnvInfo* envs, const uint32_t* counts, uint32_t* o
 cudaError_t launch_scatter(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st);
 // grid = persistent CTAs; returns the grid size used through *ctas
 cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas);
+// Most CTAs a compositing launch of this tile shape uses on the current
+// device (resident CTAs per SM x SMs): the number of spill regions to provide.
+cudaError_t composite_max_ctas(int tile_w, int tile_h, int* ctas);
 
 constexpr int kWordsPerBlock = 256;  // binning block: 8 warps x 32 visibility words (8192 slots)
 
@@ -175,6 +181,8 @@ constexpr int kWordsPerBlock = 256;  // binning block: 8 warps x 32 visibility w
 // buckets less often; 768 measured best on the 2048 x 640x480 workload
 // (1024: +2 %, 512: +4 %, 2048: +19 % compositing time).
 constexpr int kCompCap = 768;
+constexpr int kBins = 2048;         // key ranges of the long-bucket partition
+constexpr int kSpillMax = 32768;    // keys per CTA in the spill region, at most
 
 // Read-only view of a scene's device data for entry points outside gs_api.cu.
 struct SceneView {

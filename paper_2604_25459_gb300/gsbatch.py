@@ -74,7 +74,7 @@ class GsRequestResult(C.Structure):
 class GsServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("cancelled", C.c_int64),
                 ("batches", C.c_int64), ("peak_inflight_bytes", C.c_int64), ("max_concurrent", C.c_int32),
-                ("max_batch", C.c_int32)]
+                ("max_batch", C.c_int32), ("retried", C.c_int64)]
 
 
 _lib = None
@@ -424,9 +424,10 @@ class Server:
 
     def submit(self, env_id: int, link_poses=None, arrival_s: float = -1.0) -> int:
         p = None
-        if self._env_links[env_id] > 0:
+        nl = self._env_links[env_id] if 0 <= env_id < len(self._env_links) else 0  # the library checks env_id
+        if nl > 0:
             link_poses = np.ascontiguousarray(link_poses, dtype=np.float32)
-            if link_poses.size != self._env_links[env_id] * 7:
+            if link_poses.size != nl * 7:
                 raise ValueError("link_poses must hold 7 floats per link of the env")
             p = _ptr(link_poses)
         rid = C.c_int64()

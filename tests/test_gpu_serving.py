@@ -135,3 +135,54 @@ def test_cancel_and_argument_errors():
     sv.close()
     for s in scenes:
         s.close()
+
+
+def _in_front_of_camera(cam, n_links, dist=0.35):
+    """Link poses that put every link just in front of the camera (far more
+    intersections than the robot at its usual place)."""
+    from scipy.spatial.transform import Rotation
+
+    q = cam["q_cw"].astype(np.float64)
+    t = cam["t_cw"].astype(np.float64)
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    centre = -R.T @ t
+    fwd = R.T @ np.array([0.0, 0.0, 1.0])
+    p = np.zeros((n_links, 7), np.float32)
+    p[:, 0] = 1.0
+    p[:, 4:7] = centre + dist * fwd
+    return p
+
+
+def test_overflowing_estimate_is_rendered_again_exactly():
+    """Once the key estimates are learned, requests that need far more keys
+    overflow the planned capacity on the device; the scheduler renders those
+    batches again, exactly, before completing them."""
+    import torch
+
+    ensure_built()
+    w, scenes = _setup(n_envs=8)
+    E, L = w.n_envs, w.n_links
+    pa = w.request_poses(E, stream=4)
+    sv = _server(w, scenes, budget_bytes=8 << 30, max_inflight=2, max_batch_envs=8)
+    sv.start()
+    for rep in range(2):  # learn the estimates (the first batch of each kind is sized exactly)
+        for i in range(E):
+            sv.submit(i, pa[i])
+        sv.drain(300.0)
+    st0 = sv.stats()
+    near = {i: _in_front_of_camera(w.cams[i], L) for i in range(E)}
+    for i in range(E):
+        sv.submit(i, near[i])
+    sv.drain(300.0)
+    st = sv.stats()
+    print("overflow stats", st)
+    assert st["retried"] > st0["retried"]
+    res = sv.poll(1 << 12)
+    assert all(r["status"] == 0 for r in res)
+    for i in range(E):
+        ref = _alone(torch, scenes[int(w.env_scene[i])], w.cams[i], near[i][None], L)
+        rgb, depth = sv.env_output(i)
+        assert torch.equal(rgb.cpu(), ref[0]) and torch.equal(depth.cpu(), ref[1]), f"env {i}"
+    sv.close()
+    for s in scenes:
+        s.close()
