@@ -523,7 +523,7 @@ def run_c4(a, rank, world, local_rank):
         sweep.append({"offered_req_s": rate, "requests": n, "served_env_frames_s": len(ok) / span,
                       "p50_ms": _pct(lat, 0.50), "p99_ms": _pct(lat, 0.99), "max_ms": max(lat),
                       "batches": nb, "mean_batch": len(ok) / max(nb, 1), "max_batch": st1["max_batch"],
-                      "max_concurrent": st1["max_concurrent"],
+                      "max_concurrent": st1["max_concurrent"], "retried": st1["retried"] - st0["retried"],
                       "peak_inflight_gb": st1["peak_inflight_bytes"] / 1e9})
         print("c4 rate", json.dumps(sweep[-1]), file=sys.stderr, flush=True)
     ck = clocks.stop()

@@ -1035,6 +1035,15 @@ gs_status gs_plan_create(gs_scene s, int n_envs, const gs_env* envs, int flags, 
     p->s = s;
     p->flags = flags;
     p->envs.assign(envs, envs + n_envs);
+    // Render low-resolution envs first: their tiles have the longest buckets,
+    // so the persistent compositor claims them early instead of finishing on
+    // them.  Outputs are placed by pixel_offset, so the order is not visible.
+    std::stable_sort(p->envs.begin(), p->envs.end(), [](const gs_env& a, const gs_env& b) {
+        const int64_t pa = (int64_t)a.cam.width * a.cam.height, pb = (int64_t)b.cam.width * b.cam.height;
+        if (pa != pb) return pa < pb;
+        if (a.link_begin != b.link_begin) return a.link_begin < b.link_begin;
+        return a.link_end < b.link_end;
+    });
     p->tile_w = s->tile_w;
     p->tile_h = s->tile_h;
     std::vector<EnvSpec> specs;
@@ -1499,6 +1508,7 @@ struct gs_server_s {
     double inflight_bytes = 0;
     gs_server_stats stats{};
     std::map<std::tuple<int, int, int>, double> keys_ema;  // (scene, W, H) -> intersections per env
+    std::map<std::tuple<int, int, int>, double> keys_max;  // (scene, W, H) -> most seen for one env
     std::string error;
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1565,7 +1575,7 @@ gs_status server_launch(gs_server sv, gs_server_s::Slot& sl) {
     CK(sl.poses.ensure(pose_floats * 4), "alloc poses");
     CK(sl.dstat.ensure(8), "alloc status");
     std::vector<EnvSpec> specs(n);
-    double est = 0;
+    double est = 0, spread = 0;  // sum of the running averages; the largest (most seen - average)
     bool known = true;
     for (size_t i = 0; i < n; ++i) {
         const auto& rq = sv->reqs[batch[i]];
@@ -1576,6 +1586,8 @@ gs_status server_launch(gs_server sv, gs_server_s::Slot& sl) {
         const double k = keys_estimate(sv, ev);
         if (k < 0) known = false;
         est += k;
+        auto mt = sv->keys_max.find({ev.scene, ev.cam.width, ev.cam.height});
+        if (mt != sv->keys_max.end()) spread = std::max(spread, mt->second - k);
     }
     const bool eager = sl.eager || !known;
     sl.eager = eager;
@@ -1587,7 +1599,9 @@ gs_status server_launch(gs_server sv, gs_server_s::Slot& sl) {
                      sl.st, false, &wt));
     int64_t launches = 0;
     unsigned long long keys = 0;
-    const unsigned long long cap = eager ? 0ull : (unsigned long long)(est * 1.25) + 65536ull;
+    // capacity: 25% over the averages, plus room for one env at the most seen
+    // of its kind (what a batch of a few envs needs)
+    const unsigned long long cap = eager ? 0ull : (unsigned long long)(est * 1.25 + spread) + 65536ull;
     WaveIO io{sl.poses.as<float>(), sr.rgb.as<float>(), sr.depth.as<float>(), nullptr, 0, sl.dstat.as<uint32_t>()};
     ST(run_wave(s, sl.sc, wt, io, sv->cfg.tile_w, sv->cfg.tile_h, 1, cap, sl.st, false, &launches, &keys));
     CK(cudaMemcpyAsync(sl.h_meta, sl.dstat.p, 4, cudaMemcpyDeviceToHost, sl.st), "read status");
@@ -1605,9 +1619,12 @@ bool server_batch_done(gs_server sv, gs_server_s::Slot& sl, uint32_t* status_out
     for (size_t i = 0; i < sl.batch.size(); ++i) {
         const auto& ev = sv->envs[sv->reqs[sl.batch[i]].env];
         const double k = (double)(base[i + 1] - base[i]);
-        auto it = sv->keys_ema.find({ev.scene, ev.cam.width, ev.cam.height});
-        if (it == sv->keys_ema.end()) sv->keys_ema[{ev.scene, ev.cam.width, ev.cam.height}] = k;
+        const std::tuple<int, int, int> kind{ev.scene, ev.cam.width, ev.cam.height};
+        auto it = sv->keys_ema.find(kind);
+        if (it == sv->keys_ema.end()) sv->keys_ema[kind] = k;
         else it->second = 0.9 * it->second + 0.1 * k;
+        double& mx = sv->keys_max[kind];
+        mx = std::max(mx, k);
     }
     *status_out = st;
     return (st & kStOverflow) && !sl.eager;
