@@ -39,9 +39,9 @@ UNIT = "env-frames/s"
 # summarised in profiles/k_composite_c1.md (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 32-env launch, divided by 32), valid only for
 # the compositor sources it was taken on.
-COMPOSITE_TRAFFIC_PER_ENV = 1.2366e9 / 32
+COMPOSITE_TRAFFIC_PER_ENV = (1.186630e9 + 0.580130e9) / 32
 COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu", "paper_2604_25459_gb300/csrc/gs_internal.cuh")
-COMPOSITE_TRAFFIC_SHA = "d14f96d19f61c27a"
+COMPOSITE_TRAFFIC_SHA = "6401e993c33097c6"
 
 
 def _sources_sha(paths) -> str:
@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--oracle-envs", type=int, default=2, help="envs in the CPU-baseline sample")
+    ap.add_argument("--oracle-seconds", type=float, default=12.0,
+                    help="CPU-baseline sample: oracle envs rendered one by one until this much time has passed")
     ap.add_argument("--workload", choices=["c1", "c3", "c4"], default="c1",
                     help="c1: uniform 640x480 batch (headline); c3: batched uneven form through a plan")
     ap.add_argument("--no-graph", action="store_true", help="c3: eager plan launches instead of a CUDA graph")
@@ -141,8 +142,10 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
 
-def oracle_sample(w, envs, threads=None):
-    """Time the plain FP64 oracle on `envs` of workload w; returns (seconds, cores)."""
+def oracle_sample(w, envs, threads=None, budget_s=None):
+    """Time the plain FP64 oracle on `envs` of workload w, one env after the
+    other, stopping early once budget_s seconds have passed; returns (seconds,
+    cores, envs rendered)."""
     from oracle import oracle
 
     if threads:
@@ -150,9 +153,13 @@ def oracle_sample(w, envs, threads=None):
     cores = oracle.num_threads()
     S = oracle.scene_arrays(w)
     t0 = time.perf_counter()
+    done = 0
     for e in envs:
         oracle.render_env(w, e, S=S)
-    return time.perf_counter() - t0, cores
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 >= budget_s:
+            break
+    return time.perf_counter() - t0, cores, done
 
 
 def run_reference(a, rank, world):
@@ -166,7 +173,7 @@ def run_reference(a, rank, world):
     ts = []
     cores = 1
     for k in range(a.steps):
-        t, cores = oracle_sample(w, [(a.warmup + k) % a.envs])
+        t, cores, _ = oracle_sample(w, [(a.warmup + k) % a.envs])
         ts.append(t)
     tot = sum(ts)
     val = a.steps / tot
@@ -305,10 +312,10 @@ def run_ours(a, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        envs = list(range(a.oracle_envs))
-        t, cores = oracle_sample(w, envs)
-        cpu = {"value": len(envs) / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"envs {envs} of the same c1 batch, plain FP64 oracle, {t:.1f} s"}
+        t, cores, done = oracle_sample(w, list(range(E)), budget_s=a.oracle_seconds)
+        cpu = {"value": done / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"envs 0..{done - 1} of the same c1 batch rendered one by one by the plain FP64 oracle "
+                         f"({t:.1f} s of CPU time budgeted at {a.oracle_seconds:.0f} s)"}
 
     if rank == 0:
         lat_sorted = sorted(lat)
