@@ -252,9 +252,7 @@ __device__ __noinline__ void conic_factor_fp64(const LinkXf& X, const float4& a0
 // sqrt(15/(4 pi)), sqrt(5/(16 pi)), sqrt(15/(16 pi)), sqrt(35/(32 pi)),
 // sqrt(105/(4 pi)), sqrt(21/(32 pi)), sqrt(7/(16 pi)), sqrt(105/(16 pi)).
 template <int D>
-__device__ __forceinline__ void sh_colour(const float* sh, float x, float y, float z, float& r, float& g,
-                                          float& b) {
-    float Y[16];
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
     Y[0] = 0.28209479177387814f;
     if constexpr (D >= 1) {
         Y[1] = -0.4886025119029199f * y;
@@ -278,32 +276,31 @@ __device__ __forceinline__ void sh_colour(const float* sh, float x, float y, flo
             Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
         }
     }
-    constexpr int K = (D + 1) * (D + 1);
-    float cr = 0.0f, cg = 0.0f, cb = 0.0f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        cr += Y[k] * sh[3 * k];
-        cg += Y[k] * sh[3 * k + 1];
-        cb += Y[k] * sh[3 * k + 2];
-    }
-    r = fmaxf(cr + 0.5f, 0.0f);
-    g = fmaxf(cg + 0.5f, 0.0f);
-    b = fmaxf(cb + 0.5f, 0.0f);
 }
 
+// Colour max(0, sum_k Y_k sh_k + 0.5) per channel for Gaussian g.  The
+// coefficients are consumed plane by plane as they arrive (flattened value f
+// = 3k + channel), so only the basis and three sums stay live; each channel
+// accumulates in ascending k.
 template <int D, int DT>
-__device__ __forceinline__ void load_sh(const void* base, int64_t n, int64_t g, float* out) {
+__device__ __forceinline__ void sh_colour(const void* base, int64_t n, int64_t g, float x, float y, float z,
+                                          float& r, float& gr, float& b) {
     constexpr int NV = 3 * (D + 1) * (D + 1);
+    float Y[16];
+    sh_basis<D>(x, y, z, Y);
+    float acc[3] = {0.0f, 0.0f, 0.0f};
     if constexpr (DT == GS_F32) {
         constexpr int NP = (NV + 3) / 4;
         const float4* P = static_cast<const float4*>(base);
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             const float4 v = __ldg(P + (size_t)p * n + g);
-            out[4 * p] = v.x;
-            if (4 * p + 1 < NV) out[4 * p + 1] = v.y;
-            if (4 * p + 2 < NV) out[4 * p + 2] = v.z;
-            if (4 * p + 3 < NV) out[4 * p + 3] = v.w;
+            const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int f = 4 * p + h;
+                if (f < NV) acc[f % 3] += Y[f / 3] * w[h];
+            }
         }
     } else {
         constexpr int NP = (NV + 7) / 8;
@@ -317,14 +314,19 @@ __device__ __forceinline__ void load_sh(const void* base, int64_t n, int64_t g, 
                 const int f = 8 * p + h;
                 if (f < NV) {
                     const uint16_t bits = (uint16_t)(w[h >> 1] >> (16 * (h & 1)));
+                    float val;
                     if constexpr (DT == GS_BF16)
-                        out[f] = __uint_as_float((uint32_t)bits << 16);
+                        val = __uint_as_float((uint32_t)bits << 16);
                     else
-                        out[f] = __half2float(__ushort_as_half(bits));
+                        val = __half2float(__ushort_as_half(bits));
+                    acc[f % 3] += Y[f / 3] * val;
                 }
             }
         }
     }
+    r = fmaxf(acc[0] + 0.5f, 0.0f);
+    gr = fmaxf(acc[1] + 0.5f, 0.0f);
+    b = fmaxf(acc[2] + 0.5f, 0.0f);
 }
 
 // Pixel range [lo, hi] of a support interval centred at c with half extent h:
@@ -362,7 +364,6 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
     const float qstar = a3.y;
     const bool live = act && qstar >= 0.0f;
     const float trace = a3.z;  // trace(Sigma) >= its largest eigenvalue (rotation-invariant)
-    float sh[NV];
     for (int el = blk.e0; el < blk.e1; ++el) {
         bool vis = false;
         const EnvInfo* E = P.envs + el;
@@ -424,9 +425,8 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                     const float hy = sqrtf(qstar * cC) * 1.0001f;
                     int i0, i1, j0, j1;
                     if (ok && pixel_range(u, hx, W, i0, i1) && pixel_range(v, hy, H, j0, j1)) {
-                        // reloaded per visible env (L1/L2 hits): keeping all SH
-                        // coefficients live across the env loop costs more occupancy
-                        load_sh<D, DT>(P.sh, P.n_gauss, g, sh);
+                        // SH coefficients are re-read per visible env (L1/L2 hits) and
+                        // streamed into the colour sums
                         const float4 O = __ldg(&Xp->o);
                         float dx = a0.x - O.x, dy = a0.y - O.y, dz = a0.z - O.z;
                         const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                         dy *= inv;
                         dz *= inv;
                         float r, gg, b;
-                        sh_colour<D>(sh, dx, dy, dz, r, gg, b);
+                        sh_colour<D, DT>(P.sh, P.n_gauss, g, dx, dy, dz, r, gg, b);
                         const uint32_t rx = (uint32_t)i0 | ((uint32_t)i1 << 16);
                         const uint32_t ry = (uint32_t)j0 | ((uint32_t)j1 << 16);
                         const size_t ri = (size_t)__ldg(&E->rec_base) + local;
