@@ -62,8 +62,20 @@ __device__ __forceinline__ void block_histogram(const BinParams& P, const EnvInf
         const uint4 q = r3[j];
         int tx0, tx1, ty0, ty1;
         tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * E.ntx + tx], 1u);
+        // one flat loop over the span (lanes with spans of different shapes
+        // then diverge only by their tile counts)
+        const int n = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+        int tx = tx0, t = ty0 * E.ntx + tx0;
+        for (int k = 0; k < n; ++k) {
+            atomicAdd(&hist[t], 1u);
+            if (tx == tx1) {
+                tx = tx0;
+                t += E.ntx - (tx1 - tx0);
+            } else {
+                ++tx;
+                ++t;
+            }
+        }
     });
 }
 
@@ -216,14 +228,21 @@ __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
         const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)(uint32_t)j;
         int tx0, tx1, ty0, ty1;
         tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                const int t = ty * E.ntx + tx;
-                const uint32_t k = atomicAdd(&hist[t], 1u);
-                const unsigned long long pos = eb + base[t] + k;
-                if (pos < P.pair_cap) P.pairs[pos] = key;
-                else dropped = true;
+        const int n = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+        int tx = tx0, t = ty0 * E.ntx + tx0;
+        for (int i = 0; i < n; ++i) {
+            const uint32_t k = atomicAdd(&hist[t], 1u);
+            const unsigned long long pos = eb + base[t] + k;
+            if (pos < P.pair_cap) P.pairs[pos] = key;
+            else dropped = true;
+            if (tx == tx1) {
+                tx = tx0;
+                t += E.ntx - (tx1 - tx0);
+            } else {
+                ++tx;
+                ++t;
             }
+        }
     });
     if (__syncthreads_or(dropped) && threadIdx.x == 0) atomicOr(P.status, kStOverflow);
 }
