@@ -77,14 +77,105 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* re
 // hits 32 different banks across a warp.
 __device__ __forceinline__ int cidx(int e) { return e + ((e >> 4) << 1); }
 
+constexpr int kSortBins = 1024;  // depth ranges of the window counting sort
+
+// Block-wide min and max of one u32 per thread; red holds 32 words.
+template <int NT>
+__device__ __forceinline__ void block_minmax_u32(uint32_t& mn, uint32_t& mx, uint32_t* red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) {
+        red[warp] = mn;
+        red[16 + warp] = mx;
+    }
+    __syncthreads();
+    mn = red[0];
+    mx = red[16];
+    for (int w = 1; w < NT / 32; ++w) {
+        mn = red[w] < mn ? red[w] : mn;
+        mx = red[16 + w] > mx ? red[16 + w] : mx;
+    }
+    __syncthreads();
+}
+
+// Sort keys[0, n) into tmp when the window's depths spread out: a counting
+// sort by kSortBins equal ranges of the depth bits, then an insertion sort of
+// each range by whole keys (equal depths fall in index order).  Applies when
+// no range holds more than 32 keys; returns tmp then, else nullptr with keys
+// untouched.  c32: kSortBins u32; red: 32 u32.
+template <int NT>
+__device__ unsigned long long* bin_sort(const unsigned long long* keys, unsigned long long* tmp, uint32_t* c32,
+                                        uint32_t* red, int n) {
+    constexpr int PER = kSortBins / NT;
+    static_assert(kSortBins % NT == 0, "ranges per thread");
+    const int tid = threadIdx.x;
+    uint32_t zmin = 0xffffffffu, zmax = 0u;
+    for (int i = tid; i < n; i += NT) {
+        const uint32_t z = (uint32_t)(keys[i] >> 32);
+        zmin = z < zmin ? z : zmin;
+        zmax = z > zmax ? z : zmax;
+    }
+    block_minmax_u32<NT>(zmin, zmax, red);
+    const uint32_t span = zmax - zmin;
+    const int shift = (span >> 10) ? 22 - __clz(span) : 0;  // span >> shift < kSortBins
+    for (int b = tid; b < kSortBins; b += NT) c32[b] = 0u;
+    __syncthreads();
+    for (int i = tid; i < n; i += NT) atomicAdd(&c32[((uint32_t)(keys[i] >> 32) - zmin) >> shift], 1u);
+    __syncthreads();
+    uint32_t loc[PER];
+    uint32_t sum = 0;
+    bool crowded = false;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        loc[j] = c32[tid * PER + j];
+        sum += loc[j];
+        crowded |= loc[j] > 32u;
+    }
+    if (__syncthreads_or(crowded)) return nullptr;
+    uint32_t run = block_excl_scan_u32<NT>(sum, red);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        c32[tid * PER + j] = run;
+        run += loc[j];
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += NT) {
+        const unsigned long long k = keys[i];
+        const uint32_t pos = atomicAdd(&c32[((uint32_t)(k >> 32) - zmin) >> shift], 1u);
+        tmp[pos] = k;
+    }
+    __syncthreads();
+    // range b is now [c32[b-1], c32[b]) (c32 holds each range's end)
+#pragma unroll 1
+    for (int j = 0; j < PER; ++j) {
+        const int b = tid * PER + j;
+        const int e = (int)c32[b];
+        const int a = b ? (int)c32[b - 1] : 0;
+        for (int x = a + 1; x < e; ++x) {
+            const unsigned long long k = tmp[x];
+            int y = x - 1;
+            while (y >= a && tmp[y] > k) {
+                tmp[y + 1] = tmp[y];
+                --y;
+            }
+            tmp[y + 1] = k;
+        }
+    }
+    __syncthreads();
+    return tmp;
+}
+
 // Sort keys[0, n) ascending by the full 64-bit key (depth bits high, global
-// index low; all distinct), n <= kCompCap.  LSD radix passes of 4 bits over
-// the depth bits that differ inside the window give a stable order by depth;
-// runs of equal depth are then ordered by index.  Returns the array that
-// holds the result (keys or tmp).  cnt: cidx(16*NT) u16; red: NT/32 u32.
+// index low; all distinct), n <= kCompCap.  bin_sort when the depths spread
+// out; otherwise LSD radix passes of 4 bits over the depth bits that differ
+// inside the window give a stable order by depth, and runs of equal depth are
+// then ordered by index.  Returns the array that holds the result (keys or
+// tmp).  cnt: cidx(16*NT) u16 and at least kSortBins u32; red: 32 u32.
 template <int NT>
 __device__ unsigned long long* window_sort(unsigned long long* keys, unsigned long long* tmp, uint16_t* cnt,
                                            uint32_t* red, int n) {
+    if (unsigned long long* r = bin_sort<NT>(keys, tmp, reinterpret_cast<uint32_t*>(cnt), red, n)) return r;
     const int tid = threadIdx.x;
     const int I = (n + NT - 1) / NT;  // keys per thread, blocked arrangement
     const int b0 = tid * I;
@@ -220,7 +311,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_compo
     constexpr int CAP = kCompCap;
     constexpr int HALF = kCompCap / 2;
     constexpr int UB = (CAP * 8 > NB * 64) ? CAP * 8 : NB * 64;
-    constexpr int CB = (18 * NT * 2 > 256 * 4) ? 18 * NT * 2 : 256 * 4;
+    constexpr int CB = (18 * NT * 2 > kSortBins * 4) ? 18 * NT * 2 : kSortBins * 4;  // >= selection histogram
     constexpr int NW = NT / 32;
     static_assert(CAP * 8 + UB >= kBins * 4, "bin counters alias the key and staging buffers");
     static_assert(kBins % NT == 0, "bins per thread");
