@@ -290,6 +290,36 @@ __device__ __forceinline__ float splat_alpha(const float4& A, const float4& B, f
     return fminf(0.99f, __fmul_rn(A.z, ex2_approx(pw)));
 }
 
+// Whether a splat can reach alpha >= 1/255 at any pixel centre of the 8x8
+// subtile whose first centre is (x0, y0): the minimum of its quadratic form
+// q = (l00 dx + l01 dy)^2 + (l11 dy)^2 over the rectangle spanned by the
+// centres, against log2(255 o) (B.w).  q is convex, so with the splat centre
+// outside the rectangle the minimum lies on an edge, where it is the clamped
+// stationary point of a 1D quadratic.  The test only skips splats that no
+// pixel of the subtile blends: it keeps a relative margin of 1e-3 plus 1e-3
+// on the threshold, far above the rounding of q here and in the blend loop.
+__device__ __forceinline__ bool reaches_rect(const float4& A, const float4& B, float x0, float y0) {
+    const float ax = x0 - A.x, bx = ax + 7.0f;  // dx range
+    const float ay = y0 - A.y, by = ay + 7.0f;  // dy range
+    if (ax <= 0.0f && bx >= 0.0f && ay <= 0.0f && by >= 0.0f) return true;
+    const float l00 = B.x, l01 = B.y, l11 = B.z;
+    auto q = [&](float dx, float dy) {
+        const float t = fmaf(l01, dy, l00 * dx);
+        const float u = l11 * dy;
+        return fmaf(t, t, u * u);
+    };
+    // vertical edges dx = const: stationary dy = -l00 l01 dx / (l01^2 + l11^2)
+    const float kv = -l00 * l01 / fmaf(l01, l01, l11 * l11);
+    // horizontal edges dy = const: stationary dx = -l01 dy / l00
+    const float kh = -l01 / l00;
+    const float q1 = q(ax, fminf(fmaxf(kv * ax, ay), by));
+    const float q2 = q(bx, fminf(fmaxf(kv * bx, ay), by));
+    const float q3 = q(fminf(fmaxf(kh * ay, ax), bx), ay);
+    const float q4 = q(fminf(fmaxf(kh * by, ax), bx), by);
+    const float qmin = fminf(fminf(q1, q2), fminf(q3, q4));
+    return qmin <= fmaf(B.w, 1.001f, 1e-3f);
+}
+
 // Persistent CTAs of TW*TH/2 threads claim (env, tile) items from a work
 // counter, `chunk` consecutive items at a time (items run env-major, tiles
 // row-major, so envs of any resolution mix in one launch).  For an item the
@@ -409,7 +439,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_compo
                     const float4 q2 = P.r2[ri];
                     const uint32_t rx = __float_as_uint(q1.w), ry = __float_as_uint(q2.w);
                     sA[s] = q0;
-                    sB[s] = make_float4(q1.x, q1.y, q1.z, 0.0f);
+                    sB[s] = make_float4(q1.x, q1.y, q1.z, log2f(255.0f * q0.z));  // alpha >= 1/255 iff q <= w
                     sC[s] = q2;
                     sR[s] = make_int4((int)(rx & 0xffffu), (int)((rx >> 16) - (rx & 0xffffu)), (int)(ry & 0xffffu),
                                       (int)((ry >> 16) - (ry & 0xffffu)));
@@ -429,6 +459,9 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_compo
                     if (j < cnt_b) {
                         const int4 R = sR[j];
                         ov = R.x <= wx1 && R.x + R.y >= wx0 && R.z <= wy1 && R.z + R.w >= wy0;
+                        // large splats: their box overstates the ellipse most (a box
+                        // under 24 px in width + height is kept as it is)
+                        if (ov && R.y + R.w >= 24) ov = reaches_rect(sA[j], sB[j], (float)wx0 + 0.5f, (float)wy0 + 0.5f);
                     }
                     uint32_t m = __ballot_sync(0xffffffffu, ov);
                     // two splats per iteration: their four alpha evaluations are
