@@ -41,7 +41,7 @@ UNIT = "env-frames/s"
 # the compositor sources it was taken on.
 COMPOSITE_TRAFFIC_PER_ENV = (1.167529e9 + 0.593587e9) / 32
 COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu", "paper_2604_25459_gb300/csrc/gs_internal.cuh")
-COMPOSITE_TRAFFIC_SHA = "c48d78b8446dd1bf"
+COMPOSITE_TRAFFIC_SHA = "af9d1a44b02932ed"
 
 
 def _sources_sha(paths) -> str:
@@ -224,6 +224,8 @@ def run_ours(a, rank, world, local_rank):
     torch.cuda.synchronize()
     st = scene.stats()
     n_eval = st["composited"]
+    n_vis = st["visible"]
+    n_pairs = st["n_gaussians"] * E  # (env, Gaussian) pairs tested
     intersections = st["intersections"]
     launches_per_step = st["kernel_launches"]
     scene.set_counters(False)
@@ -271,7 +273,13 @@ def run_ours(a, rank, world, local_rank):
     traffic = None
     if _sources_sha(COMPOSITE_TRAFFIC_SOURCES) == COMPOSITE_TRAFFIC_SHA:
         traffic = COMPOSITE_TRAFFIC_PER_ENV * E / max(launches_per_batch, 1)  # bytes per launch
+    try:  # measured plain-ALU rates, reported beside the derived peak
+        alu = gsbatch.measure_alu_peak(stream)
+    except Exception as ex:  # noqa: BLE001
+        alu = {"error": str(ex)}
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_lane_ops / 1e9, "unit": "Glane-op/s",
+                "measured_fma_glane_ops": alu.get("fma_lane_ops_per_s", 0.0) / 1e9,
+                "measured_ex2_glane_ops": alu.get("ex2_lane_ops_per_s", 0.0) / 1e9,
                 "frac": achieved / peak_lane_ops, "traffic": traffic,
                 "kernel": "k_composite", "per_launch_ms": per_launch_ms,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x median {sm_mhz:.0f} MHz "
@@ -288,6 +296,19 @@ def run_ours(a, rank, world, local_rank):
     attr_bytes = (w.background.n + w.links.n) * (236 if a.dtype == "f32" else 132)
     out_bytes = E * H * W * 16
     io_bytes = attr_bytes + E * (w.n_links * 28 + 56) + out_bytes
+
+    # whole step: time floor = max(algorithmic bytes / HBM peak, algorithmic FP32 work / ALU peak), the
+    # work being N_eval x 20 (compositing) + E G x 20 (culling every pair) + E V x 300 (projecting the
+    # visible pairs: covariance, conic, SH degree 3)
+    fp32_ops = n_eval * 20.0 + n_pairs * 20.0 + n_vis * 300.0
+    hbm_floor_ms = io_bytes / (hbm * 1e9) * 1e3
+    alu_floor_ms = fp32_ops / peak_lane_ops * 1e3
+    step_roofline = {"io_bytes": io_bytes, "hbm_floor_ms": hbm_floor_ms, "hbm_gbs_peak": hbm,
+                     "fp32_lane_ops": fp32_ops, "alu_floor_ms": alu_floor_ms,
+                     "bound": "alu" if alu_floor_ms > hbm_floor_ms else "hbm",
+                     "frac": max(alu_floor_ms, hbm_floor_ms) / ms_step,
+                     "composited_pairs": n_eval, "visible_pairs": n_vis, "tested_pairs": n_pairs,
+                     "intersections": intersections}
 
     e2e = None
     if not a.no_e2e:
@@ -333,9 +354,7 @@ def run_ours(a, rank, world, local_rank):
                            "mean": sum(lat) / len(lat)},
             "clocks": ck,
             "roofline": roofline,
-            "step_roofline": {"io_bytes": io_bytes, "hbm_floor_ms": io_bytes / (hbm * 1e9) * 1e3,
-                              "hbm_gbs_peak": hbm, "composited_pairs": n_eval,
-                              "intersections": intersections},
+            "step_roofline": step_roofline,
             "phase_ms_per_step": phase_ms,
             "gpu_launches": int(launches_per_step * a.steps),
             "e2e": e2e,

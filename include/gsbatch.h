@@ -230,6 +230,8 @@ typedef struct {
     int64_t n_gaussians;    /* background + link Gaussians */
     int64_t composited;     /* with counters on: (pixel, Gaussian) pairs with alpha >= 1/255
                                examined before termination, summed since counters were enabled */
+    int64_t visible;        /* with counters on: (env, Gaussian) pairs projected to a record
+                               (non-empty support on screen), summed since counters were enabled */
 } gs_stats;
 /* Synchronises the device when counters are on (to read the device counter). */
 gs_status gs_scene_get_stats(gs_scene s, gs_stats* out);
@@ -374,6 +376,13 @@ gs_status gs_server_env_output(gs_server sv, int env_id, float** rgb, float** de
 /* Stop the scheduler (requests not yet admitted are dropped), wait for the
  * batches in flight and free everything the server owns (NULL is a no-op). */
 void gs_server_destroy(gs_server sv);
+
+/* Measurement support (no paper counterpart): the current device's plain-ALU
+ * rates, from two short microbenchmarks on cuda_stream (synchronises it):
+ * FP32 FMA lane-ops/s (independent fmaf chains) and MUFU ex2 lane-ops/s
+ * (ex2.approx chains), each the best of three timed runs after a warm-up.
+ * The compositor is bound by these two pipes.  GS_ERR_CUDA on failure. */
+gs_status gs_measure_alu_peak(double* fma_lane_ops_per_s, double* ex2_lane_ops_per_s, void* cuda_stream);
 
 /* Thread-local description of the last failure ("" if none). */
 const char* gs_last_error(void);

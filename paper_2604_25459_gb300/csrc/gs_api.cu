@@ -496,6 +496,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     P.r3 = sc.r3.as<uint4>();
     P.mask = sc.mask.as<uint32_t>();
     P.dbg_hxy = debug ? sc.dbg_hxy.as<float2>() : nullptr;
+    P.nvis = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() + 1 : nullptr;
     PhaseTimer t2(s, st, GS_PHASE_PROJECT, timers);
     CK(launch_project(s->D, P, wt.n_blocks, st), "projection");
     t2.done(1);
@@ -1268,8 +1269,8 @@ gs_status gs_scene_set_counters(gs_scene s, int enable) {
     s->counters = enable ? 1 : 0;
     if (s->counters) {
         CK(cudaSetDevice(s->device), "set device");
-        CK(s->neval.ensure(8), "alloc counter");
-        CK(cudaMemset(s->neval.p, 0, 8), "clear counter");
+        CK(s->neval.ensure(16), "alloc counters");
+        CK(cudaMemset(s->neval.p, 0, 16), "clear counters");
     }
     return GS_OK;
 }
@@ -1313,12 +1314,14 @@ gs_status gs_scene_get_stats(gs_scene s, gs_stats* out) {
     for (const DevBuf* b : bufs) bytes += (int64_t)b->bytes;
     s->stats.scratch_bytes = bytes;
     s->stats.composited = 0;
+    s->stats.visible = 0;
     if (s->counters && s->neval.p) {
         CK(cudaSetDevice(s->device), "set device");
         CK(cudaDeviceSynchronize(), "sync");
-        unsigned long long c = 0;
-        CK(cudaMemcpy(&c, s->neval.p, 8, cudaMemcpyDeviceToHost), "read counter");
-        s->stats.composited = (int64_t)c;
+        unsigned long long c[2] = {0, 0};
+        CK(cudaMemcpy(c, s->neval.p, 16, cudaMemcpyDeviceToHost), "read counters");
+        s->stats.composited = (int64_t)c[0];
+        s->stats.visible = (int64_t)c[1];
     }
     *out = s->stats;
     return GS_OK;

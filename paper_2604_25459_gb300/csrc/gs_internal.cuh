@@ -109,6 +109,7 @@ struct ProjParams {
     uint4* r3;
     uint32_t* mask;
     float2* dbg_hxy;  // nullable, per record slot
+    unsigned long long* nvis;  // nullable: visible (env, Gaussian) pair counter
 };
 
 struct BinParams {

@@ -449,7 +449,10 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
             }
         }
         const uint32_t m = __ballot_sync(0xffffffffu, vis);
-        if (lane == 0 && warp_live) P.mask[(size_t)__ldg(&E->mask_base) + (local >> 5)] = m;
+        if (lane == 0 && warp_live) {
+            P.mask[(size_t)__ldg(&E->mask_base) + (local >> 5)] = m;
+            if (P.nvis && m) atomicAdd(P.nvis, (unsigned long long)__popc(m));
+        }
     }
 }
 

@@ -38,7 +38,8 @@ class GsGaussians(C.Structure):
 
 class GsStats(C.Structure):
     _fields_ = [("waves", C.c_int64), ("kernel_launches", C.c_int64), ("intersections", C.c_int64),
-                ("scratch_bytes", C.c_int64), ("n_gaussians", C.c_int64), ("composited", C.c_int64)]
+                ("scratch_bytes", C.c_int64), ("n_gaussians", C.c_int64), ("composited", C.c_int64),
+                ("visible", C.c_int64)]
 
 
 PHASES = ("link", "project", "count", "scan", "scatter", "composite")
@@ -115,6 +116,7 @@ _SIGS = {
     "gs_server_env_output": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "gs_server_now": (C.c_double, [C.c_void_p]),
     "gs_server_destroy": (None, [C.c_void_p]),
+    "gs_measure_alu_peak": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "gs_last_error": (C.c_char_p, []),
     "gs_version": (C.c_char_p, []),
 }
@@ -480,6 +482,13 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def measure_alu_peak(stream=None) -> dict:
+    """Measured FP32 FMA and MUFU ex2 lane-op rates of the current device."""
+    f, e = C.c_double(), C.c_double()
+    _check(lib().gs_measure_alu_peak(C.byref(f), C.byref(e), _stream_handle(stream)))
+    return {"fma_lane_ops_per_s": f.value, "ex2_lane_ops_per_s": e.value}
 
 
 def make_envs(cams: np.ndarray, link_ranges=None, pose_offsets=None) -> np.ndarray:
