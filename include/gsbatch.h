@@ -149,7 +149,7 @@ gs_status gs_render_batch_v(gs_scene s, int n_envs, const gs_env* envs, const fl
 
 /* A plan is a fixed batch (environments, resolutions, link subsets) rendered
  * repeatedly with changing poses.  Its first launch runs eagerly: with
- * GS_PLAN_AUTOTUNE it times every tile shape (8x8, 16x8, 16x16, 32x8) and
+ * GS_PLAN_AUTOTUNE it times every tile shape (8x8, 16x8, 16x16, 32x8, 32x16) and
  * compositor claim size (1 or 4 tiles per atomic) and keeps the fastest (the
  * images do not depend on the choice); it sizes the intersection-key buffer at
  * 1.25x what that launch needed.  With GS_PLAN_GRAPH the whole render (all
@@ -203,7 +203,7 @@ gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float* link_pose
                                   float* rgb, float* depth, float* alpha, void* cuda_stream);
 
 /* Tile shape used by the binning and compositing kernels.  Allowed:
- * 8x8, 16x8, 16x16, 32x8 (tw x th).  Results do not depend on the tile shape
+ * 8x8, 16x8, 16x16, 32x8, 32x16 (tw x th).  Results do not depend on the tile shape
  * (each splat's support box is inflated by a relative 1e-4 so every tile it
  * may reach sees it).  Default 16x16. */
 gs_status gs_scene_set_tile(gs_scene s, int tile_w, int tile_h);
@@ -319,7 +319,7 @@ typedef struct {
     int64_t budget_bytes;  /* device working-set budget of the batches in flight (>= 1 MiB) */
     int max_inflight;      /* stream slots, 1..64 */
     int max_batch_envs;    /* requests per batch, >= 1 */
-    int tile_w, tile_h;    /* tile shape: 8x8, 16x8, 16x16 or 32x8 */
+    int tile_w, tile_h;    /* tile shape: 8x8, 16x8, 16x16, 32x8 or 32x16 */
 } gs_server_config;
 
 typedef struct {

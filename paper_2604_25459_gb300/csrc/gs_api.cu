@@ -99,7 +99,8 @@ struct Scratch {
 };
 
 bool valid_tile(int tw, int th) {
-    return (tw == 8 && th == 8) || (tw == 16 && th == 8) || (tw == 16 && th == 16) || (tw == 32 && th == 8);
+    return (tw == 8 && th == 8) || (tw == 16 && th == 8) || (tw == 16 && th == 16) || (tw == 32 && th == 8) ||
+           (tw == 32 && th == 16);
 }
 
 }  // namespace
@@ -1105,7 +1106,7 @@ gs_status gs_plan_launch(gs_plan p, const float* link_poses, float* rgb, float* 
         };
         std::vector<Cand> cands;
         if (p->flags & GS_PLAN_AUTOTUNE) {
-            const int shapes[4][2] = {{16, 16}, {32, 8}, {16, 8}, {8, 8}};
+            const int shapes[5][2] = {{16, 16}, {32, 8}, {16, 8}, {8, 8}, {32, 16}};
             for (auto& sh : shapes)
                 for (int ch : {1, 4}) cands.push_back({sh[0], sh[1], ch});
         } else {
@@ -1222,7 +1223,7 @@ void gs_plan_destroy(gs_plan p) {
 
 gs_status gs_scene_set_tile(gs_scene s, int tw, int th) {
     if (!s) return fail(GS_ERR_INVALID, "null scene");
-    if (!valid_tile(tw, th)) return fail(GS_ERR_INVALID, "tile %dx%d not one of 8x8, 16x8, 16x16, 32x8", tw, th);
+    if (!valid_tile(tw, th)) return fail(GS_ERR_INVALID, "tile %dx%d not one of 8x8, 16x8, 16x16, 32x8, 32x16", tw, th);
     s->tile_w = tw;
     s->tile_h = th;
     return GS_OK;

@@ -335,7 +335,7 @@ __device__ __forceinline__ bool reaches_rect(const float4& A, const float4& B, f
 // long bucket when there is no spill region) is cut into windows by radix
 // selection over its keys instead.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 256 ? 8 : 12)) k_composite(CompParams P) {
+__global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 256 ? 8 : 12))) k_composite(CompParams P) {
     constexpr int NT = TW * TH / 2;
     constexpr int NB = NT;  // splats staged per batch (one per thread)
     constexpr int CAP = kCompCap;
@@ -838,6 +838,7 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
     if (P.spill && (P.spill_cap < (unsigned)kCompCap || P.spill_cap > (unsigned)kSpillMax || P.spill_ctas == 0))
         return cudaErrorInvalidValue;
     if (P.tile_w == 16 && P.tile_h == 16) return launch_tiles<16, 16>(P, st, ctas);
+    if (P.tile_w == 32 && P.tile_h == 16) return launch_tiles<32, 16>(P, st, ctas);
     if (P.tile_w == 8 && P.tile_h == 8) return launch_tiles<8, 8>(P, st, ctas);
     if (P.tile_w == 16 && P.tile_h == 8) return launch_tiles<16, 8>(P, st, ctas);
     return launch_tiles<32, 8>(P, st, ctas);
@@ -845,6 +846,7 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
 
 cudaError_t composite_max_ctas(int tile_w, int tile_h, int* ctas) {
     if (tile_w == 16 && tile_h == 16) return resident_ctas<16, 16>(ctas);
+    if (tile_w == 32 && tile_h == 16) return resident_ctas<32, 16>(ctas);
     if (tile_w == 8 && tile_h == 8) return resident_ctas<8, 8>(ctas);
     if (tile_w == 16 && tile_h == 8) return resident_ctas<16, 8>(ctas);
     return resident_ctas<32, 8>(ctas);

@@ -69,7 +69,7 @@ def test_c0_projection_records():
     np.testing.assert_allclose(rec["opacity"][both], p["opacity"][both], rtol=1e-7)
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (16, 8)])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (16, 8), (32, 16)])
 def test_binning_keyed_bit_exact(tile):
     """Counts and depth-ordered per-tile lists equal the binning oracle fed the
     GPU's (u, v, hx, hy, depth bits, index), for a scene whose dense tiles have
@@ -106,7 +106,7 @@ def test_tile_shape_and_batch_invariance_bit_exact():
     other envs share the batch."""
     w = synth.make_c1(n_envs=6, width=96, height=72, f=75.0, n_bg=40_000, per_link=1000)
     base = gpu_render(w)
-    for tile in ((8, 8), (32, 8), (16, 8)):
+    for tile in ((8, 8), (32, 8), (16, 8), (32, 16)):
         o = gpu_render(w, tile=tile)
         for k in ("rgb", "depth", "alpha"):
             np.testing.assert_array_equal(o[k], base[k], err_msg=f"{k} {tile}")

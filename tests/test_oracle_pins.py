@@ -385,7 +385,7 @@ def test_bin_oracle_against_brute_enumeration():
     z[:20] = z[20:40]  # exact depth ties
     zb = z.view(np.uint32)
     gidx = rng.permutation(10 * n)[:n].astype(np.uint32)
-    for tw, th in ((8, 8), (16, 16), (32, 8), (16, 8)):
+    for tw, th in ((8, 8), (16, 16), (32, 8), (16, 8), (32, 16)):
         counts, lists = oracle.bin_records(u, v, hx, hy, zb, gidx, W, H, tw, th)
         ntx, nty = -(-W // tw), -(-H // th)
         off = 0
