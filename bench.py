@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--workload", choices=["c1", "c3", "c4"], default="c1",
                     help="c1: uniform 640x480 batch (headline); c3: batched uneven form through a plan")
     ap.add_argument("--no-graph", action="store_true", help="c3: eager plan launches instead of a CUDA graph")
+    ap.add_argument("--obs", action="store_true",
+                    help="c1 in the observation form: 8-bit RGB after per-env appearance randomisation + half depth")
     ap.add_argument("--rates", default="1000,3000,10000,30000", help="c4: offered request rates (req/s)")
     ap.add_argument("--duration", type=float, default=2.0, help="c4: seconds of arrivals per rate")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="c4: HBM budget of the request loop")
@@ -207,12 +209,23 @@ def run_ours(a, rank, world, local_rank):
     scene = gsbatch.scene_from_workload(w, a.dtype)
     scene.set_tile(tw, th)
     poses = torch.from_numpy(w.link_poses).to(dev)
-    rgb = torch.empty((E, H, W, 3), dtype=torch.float32, device=dev)
-    depth = torch.empty((E, H, W), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    if a.obs:  # observation form: per-env exposure, contrast, brightness
+        arng = np.random.default_rng([a.envs, 91])
+        ap_h = np.stack([arng.uniform(-0.5, 0.5, E), arng.uniform(0.7, 1.3, E), arng.uniform(-0.1, 0.1, E)],
+                        1).astype(np.float32)
+        ap_d = torch.from_numpy(ap_h).to(dev)
+        rgb8 = torch.empty((E, H, W, 3), dtype=torch.uint8, device=dev)
+        depth16 = torch.empty((E, H, W), dtype=torch.float16, device=dev)
 
-    def step():
-        scene.render(poses, w.cams, rgb=rgb, depth=depth, want_alpha=False, stream=stream)
+        def step():
+            scene.render_obs(poses, w.cams, appearance=ap_d, rgb8=rgb8, depth16=depth16, stream=stream)
+    else:
+        rgb = torch.empty((E, H, W, 3), dtype=torch.float32, device=dev)
+        depth = torch.empty((E, H, W), dtype=torch.float32, device=dev)
+
+        def step():
+            scene.render(poses, w.cams, rgb=rgb, depth=depth, want_alpha=False, stream=stream)
 
     for _ in range(a.warmup):
         step()
@@ -294,7 +307,7 @@ def run_ours(a, rank, world, local_rank):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     attr_bytes = (w.background.n + w.links.n) * (236 if a.dtype == "f32" else 132)
-    out_bytes = E * H * W * 16
+    out_bytes = E * H * W * (6 if a.obs else 16)
     io_bytes = attr_bytes + E * (w.n_links * 28 + 56) + out_bytes
 
     # whole step: time floor = max(algorithmic bytes / HBM peak, algorithmic FP32 work / ALU peak), the
@@ -312,15 +325,20 @@ def run_ours(a, rank, world, local_rank):
 
     e2e = None
     if not a.no_e2e:
-        pin = lambda shape: torch.empty(shape, dtype=torch.float32, pin_memory=True).numpy()
-        rgb_h, depth_h = pin((E, H, W, 3)), pin((E, H, W))
+        pin = lambda shape, dt=torch.float32: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
         poses_h = torch.from_numpy(w.link_poses).pin_memory().numpy()
-        scene.render_host(poses_h, w.cams, rgb_h, depth_h)
+        if a.obs:
+            rgb_h, depth_h = pin((E, H, W, 3), torch.uint8), pin((E, H, W), torch.float16)
+            host_step = lambda: scene.render_obs_host(poses_h, w.cams, ap_h, rgb_h, depth_h)
+        else:
+            rgb_h, depth_h = pin((E, H, W, 3)), pin((E, H, W))
+            host_step = lambda: scene.render_host(poses_h, w.cams, rgb_h, depth_h)
+        host_step()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(a.e2e_steps):
-            scene.render_host(poses_h, w.cams, rgb_h, depth_h)
+            host_step()
         dt = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([dt], dtype=torch.float64, device=dev)
@@ -329,7 +347,8 @@ def run_ours(a, rank, world, local_rank):
         e2e = {"value": world * E * a.e2e_steps / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(poses_h.nbytes + w.cams.nbytes),
                "d2h_bytes_per_step": int(rgb_h.nbytes + depth_h.nbytes),
-               "ms_per_step": 1e3 * dt / a.e2e_steps, "api": "gs_render_batch_host"}
+               "ms_per_step": 1e3 * dt / a.e2e_steps,
+               "api": "gs_render_batch_obs_host" if a.obs else "gs_render_batch_host"}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -345,7 +364,9 @@ def run_ours(a, rank, world, local_rank):
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": a.dtype if a.dtype != "f32" else "f32", "data": "synthetic",
             "config": {"workload": f"c1: {E} envs x {W}x{H} RGB-D, 500k room-shell background + 20 links x 5k "
-                                   f"Gaussians, SH degree 3, tile {a.tile}",
+                                   f"Gaussians, SH degree 3, tile {a.tile}"
+                                   + (", observation form: u8 RGB after per-env exposure/contrast/brightness + f16 depth"
+                                      if a.obs else ""),
                        "envs_per_gpu": E, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": f"outputs of {out_bytes / 1e9:.1f} GB written per step (> 129 MB L2)"},
             "mpix_per_s": value * H * W / 1e6,

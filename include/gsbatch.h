@@ -127,6 +127,38 @@ gs_status gs_render_batch(gs_scene s, int n_envs, const float* link_poses, const
 gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
                                float* depth, float* alpha, void* cuda_stream);
 
+/* Observation form.  Policies consume 8-bit images; the paper's manipulation
+ * experiments randomise image-level appearance (brightness, contrast and
+ * exposure) during training (Sec. IV-E).  The library applies both in the
+ * compositor's store, per environment:
+ *   c  = clamp(colour, 0, 1) per channel (the float image's value)
+ *   v  = clamp((c * 2^exposure - 0.5) * contrast + 0.5 + brightness, 0, 1)
+ *   u8 = round-to-nearest-even(255 v)
+ * in FP32 with fused multiply-adds; depth (the float image's value) is
+ * rounded to IEEE half.  {exposure 0, contrast 1, brightness 0} leaves the
+ * colour unchanged.  12 bytes. */
+typedef struct {
+    float exposure;    /* stops: linear gain 2^exposure */
+    float contrast;    /* scale about 0.5 */
+    float brightness;  /* offset */
+} gs_appearance;
+
+/* As gs_render_batch, writing the observation form:
+ *   appearance  DEVICE gs_appearance [n_envs], or NULL for the identity
+ *   rgb8        DEVICE uint8 [n_envs][H][W][3]
+ *   depth16     DEVICE uint16 (half bits) [n_envs][H][W], or NULL (no depth)
+ * 4 (RGB) + 2 (depth) bytes per pixel instead of 16.  Errors as
+ * gs_render_batch. */
+gs_status gs_render_batch_obs(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
+                              const gs_appearance* appearance, uint8_t* rgb8, uint16_t* depth16, void* cuda_stream);
+
+/* As gs_render_batch_obs with HOST link_poses, appearance, rgb8 and depth16
+ * (copied in and out as in gs_render_batch_host); returns when the images are
+ * on the host. */
+gs_status gs_render_batch_obs_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
+                                   const gs_appearance* appearance, uint8_t* rgb8, uint16_t* depth16,
+                                   void* cuda_stream);
+
 /* One environment of an uneven batch (gs_render_batch_v, plans).  80 bytes. */
 typedef struct {
     gs_camera cam;        /* its own camera, width and height */

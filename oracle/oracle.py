@@ -213,3 +213,20 @@ def bin_records(u, v, hx, hy, zbits, gidx, width: int, height: int, tile_w: int,
     L.or_bin(len(u), _ptr(u), _ptr(v), _ptr(hx), _ptr(hy), _ptr(zb), _ptr(gi), width, height, tile_w, tile_h,
              _ptr(counts), _ptr(lists))
     return counts, lists[:total]
+
+
+def observation(rgb, depth, appearance=None):
+    """Observation form of a rendered image: the paper's manipulation
+    experiments randomise image-level brightness, contrast and exposure
+    (Sec. IV-E); policies take 8-bit colour.  Reading (the paper gives no
+    formula): per channel c = clamp(colour, 0, 1), v = clamp((c 2^exposure -
+    0.5) contrast + 0.5 + brightness, 0, 1), u8 = round half to even of 255 v;
+    depth as IEEE half.  ``appearance`` = (exposure, contrast, brightness) or
+    None for the identity.  Computed in FP64 (depth rounded from FP64)."""
+    c = np.clip(np.asarray(rgb, dtype=np.float64), 0.0, 1.0)
+    if appearance is not None:
+        e, k, b = (float(x) for x in appearance)
+        c = np.clip((c * 2.0 ** e - 0.5) * k + 0.5 + b, 0.0, 1.0)
+    u8 = np.rint(c * 255.0).astype(np.uint8)
+    d16 = np.asarray(depth, dtype=np.float64).astype(np.float16)
+    return u8, d16

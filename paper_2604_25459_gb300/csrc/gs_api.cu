@@ -141,6 +141,7 @@ struct gs_scene_s {
     int64_t prof_launches[GS_PHASES] = {0};
     int counters = 0;
     DevBuf neval;
+    DevBuf appear;  // appearance parameters copied from the host (observation form)
     // host staging of tables
     std::vector<EnvInfo> h_envs;
     std::vector<ProjBlock> h_blocks;
@@ -390,6 +391,23 @@ struct WaveIO {
     float* alpha;
     long long pix_rebase;
     uint32_t* status = nullptr;  // device status word of this wave (NULL: the scene's)
+    uint8_t* rgb8 = nullptr;     // observation form (replaces rgb / depth when set)
+    uint16_t* depth16 = nullptr;
+    const gs_appearance* appear = nullptr;  // device, indexed by the wave's env
+};
+
+// Where a render's images go: float RGB / depth / alpha, or the observation
+// form (8-bit RGB after the appearance transform, half depth).
+struct Outputs {
+    float* rgb = nullptr;
+    float* depth = nullptr;
+    float* alpha = nullptr;
+    uint8_t* rgb8 = nullptr;
+    uint16_t* depth16 = nullptr;
+    const gs_appearance* appear = nullptr;
+    bool obs() const { return rgb8 != nullptr; }
+    size_t rgb_px() const { return obs() ? 3 : 12; }                  // bytes per pixel
+    size_t depth_px() const { return obs() ? (depth16 ? 2 : 0) : 4; }
 };
 
 struct WaveTables {       // device copies of one wave's tables
@@ -614,6 +632,9 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.rgb = io.rgb;
         C.depth = io.depth;
         C.alpha = io.alpha;
+        C.rgb8 = io.rgb8;
+        C.depth16 = io.depth16;
+        C.appear = io.appear;
         C.status = status;
         CK(cudaMemsetAsync(sc.work.p, 0, 4, st), "memset work counter");
         int ctas = 0;
@@ -635,8 +656,11 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
 
 enum class Out { Device, Host };
 
-gs_status render_specs(gs_scene s, const std::vector<EnvSpec>& specs, const float* poses_dev, float* rgb,
-                       float* depth, float* alpha, cudaStream_t st, Out mode, int64_t pix_per_env_host) {
+gs_status render_specs(gs_scene s, const std::vector<EnvSpec>& specs, const float* poses_dev, const Outputs& o,
+                       cudaStream_t st, Out mode, int64_t pix_per_env_host) {
+    float* const rgb = o.rgb;
+    float* const depth = o.depth;
+    float* const alpha = o.alpha;
     const int tw = s->tile_w, th = s->tile_h;
     ST(check_specs(s, specs, tw, th));
     CK(cudaSetDevice(s->device), "set device");
@@ -645,7 +669,7 @@ gs_status render_specs(gs_scene s, const std::vector<EnvSpec>& specs, const floa
     s->stats.intersections = 0;
     const int E = (int)specs.size();
     size_t extra = 0;
-    if (mode == Out::Host) extra = (size_t)pix_per_env_host * 20 * 2;
+    if (mode == Out::Host) extra = (size_t)pix_per_env_host * (o.rgb_px() + o.depth_px() + (alpha ? 4 : 0)) * 2;
     std::vector<std::pair<int, int>> waves;
     ST(plan_waves(s, specs, tw, th, s->debug != 0, s->max_wave, extra, &waves));
     int64_t launches = 0;
@@ -655,8 +679,11 @@ gs_status render_specs(gs_scene s, const std::vector<EnvSpec>& specs, const floa
             ST(upload_tables(s, specs, w.first, w.second, tw, th, 0, s->sc.envs, s->sc.blocks, s->sc.cams, st, false,
                              &wt));
             s->last_envs.assign(wt.host_envs, wt.host_envs + wt.We + 1);
-            ST(run_wave(s, s->sc, wt, WaveIO{poses_dev, rgb, depth, alpha, 0}, tw, th, 1, 0, st, true, &launches,
-                        nullptr));
+            WaveIO io{poses_dev, rgb, depth, alpha, 0};
+            io.rgb8 = o.rgb8;
+            io.depth16 = o.depth16;
+            io.appear = o.appear ? o.appear + w.first : nullptr;
+            ST(run_wave(s, s->sc, wt, io, tw, th, 1, 0, st, true, &launches, nullptr));
             s->last_e0 = w.first;
             s->last_We = wt.We;
             s->stats.waves++;
@@ -671,8 +698,8 @@ gs_status render_specs(gs_scene s, const std::vector<EnvSpec>& specs, const floa
         for (int k = 0; k < 2; ++k) {
             if (!s->ev_done[k]) CK(cudaEventCreateWithFlags(&s->ev_done[k], cudaEventDisableTiming), "event");
             if (!s->ev_copied[k]) CK(cudaEventCreateWithFlags(&s->ev_copied[k], cudaEventDisableTiming), "event");
-            CK(s->stage_rgb[k].ensure((size_t)maxw * px * 12), "alloc staging");
-            CK(s->stage_depth[k].ensure((size_t)maxw * px * 4), "alloc staging");
+            CK(s->stage_rgb[k].ensure((size_t)maxw * px * o.rgb_px()), "alloc staging");
+            CK(s->stage_depth[k].ensure((size_t)maxw * px * std::max<size_t>(o.depth_px(), 1)), "alloc staging");
             if (alpha) CK(s->stage_alpha[k].ensure((size_t)maxw * px * 4), "alloc staging");
         }
         int wave = 0;
@@ -685,20 +712,36 @@ gs_status render_specs(gs_scene s, const std::vector<EnvSpec>& specs, const floa
             ST(upload_tables(s, specs, w.first, w.second, tw, th, rebase, s->sc.envs, s->sc.blocks, s->sc.cams, st,
                              false, &wt));
             s->last_envs.assign(wt.host_envs, wt.host_envs + wt.We + 1);
-            ST(run_wave(s, s->sc, wt,
-                        WaveIO{poses_dev, s->stage_rgb[k].as<float>(), s->stage_depth[k].as<float>(),
-                               alpha ? s->stage_alpha[k].as<float>() : nullptr, rebase},
-                        tw, th, 1, 0, st, true, &launches, nullptr));
+            WaveIO io{poses_dev, s->stage_rgb[k].as<float>(), s->stage_depth[k].as<float>(),
+                      alpha ? s->stage_alpha[k].as<float>() : nullptr, rebase};
+            if (o.obs()) {
+                io.rgb = nullptr;
+                io.depth = nullptr;
+                io.rgb8 = s->stage_rgb[k].as<uint8_t>();
+                io.depth16 = o.depth16 ? s->stage_depth[k].as<uint16_t>() : nullptr;
+                io.appear = o.appear ? o.appear + w.first : nullptr;
+            }
+            ST(run_wave(s, s->sc, wt, io, tw, th, 1, 0, st, true, &launches, nullptr));
             s->last_e0 = w.first;
             s->last_We = We;
             CK(cudaEventRecord(s->ev_done[k], st), "record");
             CK(cudaStreamWaitEvent(s->copy_stream, s->ev_done[k], 0), "wait render");
-            CK(cudaMemcpyAsync(rgb + (size_t)rebase * 3, s->stage_rgb[k].p, (size_t)We * px * 12,
-                               cudaMemcpyDeviceToHost, s->copy_stream),
-               "copy rgb out");
-            CK(cudaMemcpyAsync(depth + rebase, s->stage_depth[k].p, (size_t)We * px * 4, cudaMemcpyDeviceToHost,
-                               s->copy_stream),
-               "copy depth out");
+            if (o.obs()) {
+                CK(cudaMemcpyAsync(o.rgb8 + (size_t)rebase * 3, s->stage_rgb[k].p, (size_t)We * px * 3,
+                                   cudaMemcpyDeviceToHost, s->copy_stream),
+                   "copy rgb out");
+                if (o.depth16)
+                    CK(cudaMemcpyAsync(o.depth16 + rebase, s->stage_depth[k].p, (size_t)We * px * 2,
+                                       cudaMemcpyDeviceToHost, s->copy_stream),
+                       "copy depth out");
+            } else {
+                CK(cudaMemcpyAsync(rgb + (size_t)rebase * 3, s->stage_rgb[k].p, (size_t)We * px * 12,
+                                   cudaMemcpyDeviceToHost, s->copy_stream),
+                   "copy rgb out");
+                CK(cudaMemcpyAsync(depth + rebase, s->stage_depth[k].p, (size_t)We * px * 4, cudaMemcpyDeviceToHost,
+                                   s->copy_stream),
+                   "copy depth out");
+            }
             if (alpha)
                 CK(cudaMemcpyAsync(alpha + rebase, s->stage_alpha[k].p, (size_t)We * px * 4, cudaMemcpyDeviceToHost,
                                    s->copy_stream),
@@ -716,6 +759,7 @@ gs_status render_specs(gs_scene s, const std::vector<EnvSpec>& specs, const floa
 }
 
 gs_status clear_outputs(float* rgb, float* depth, float* alpha, size_t px, cudaStream_t st, bool host) {
+    if (!rgb) return GS_OK;  // observation form: cleared by clear_obs
     if (host) {
         memset(rgb, 0, px * 12);
         memset(depth, 0, px * 4);
@@ -728,13 +772,33 @@ gs_status clear_outputs(float* rgb, float* depth, float* alpha, size_t px, cudaS
     return GS_OK;
 }
 
+// An empty scene in the observation form: every pixel of env e is the
+// appearance transform of black (the same value in all three channels), depth 0.
+gs_status clear_obs(const Outputs& o, int E, size_t px, const gs_appearance* appear_host, cudaStream_t st, bool host) {
+    for (int e = 0; e < E; ++e) {
+        float v = 0.0f;  // black through the transform: clamp(0.5 + brightness - 0.5 contrast)
+        if (appear_host) v = std::fma(std::fma(0.0f, 1.0f, -0.5f), appear_host[e].contrast, 0.5f + appear_host[e].brightness);
+        v = std::fmin(std::fmax(v, 0.0f), 1.0f);
+        const int q = (int)std::nearbyint(v * 255.0f);
+        uint8_t* dst = o.rgb8 + (size_t)e * px * 3;
+        if (host) memset(dst, q, px * 3);
+        else CK(cudaMemsetAsync(dst, q, px * 3, st), "clear rgb");
+    }
+    if (o.depth16) {
+        if (host) memset(o.depth16, 0, (size_t)E * px * 2);
+        else CK(cudaMemsetAsync(o.depth16, 0, (size_t)E * px * 2, st), "clear depth");
+    }
+    return GS_OK;
+}
+
 gs_status render_uniform(gs_scene s, int E, const float* link_poses, const gs_camera* cams, float* rgb, float* depth,
-                         float* alpha, void* stream, bool host_mode) {
+                         float* alpha, void* stream, bool host_mode, const Outputs* obs = nullptr) {
     if (!s) return fail(GS_ERR_INVALID, "null scene");
     if (E < 0) return fail(GS_ERR_INVALID, "negative n_envs");
     if (E == 0) return GS_OK;
     if (!cams) return fail(GS_ERR_INVALID, "null cams");
-    if (!rgb || !depth) return fail(GS_ERR_INVALID, "null rgb or depth output");
+    if (!obs && (!rgb || !depth)) return fail(GS_ERR_INVALID, "null rgb or depth output");
+    if (obs && !obs->rgb8) return fail(GS_ERR_INVALID, "null rgb8 output");
     const int L = s->D.n_links;
     if (L > 0 && !link_poses) return fail(GS_ERR_INVALID, "null link_poses with %d links", L);
     const int W = cams[0].width, H = cams[0].height;
@@ -747,7 +811,32 @@ gs_status render_uniform(gs_scene s, int E, const float* link_poses, const gs_ca
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(s->device), "set device");
     const long long px = (long long)W * H;
-    if (s->D.n == 0) return clear_outputs(rgb, depth, alpha, (size_t)E * px, st, host_mode);
+    Outputs o;
+    if (obs) {
+        o = *obs;
+    } else {
+        o.rgb = rgb;
+        o.depth = depth;
+        o.alpha = alpha;
+    }
+    std::vector<gs_appearance> ap_host;
+    if (o.obs() && o.appear) {  // the appearance parameters on both sides of the bus
+        ap_host.resize((size_t)E);
+        if (host_mode) {
+            memcpy(ap_host.data(), o.appear, sizeof(gs_appearance) * (size_t)E);
+            CK(s->appear.ensure(sizeof(gs_appearance) * (size_t)E), "alloc appearance");
+            CK(cudaMemcpyAsync(s->appear.p, o.appear, sizeof(gs_appearance) * (size_t)E, cudaMemcpyHostToDevice, st),
+               "copy appearance");
+            o.appear = s->appear.as<gs_appearance>();
+        } else if (s->D.n == 0) {
+            CK(cudaMemcpy(ap_host.data(), o.appear, sizeof(gs_appearance) * (size_t)E, cudaMemcpyDeviceToHost),
+               "read appearance");
+        }
+    }
+    if (s->D.n == 0) {
+        if (o.obs()) return clear_obs(o, E, (size_t)px, ap_host.empty() ? nullptr : ap_host.data(), st, host_mode);
+        return clear_outputs(rgb, depth, alpha, (size_t)E * px, st, host_mode);
+    }
     std::vector<EnvSpec> specs((size_t)E);
     for (int e = 0; e < E; ++e) specs[e] = EnvSpec{cams + e, 0, L, (long long)e * L, (long long)e * px};
     const float* poses_dev = link_poses;
@@ -756,7 +845,7 @@ gs_status render_uniform(gs_scene s, int E, const float* link_poses, const gs_ca
         CK(cudaMemcpyAsync(s->poses.p, link_poses, (size_t)E * L * 28, cudaMemcpyHostToDevice, st), "copy poses");
         poses_dev = s->poses.as<float>();
     }
-    return render_specs(s, specs, poses_dev, rgb, depth, alpha, st, host_mode ? Out::Host : Out::Device, px);
+    return render_specs(s, specs, poses_dev, o, st, host_mode ? Out::Host : Out::Device, px);
 }
 
 gs_status specs_from_envs(gs_scene s, int n, const gs_env* envs, std::vector<EnvSpec>* specs) {
@@ -1003,6 +1092,25 @@ gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, 
     return render_uniform(s, n_envs, link_poses, cams, rgb, depth, alpha, cuda_stream, true);
 }
 
+gs_status gs_render_batch_obs(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
+                              const gs_appearance* appearance, uint8_t* rgb8, uint16_t* depth16, void* cuda_stream) {
+    Outputs o;
+    o.rgb8 = rgb8;
+    o.depth16 = depth16;
+    o.appear = appearance;
+    return render_uniform(s, n_envs, link_poses, cams, nullptr, nullptr, nullptr, cuda_stream, false, &o);
+}
+
+gs_status gs_render_batch_obs_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
+                                   const gs_appearance* appearance, uint8_t* rgb8, uint16_t* depth16,
+                                   void* cuda_stream) {
+    Outputs o;
+    o.rgb8 = rgb8;
+    o.depth16 = depth16;
+    o.appear = appearance;
+    return render_uniform(s, n_envs, link_poses, cams, nullptr, nullptr, nullptr, cuda_stream, true, &o);
+}
+
 gs_status gs_render_batch_v(gs_scene s, int n_envs, const gs_env* envs, const float* link_poses, float* rgb,
                             float* depth, float* alpha, void* cuda_stream) {
     if (!s) return fail(GS_ERR_INVALID, "null scene");
@@ -1025,7 +1133,11 @@ gs_status gs_render_batch_v(gs_scene s, int n_envs, const gs_env* envs, const fl
         }
         return GS_OK;
     }
-    return render_specs(s, specs, link_poses, rgb, depth, alpha, st, Out::Device, 0);
+    Outputs o;
+    o.rgb = rgb;
+    o.depth = depth;
+    o.alpha = alpha;
+    return render_specs(s, specs, link_poses, o, st, Out::Device, 0);
 }
 
 gs_status gs_plan_create(gs_scene s, int n_envs, const gs_env* envs, int flags, gs_plan* out) {
@@ -1428,7 +1540,7 @@ void gs_scene_destroy(gs_scene s) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&s->g0, &s->g1, &s->g2, &s->g3, &s->gsh, &s->stage_rgb[0], &s->stage_rgb[1],
                       &s->stage_depth[0], &s->stage_depth[1], &s->stage_alpha[0], &s->stage_alpha[1], &s->poses,
-                      &s->neval};
+                      &s->neval, &s->appear};
     for (DevBuf* b : bufs) b->release();
     s->sc.release();
     for (auto& m : s->marks) {

@@ -768,24 +768,42 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
         if (lane == 0 && c) atomicAdd(P.neval, (unsigned long long)c);
     }
-    if (in0) {
-        const size_t pix = pix_base + (size_t)py0 * W + px;
-        P.rgb[3 * pix] = fminf(fmaxf(r0, 0.0f), 1.0f);
-        P.rgb[3 * pix + 1] = fminf(fmaxf(g0, 0.0f), 1.0f);
-        P.rgb[3 * pix + 2] = fminf(fmaxf(b0, 0.0f), 1.0f);
-        const float a = 1.0f - T0;
-        P.depth[pix] = a > 0.0f ? d0 / a : 0.0f;
-        if (P.alpha) P.alpha[pix] = a;
+    // Outputs.  Observation form (rgb8 / depth16): the clamped colour goes
+    // through the env's appearance transform (exposure gain 2^e, contrast c
+    // about 0.5, brightness offset b), is clamped again and rounded to 8 bits;
+    // depth is rounded to half precision.
+    float gain = 1.0f, con = 1.0f, bri = 0.0f;
+    if (P.rgb8 && P.appear) {
+        const gs_appearance ap = P.appear[el];
+        gain = exp2f(ap.exposure);
+        con = ap.contrast;
+        bri = ap.brightness;
     }
-    if (in1) {
-        const size_t pix = pix_base + (size_t)py1 * W + px;
-        P.rgb[3 * pix] = fminf(fmaxf(r1, 0.0f), 1.0f);
-        P.rgb[3 * pix + 1] = fminf(fmaxf(g1, 0.0f), 1.0f);
-        P.rgb[3 * pix + 2] = fminf(fmaxf(b1, 0.0f), 1.0f);
-        const float a = 1.0f - T1;
-        P.depth[pix] = a > 0.0f ? d1 / a : 0.0f;
+    auto store = [&](int py, float T, float r, float g, float b, float d) {
+        const size_t pix = pix_base + (size_t)py * W + px;
+        const float cr = fminf(fmaxf(r, 0.0f), 1.0f), cg = fminf(fmaxf(g, 0.0f), 1.0f),
+                    cb = fminf(fmaxf(b, 0.0f), 1.0f);
+        const float a = 1.0f - T;
+        const float dep = a > 0.0f ? d / a : 0.0f;
+        if (P.rgb8) {
+            auto q = [&](float v) {
+                v = fmaf(fmaf(v, gain, -0.5f), con, 0.5f + bri);
+                return (uint8_t)__float2int_rn(fminf(fmaxf(v, 0.0f), 1.0f) * 255.0f);
+            };
+            P.rgb8[3 * pix] = q(cr);
+            P.rgb8[3 * pix + 1] = q(cg);
+            P.rgb8[3 * pix + 2] = q(cb);
+        } else {
+            P.rgb[3 * pix] = cr;
+            P.rgb[3 * pix + 1] = cg;
+            P.rgb[3 * pix + 2] = cb;
+        }
+        if (P.depth16) P.depth16[pix] = __half_as_ushort(__float2half_rn(dep));
+        else if (P.depth) P.depth[pix] = dep;
         if (P.alpha) P.alpha[pix] = a;
-    }
+    };
+    if (in0) store(py0, T0, r0, g0, b0, d0);
+    if (in1) store(py1, T1, r1, g1, b1, d1);
     __syncthreads();  // shared staging is reused by the next item
     }  // items of the claim
     if (tid == 0) s_item = atomicAdd(P.work, (unsigned)P.chunk);  // every thread has read the last claim

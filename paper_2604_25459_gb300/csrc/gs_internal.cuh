@@ -150,9 +150,12 @@ struct CompParams {
     unsigned long long* dbg_sorted;  // nullable: receives the full depth-ordered lists
     unsigned long long* neval;       // nullable: composited (pixel, Gaussian) pair counter
     int tile_w, tile_h;
-    float* rgb;     // images at envs[e].pix_base (x3 for rgb)
-    float* depth;
+    float* rgb;     // images at envs[e].pix_base (x3 for rgb); unused when rgb8 is set
+    float* depth;   // unused when depth16 is set
     float* alpha;   // nullable
+    uint8_t* rgb8;        // nullable: observation RGB, 8 bits per channel, at pix_base (x3)
+    uint16_t* depth16;    // nullable: observation depth, IEEE half bits, at pix_base
+    const gs_appearance* appear;  // nullable: per env (wave-local index) for rgb8
     uint32_t* status;
 };
 

@@ -88,6 +88,8 @@ _SIGS = {
     "gs_render_batch_host": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_render_batch_noalloc": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_render_batch_v": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
+    "gs_render_batch_obs": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
+    "gs_render_batch_obs_host": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_plan_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "gs_plan_launch": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
     "gs_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(GsPlanInfo)]),
@@ -297,6 +299,40 @@ class Scene:
         _check(lib().gs_render_batch_host(self._h, E, _ptr(link_poses), _ptr(cams), _ptr(rgb), _ptr(depth),
                                           _ptr(alpha), _stream_handle(stream)))
         return rgb, depth, alpha
+
+    def render_obs(self, link_poses, cams: np.ndarray, appearance=None, rgb8=None, depth16=None,
+                   want_depth: bool = True, stream=None):
+        """Observation form on the device (gs_render_batch_obs): appearance is a
+        CUDA float32 [E][3] (exposure, contrast, brightness) or None; returns
+        (rgb8 uint8 [E,H,W,3], depth16 float16 [E,H,W] or None)."""
+        import torch
+
+        cams = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+        E = int(cams.shape[0])
+        H, W = (int(cams["height"][0]), int(cams["width"][0])) if E else (0, 0)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if rgb8 is None:
+            rgb8 = torch.empty((E, H, W, 3), dtype=torch.uint8, device=dev)
+        if depth16 is None and want_depth:
+            depth16 = torch.empty((E, H, W), dtype=torch.float16, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        _check(lib().gs_render_batch_obs(self._h, E, _ptr(link_poses), _ptr(cams), _ptr(appearance), _ptr(rgb8),
+                                         _ptr(depth16), _stream_handle(stream)))
+        return rgb8, depth16
+
+    def render_obs_host(self, link_poses: np.ndarray, cams: np.ndarray, appearance, rgb8: np.ndarray, depth16=None,
+                        stream=None):
+        """Observation form with host buffers (gs_render_batch_obs_host):
+        appearance numpy float32 [E][3] or None, rgb8 uint8 [E,H,W,3], depth16
+        float16 [E,H,W] or None.  Returns when the images are on the host."""
+        cams = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+        E = int(cams.shape[0])
+        if appearance is not None:
+            appearance = np.ascontiguousarray(appearance, dtype=np.float32)
+        _check(lib().gs_render_batch_obs_host(self._h, E, _ptr(link_poses), _ptr(cams), _ptr(appearance), _ptr(rgb8),
+                                              _ptr(depth16), _stream_handle(stream)))
+        return rgb8, depth16
 
     def render_v(self, envs: np.ndarray, link_poses, rgb, depth, alpha=None, stream=None):
         """Uneven batch (gs_render_batch_v): envs is a numpy ENV_DTYPE array (host);

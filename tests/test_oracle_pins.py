@@ -403,3 +403,23 @@ def test_bin_oracle_against_brute_enumeration():
             assert counts[t] == len(members)
             assert list(lists[off:off + counts[t]]) == [g for _, g in members]
             off += counts[t]
+
+
+def test_observation_transform_hand_values():
+    """Observation form (appearance randomisation of Sec. IV-E, 8-bit colour,
+    half depth), against values worked out by hand."""
+    rgb = np.array([[[0.0, 0.25, 1.0], [0.5, -0.3, 1.7]]])
+    depth = np.array([[1.0, 3.14159]])
+    u8, d16 = oracle.observation(rgb, depth)
+    # identity: clamp then 255 c rounded half to even (63.75 -> 64)
+    assert u8.tolist() == [[[0, 64, 255], [128, 0, 255]]]  # 127.5 -> 128 (even)
+    assert d16.dtype == np.float16 and float(d16[0, 0]) == 1.0 and float(d16[0, 1]) == 3.140625
+    # exposure +1 doubles the linear colour before the clamp: 0.25 -> 0.5 -> 127.5 -> 128
+    u8, _ = oracle.observation(rgb, depth, (1.0, 1.0, 0.0))
+    assert u8.tolist() == [[[0, 128, 255], [255, 0, 255]]]
+    # contrast 0: every channel 0.5 + brightness = 0.6 -> 153
+    u8, _ = oracle.observation(rgb, depth, (0.0, 0.0, 0.1))
+    assert (u8 == 153).all()
+    # contrast 2 about 0.5: 0.25 -> 0, 0.5 -> 0.5 (127.5 -> 128), 1 -> 1
+    u8, _ = oracle.observation(rgb, depth, (0.0, 2.0, 0.0))
+    assert u8.tolist() == [[[0, 0, 255], [128, 0, 255]]]
