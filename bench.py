@@ -70,12 +70,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0,
                     help="CPU-baseline sample: oracle envs rendered one by one until this much time has passed")
-    ap.add_argument("--workload", choices=["c1", "c3", "c4"], default="c1",
+    ap.add_argument("--workload", choices=["c1", "c3", "c4", "prune"], default="c1",
                     help="c1: uniform 640x480 batch (headline); c3: batched uneven form through a plan")
     ap.add_argument("--no-graph", action="store_true", help="c3: eager plan launches instead of a CUDA graph")
     ap.add_argument("--obs", action="store_true",
                     help="c1 in the observation form: 8-bit RGB after per-env appearance randomisation + half depth")
     ap.add_argument("--rates", default="1000,3000,10000,30000", help="c4: offered request rates (req/s)")
+    ap.add_argument("--prune-envs", type=int, default=64, help="prune: envs whose cameras rank the Gaussians")
     ap.add_argument("--duration", type=float, default=2.0, help="c4: seconds of arrivals per rate")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="c4: HBM budget of the request loop")
     ap.add_argument("--slots", type=int, default=4, help="c4: stream slots (batches in flight)")
@@ -600,6 +601,83 @@ def run_c4(a, rank, world, local_rank):
         sc.close()
 
 
+
+def run_prune(a, rank, world, local_rank):
+    """Pruning as a scene transform on c1: rank every Gaussian by its summed
+    blending weight over the cameras of the first --prune-envs envs of the
+    batch (the contribution pass), keep the top 30 % of the background and 10 %
+    of each link's cluster, then time the full 2048-env batch on the pruned
+    scene; error: PSNR of the pruned render against the FP64 oracle of the
+    unpruned scene on sampled envs."""
+    import torch
+
+    import __graft_entry__
+    from oracle import oracle
+    from paper_2604_25459_gb300 import gsbatch, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    E, H, W = a.envs, a.height, a.width
+    w = synth.make_c1(n_envs=E, width=W, height=H, f=500.0 * W / 640)
+    poses = torch.from_numpy(w.link_poses).to(dev)
+    stream = torch.cuda.current_stream()
+    scene = gsbatch.scene_from_workload(w)
+    ns = min(a.prune_envs, E)
+    t0 = time.perf_counter()
+    scores = scene.contribution(poses[:ns], w.cams[:ns], stream=stream)
+    torch.cuda.synchronize()
+    score_s = time.perf_counter() - t0
+    p = gsbatch.prune_workload(w, scores.cpu().numpy(), keep_bg=0.3, keep_links=0.1)
+    pscene = gsbatch.scene_from_workload(p)
+    rgb = torch.empty((E, H, W, 3), dtype=torch.float32, device=dev)
+    depth = torch.empty((E, H, W), dtype=torch.float32, device=dev)
+
+    def timed(sc):
+        for _ in range(a.warmup):
+            sc.render(poses, w.cams, rgb=rgb, depth=depth, want_alpha=False, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            sc.render(poses, w.cams, rgb=rgb, depth=depth, want_alpha=False, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sc.sync_status()
+        return e0.elapsed_time(e1) / a.steps
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    full_ms = timed(scene)
+    pruned_ms = timed(pscene)
+    ck = clocks.stop()
+    # error on sampled envs (the last rendered batch holds the pruned images)
+    S = oracle.scene_arrays(w)
+    errs = []
+    for e in (0, E // 2, E - 1):
+        ref = oracle.render_env(w, e, S=S)
+        diff = rgb[e].cpu().numpy().astype(np.float64) - ref["rgb"]
+        mse = float((diff ** 2).mean())
+        errs.append({"env": e, "psnr_db": 10 * math.log10(1.0 / max(mse, 1e-20)),
+                     "max_abs": float(np.abs(diff).max())})
+    if rank == 0:
+        line = {"metric": "env-frames/s at 2048x640x480 RGB-D, pruned scene (30 % background, 10 % per link)",
+                "value": E / (pruned_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": pruned_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"c1 pruned by contribution over the cameras of {ns} envs: "
+                                       f"{p.background.n} of {w.background.n} background and {p.links.n} of "
+                                       f"{w.links.n} link Gaussians kept"},
+                "unpruned": {"ms_per_step": full_ms, "env_frames_s": E / (full_ms / 1e3)},
+                "speedup": full_ms / pruned_ms, "error_vs_unpruned_fp64_oracle": errs,
+                "contribution_pass_s": score_s, "clocks": ck,
+                "gpu_launches": None, "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    pscene.close()
+    scene.close()
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -621,6 +699,8 @@ def main():
         run_c3(a, rank, world, local_rank)
     elif a.workload == "c4":
         run_c4(a, rank, world, local_rank)
+    elif a.workload == "prune":
+        run_prune(a, rank, world, local_rank)
     else:
         run_ours(a, rank, world, local_rank)
     if world > 1:

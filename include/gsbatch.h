@@ -159,6 +159,18 @@ gs_status gs_render_batch_obs_host(gs_scene s, int n_envs, const float* link_pos
                                    const gs_appearance* appearance, uint8_t* rgb8, uint16_t* depth16,
                                    void* cuda_stream);
 
+/* Contribution pass (support for pruning, a scene transform that follows the
+ * paper's Gaussian pruning for speed and memory, Sec. III-C): renders n_envs
+ * environments like gs_render_batch (one resolution, 16x16 tiles whatever
+ * the scene's tile setting) without writing images, and ADDS to scores[g],
+ * for every Gaussian g, the sum over pixels of its blending weight alpha T
+ * where it was composited.  scores: DEVICE float [background + link
+ * Gaussians], global order; the caller zeroes it.  Sum over g of the added
+ * weights = sum over pixels of alpha (the weights telescope).  Errors as
+ * gs_render_batch. */
+gs_status gs_scene_contribution(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
+                                float* scores, void* cuda_stream);
+
 /* One environment of an uneven batch (gs_render_batch_v, plans).  80 bytes. */
 typedef struct {
     gs_camera cam;        /* its own camera, width and height */

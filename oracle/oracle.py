@@ -65,7 +65,7 @@ class _Proj(C.Structure):
 
 
 class _Image(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("rgb", "depth", "alpha", "amb", "neval")]
+    _fields_ = [(k, C.c_void_p) for k in ("rgb", "depth", "alpha", "amb", "neval", "contrib")]
 
 
 def lib():
@@ -174,13 +174,19 @@ def project(S: SceneArrays, link_poses_env, cam, precision: str = "f64") -> dict
 
 
 def render_projected(proj: dict, width: int, height: int, mode: str = "plain", precision: str = "f64",
-                     zkey=None) -> dict:
+                     zkey=None, contrib: bool = False) -> dict:
+    """Composite projected Gaussians; with ``contrib`` also each Gaussian's
+    summed blending weight sum_p alpha T over the pixels where it was added
+    (the contribution that ranks Gaussians for pruning)."""
     img = dict(rgb=np.zeros((height, width, 3), np.float32), depth=np.zeros((height, width), np.float32),
                alpha=np.zeros((height, width), np.float32), amb=np.zeros((height, width), np.uint8),
                neval=np.zeros((height, width), np.int32))
-    I = _Image(*[_ptr(img[k]) for k in ("rgb", "depth", "alpha", "amb", "neval")])
-    zk = _f32(zkey) if zkey is not None else None
     n = len(proj["u"])
+    if contrib:
+        img["contrib"] = np.zeros(n, np.float64)
+    I = _Image(*[_ptr(img[k]) for k in ("rgb", "depth", "alpha", "amb", "neval")],
+               _ptr(img["contrib"]) if contrib else None)
+    zk = _f32(zkey) if zkey is not None else None
     rc = getattr(lib(), f"or_render_{precision}")(C.byref(proj["_P"]), n, _ptr(zk), width, height,
                                                    1 if mode == "brute" else 0, C.byref(I))
     assert rc == 0
@@ -188,12 +194,12 @@ def render_projected(proj: dict, width: int, height: int, mode: str = "plain", p
 
 
 def render_env(w, e: int = 0, mode: str = "plain", precision: str = "f64", sh_degree: int = 3, S=None,
-               zkey=None) -> dict:
+               zkey=None, contrib: bool = False) -> dict:
     """Render env ``e`` of workload ``w``: rgb [H,W,3], depth, alpha, amb (ambiguous-pixel mask), neval."""
     S = S or scene_arrays(w, sh_degree)
     cam = w.cams[e]
     proj = project(S, w.link_poses[e], cam, precision)
-    img = render_projected(proj, int(cam["width"]), int(cam["height"]), mode, precision, zkey)
+    img = render_projected(proj, int(cam["width"]), int(cam["height"]), mode, precision, zkey, contrib)
     img["proj"] = proj
     return img
 

@@ -394,6 +394,7 @@ struct WaveIO {
     uint8_t* rgb8 = nullptr;     // observation form (replaces rgb / depth when set)
     uint16_t* depth16 = nullptr;
     const gs_appearance* appear = nullptr;  // device, indexed by the wave's env
+    float* score = nullptr;      // contribution pass (no images)
 };
 
 // Where a render's images go: float RGB / depth / alpha, or the observation
@@ -635,6 +636,8 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.rgb8 = io.rgb8;
         C.depth16 = io.depth16;
         C.appear = io.appear;
+        C.score = io.score;
+        C.nbp = (unsigned)bg_slots(s->D.n_bg);
         C.status = status;
         CK(cudaMemsetAsync(sc.work.p, 0, 4, st), "memset work counter");
         int ctas = 0;
@@ -1090,6 +1093,35 @@ gs_status gs_render_batch(gs_scene s, int n_envs, const float* link_poses, const
 gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
                                float* depth, float* alpha, void* cuda_stream) {
     return render_uniform(s, n_envs, link_poses, cams, rgb, depth, alpha, cuda_stream, true);
+}
+
+gs_status gs_scene_contribution(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
+                                float* scores, void* cuda_stream) {
+    if (!s) return fail(GS_ERR_INVALID, "null scene");
+    if (n_envs < 0) return fail(GS_ERR_INVALID, "negative n_envs");
+    if (n_envs == 0 || s->D.n == 0) return GS_OK;
+    if (!cams || !scores) return fail(GS_ERR_INVALID, "null cams or scores");
+    const int L = s->D.n_links;
+    if (L > 0 && !link_poses) return fail(GS_ERR_INVALID, "null link_poses with %d links", L);
+    for (int e = 0; e < n_envs; ++e) ST(check_cam(cams[e], e));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    CK(cudaSetDevice(s->device), "set device");
+    const int tw = 16, th = 16;  // the contribution pass bins and composites on 16x16 tiles
+    std::vector<EnvSpec> specs((size_t)n_envs);
+    for (int e = 0; e < n_envs; ++e) specs[e] = EnvSpec{cams + e, 0, L, (long long)e * L, 0};
+    ST(check_specs(s, specs, tw, th));
+    std::vector<std::pair<int, int>> waves;
+    ST(plan_waves(s, specs, tw, th, false, s->max_wave, 0, &waves));
+    int64_t launches = 0;
+    for (auto& w : waves) {
+        WaveTables wt{};
+        ST(upload_tables(s, specs, w.first, w.second, tw, th, 0, s->sc.envs, s->sc.blocks, s->sc.cams, st, false,
+                         &wt));
+        WaveIO io{link_poses, nullptr, nullptr, nullptr, 0};
+        io.score = scores;
+        ST(run_wave(s, s->sc, wt, io, tw, th, 1, 0, st, false, &launches, nullptr));
+    }
+    return GS_OK;
 }
 
 gs_status gs_render_batch_obs(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,

@@ -261,23 +261,31 @@ __device__ unsigned long long* window_sort(unsigned long long* keys, unsigned lo
     return src;
 }
 
-// One pixel's blend step for a splat whose alpha is `al` (already >= 1/255):
+// One pixel's blend step for a splat whose alpha is `al` (already >= 1/255);
+// returns the weight alpha T added (0 when the step stops instead):
 // T' = T (1 - alpha); stop (splat not added) when T' < 1e-4.  The products are
 // pinned to explicit round-to-nearest operations so every tile shape and
 // every pixel slot evaluates exactly the same arithmetic.
-__device__ __forceinline__ void blend(float al, const float4& C, float z, float& T, float& r, float& g, float& b,
-                                      float& d, bool& done) {
+__device__ __forceinline__ float blend(float al, const float4& C, float z, float& T, float& r, float& g, float& b,
+                                       float& d, bool& done) {
     const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
     if (Tn < 1e-4f) {
         done = true;
-    } else {
-        const float w = __fmul_rn(al, T);
-        r = __fmaf_rn(w, C.x, r);
-        g = __fmaf_rn(w, C.y, g);
-        b = __fmaf_rn(w, C.z, b);
-        d = __fmaf_rn(w, z, d);
-        T = Tn;
+        return 0.0f;
     }
+    const float w = __fmul_rn(al, T);
+    r = __fmaf_rn(w, C.x, r);
+    g = __fmaf_rn(w, C.y, g);
+    b = __fmaf_rn(w, C.z, b);
+    d = __fmaf_rn(w, z, d);
+    T = Tn;
+    return w;
+}
+
+// Warp sum of one float per lane.
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
 }
 
 // alpha = min(0.99, o exp(-q/2)) = min(0.99, o 2^-((l00 dx + l01 dy)^2 + (l11 dy)^2))
@@ -334,7 +342,10 @@ __device__ __forceinline__ bool reaches_rect(const float4& A, const float4& B, f
 // larger than H; such a window (and a bucket longer than spill_cap, or any
 // long bucket when there is no spill region) is cut into windows by radix
 // selection over its keys instead.
-template <int TW, int TH>
+// SC: contribution pass (pruning support): instead of writing images, add
+// each blended (pixel, splat) weight alpha T to score[global index], summed
+// per warp and splat before one atomic add.
+template <int TW, int TH, bool SC = false>
 __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 256 ? 8 : 12))) k_composite(CompParams P) {
     constexpr int NT = TW * TH / 2;
     constexpr int NB = NT;  // splats staged per batch (one per thread)
@@ -362,6 +373,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     int4* sR = reinterpret_cast<int4*>(sC + NB);   // x0, x1 - x0, y0, y1 - y0
     uint16_t* cnt = reinterpret_cast<uint16_t*>(cbuf);
     uint32_t* hist = reinterpret_cast<uint32_t*>(cbuf);
+    __shared__ uint32_t sG[SC ? NB : 1];  // contribution pass: slot of each staged splat
     uint32_t* bins = reinterpret_cast<uint32_t*>(kbuf);  // partition counters (between windows only)
 
     __shared__ unsigned int s_item;
@@ -414,6 +426,11 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     }
     const unsigned long long* Lk = P.pairs + start;
     const size_t recbase = (size_t)__ldg(&Ep->rec_base);
+    // contribution pass: record slot -> global Gaussian index
+    const long long g_link0 = SC ? __ldg(&Ep->g_link0) : 0ll;
+    auto score_index = [&](uint32_t j) -> long long {
+        return j < P.nbp ? (long long)j : g_link0 + (long long)(j - P.nbp);
+    };
     bool finished = false;
 
     // Sort keys[0, wn) (the next wn keys in depth order) and composite them;
@@ -443,6 +460,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                     sC[s] = q2;
                     sR[s] = make_int4((int)(rx & 0xffffu), (int)((rx >> 16) - (rx & 0xffffu)), (int)(ry & 0xffffu),
                                       (int)((ry >> 16) - (ry & 0xffffu)));
+                    if constexpr (SC) sG[s] = g;
                 } else {  // never happens for a well-formed bucket; stage an empty range
                     sA[s] = make_float4(0.f, 0.f, 0.f, 0.f);
                     sB[s] = sA[s];
@@ -464,6 +482,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         if (ov && R.y + R.w >= 24) ov = reaches_rect(sA[j], sB[j], (float)wx0 + 0.5f, (float)wy0 + 0.5f);
                     }
                     uint32_t m = __ballot_sync(0xffffffffu, ov);
+                    float2 score_pair = make_float2(0.0f, 0.0f);  // contribution pass only
                     // two splats per iteration: their four alpha evaluations are
                     // independent; the blends then run in depth order
                     while (m) {
@@ -491,15 +510,16 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             const float a21 = splat_alpha(A2, B2, dx2, fpy1 - A2.y);
                             const bool u10 = h10 && a10 >= (1.0f / 255.0f);
                             const bool u11 = h11 && a11 >= (1.0f / 255.0f);
+                            float w1 = 0.0f, w2 = 0.0f;
                             if (u10 || u11) {
                                 const float4 C1 = sC[j1];
                                 if (u10) {
                                     ++ncomp;
-                                    blend(a10, C1, A1.w, T0, r0, g0, b0, d0, done0);
+                                    w1 += blend(a10, C1, A1.w, T0, r0, g0, b0, d0, done0);
                                 }
                                 if (u11) {
                                     ++ncomp;
-                                    blend(a11, C1, A1.w, T1, r1, g1, b1, d1, done1);
+                                    w1 += blend(a11, C1, A1.w, T1, r1, g1, b1, d1, done1);
                                 }
                             }
                             const bool u20 = h20 && !done0 && a20 >= (1.0f / 255.0f);
@@ -508,12 +528,21 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                                 const float4 C2 = sC[j2];
                                 if (u20) {
                                     ++ncomp;
-                                    blend(a20, C2, A2.w, T0, r0, g0, b0, d0, done0);
+                                    w2 += blend(a20, C2, A2.w, T0, r0, g0, b0, d0, done0);
                                 }
                                 if (u21) {
                                     ++ncomp;
-                                    blend(a21, C2, A2.w, T1, r1, g1, b1, d1, done1);
+                                    w2 += blend(a21, C2, A2.w, T1, r1, g1, b1, d1, done1);
                                 }
+                            }
+                            if constexpr (SC) score_pair = make_float2(w1, w2);
+                        }
+                        if constexpr (SC) {  // warp-uniform: every lane reaches this point
+                            const float s1 = warp_sum(score_pair.x), s2 = warp_sum(score_pair.y);
+                            score_pair = make_float2(0.0f, 0.0f);
+                            if (lane == 0) {
+                                if (s1 > 0.0f) atomicAdd(P.score + score_index(sG[j1]), s1);
+                                if (two && s2 > 0.0f) atomicAdd(P.score + score_index(sG[j2]), s2);
                             }
                         }
                     }
@@ -802,8 +831,10 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         else if (P.depth) P.depth[pix] = dep;
         if (P.alpha) P.alpha[pix] = a;
     };
-    if (in0) store(py0, T0, r0, g0, b0, d0);
-    if (in1) store(py1, T1, r1, g1, b1, d1);
+    if (!SC) {
+        if (in0) store(py0, T0, r0, g0, b0, d0);
+        if (in1) store(py1, T1, r1, g1, b1, d1);
+    }
     __syncthreads();  // shared staging is reused by the next item
     }  // items of the claim
     if (tid == 0) s_item = atomicAdd(P.work, (unsigned)P.chunk);  // every thread has read the last claim
@@ -811,7 +842,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     }  // claims
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool SC = false>
 static cudaError_t resident_ctas(int* out) {
     constexpr int NT = TW * TH / 2;
     static int per_sm[64] = {0};  // resident CTAs per SM, per device
@@ -822,7 +853,7 @@ static cudaError_t resident_ctas(int* out) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (per_sm[dev] == 0) {
         int ps = 0, n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_composite<TW, TH>, NT, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_composite<TW, TH, SC>, NT, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -833,11 +864,11 @@ static cudaError_t resident_ctas(int* out) {
     return cudaSuccess;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool SC = false>
 static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas) {
     constexpr int NT = TW * TH / 2;
     int full = 0;
-    cudaError_t e = resident_ctas<TW, TH>(&full);
+    cudaError_t e = resident_ctas<TW, TH, SC>(&full);
     if (e != cudaSuccess) return e;
     const unsigned items = P.item_end - P.item_begin;
     unsigned grid = (unsigned)full;
@@ -846,7 +877,7 @@ static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas)
     if (P.spill && grid > P.spill_ctas) grid = P.spill_ctas;
     if (grid == 0) grid = 1;
     *ctas = (int)grid;
-    k_composite<TW, TH><<<grid, NT, 0, st>>>(P);
+    k_composite<TW, TH, SC><<<grid, NT, 0, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -855,6 +886,10 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
     if (P.item_end <= P.item_begin) return cudaSuccess;
     if (P.spill && (P.spill_cap < (unsigned)kCompCap || P.spill_cap > (unsigned)kSpillMax || P.spill_ctas == 0))
         return cudaErrorInvalidValue;
+    if (P.score) {  // the contribution pass runs on 16x16 tiles only
+        if (P.tile_w != 16 || P.tile_h != 16) return cudaErrorInvalidValue;
+        return launch_tiles<16, 16, true>(P, st, ctas);
+    }
     if (P.tile_w == 16 && P.tile_h == 16) return launch_tiles<16, 16>(P, st, ctas);
     if (P.tile_w == 32 && P.tile_h == 16) return launch_tiles<32, 16>(P, st, ctas);
     if (P.tile_w == 8 && P.tile_h == 8) return launch_tiles<8, 8>(P, st, ctas);

@@ -78,6 +78,7 @@ struct EnvInfo {
     int link_begin, n_links;       // links of the scene rendered in this env
     int W, H, ntx, T;              // image and tile grid
     int pad;
+    long long g_link0;             // global index of the env's first link Gaussian (slot bg_slots)
 };
 
 // A projection block: up to 256 consecutive Gaussians (thread t takes global
@@ -156,6 +157,8 @@ struct CompParams {
     uint8_t* rgb8;        // nullable: observation RGB, 8 bits per channel, at pix_base (x3)
     uint16_t* depth16;    // nullable: observation depth, IEEE half bits, at pix_base
     const gs_appearance* appear;  // nullable: per env (wave-local index) for rgb8
+    float* score;         // nullable: contribution pass (no images): score[g] += sum of alpha T
+    unsigned int nbp;     // background slots (slot j < nbp is background Gaussian j)
     uint32_t* status;
 };
 

@@ -93,6 +93,7 @@ void build_wave_tables(const DevGaussians& D, const int64_t* link_offsets, const
         ei.ntx = ntx;
         ei.T = ntx * nty;
         ei.pad = 0;
+        ei.g_link0 = D.n_bg + (link_offsets ? link_offsets[sp.link_begin] : 0);
         rec += ei.n_local;
         mask += (ei.n_local + 31) / 32;
         tiles += (unsigned)ei.T;

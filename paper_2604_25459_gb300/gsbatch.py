@@ -89,6 +89,7 @@ _SIGS = {
     "gs_render_batch_noalloc": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_render_batch_v": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_render_batch_obs": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
+    "gs_scene_contribution": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 4),
     "gs_render_batch_obs_host": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_plan_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "gs_plan_launch": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
@@ -334,6 +335,21 @@ class Scene:
                                               _ptr(depth16), _stream_handle(stream)))
         return rgb8, depth16
 
+    def contribution(self, link_poses, cams: np.ndarray, scores=None, stream=None):
+        """Add each Gaussian's summed blending weight over the envs' pixels to
+        scores (CUDA float32 [n_gaussians], zeros if None); returns scores."""
+        import torch
+
+        cams = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+        if scores is None:
+            st = self.stats()
+            scores = torch.zeros(st["n_gaussians"], dtype=torch.float32, device="cuda")
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        _check(lib().gs_scene_contribution(self._h, int(cams.shape[0]), _ptr(link_poses), _ptr(cams), _ptr(scores),
+                                           _stream_handle(stream)))
+        return scores
+
     def render_v(self, envs: np.ndarray, link_poses, rgb, depth, alpha=None, stream=None):
         """Uneven batch (gs_render_batch_v): envs is a numpy ENV_DTYPE array (host);
         outputs are flat CUDA tensors addressed by each env's pixel_offset."""
@@ -525,6 +541,39 @@ def measure_alu_peak(stream=None) -> dict:
     f, e = C.c_double(), C.c_double()
     _check(lib().gs_measure_alu_peak(C.byref(f), C.byref(e), _stream_handle(stream)))
     return {"fma_lane_ops_per_s": f.value, "ex2_lane_ops_per_s": e.value}
+
+
+def prune_workload(w, scores, keep_bg: float = 0.3, keep_links: float = 0.1):
+    """Scene transform: keep the highest-ranked Gaussians by contribution
+    score (``scores``: numpy [n_background + n_link_gaussians], global order),
+    the top ``keep_bg`` fraction of the background and the top ``keep_links``
+    fraction of every link's cluster; kept Gaussians stay in their original
+    order.  Returns a synth.Workload with the same poses and cameras."""
+    from . import synth
+    scores = np.asarray(scores, dtype=np.float64)
+    nb = w.background.n
+
+    def top(s, frac):
+        k = int(np.ceil(frac * len(s)))
+        if k >= len(s):
+            return np.arange(len(s))
+        return np.sort(np.argpartition(-s, k - 1)[:k]) if k > 0 else np.zeros(0, np.int64)
+
+    bg_idx = top(scores[:nb], keep_bg)
+    offs = np.asarray(w.link_offsets, dtype=np.int64)
+    parts, new_offs = [], [0]
+    for l in range(len(offs) - 1):
+        a, b = int(offs[l]), int(offs[l + 1])
+        idx = a + top(scores[nb + a:nb + b], keep_links)
+        parts.append(idx)
+        new_offs.append(new_offs[-1] + len(idx))
+    link_idx = np.concatenate(parts) if parts else np.zeros(0, np.int64)
+
+    def take(g, idx):
+        return synth.Gaussians(g.mean[idx], g.quat[idx], g.log_scale[idx], g.opacity[idx], g.sh[idx])
+
+    return synth.Workload(w.name + "_pruned", take(w.background, bg_idx), np.asarray(new_offs, np.int64),
+                          take(w.links, link_idx), w.link_poses, w.cams)
 
 
 def make_envs(cams: np.ndarray, link_ranges=None, pose_offsets=None) -> np.ndarray:

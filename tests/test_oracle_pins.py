@@ -423,3 +423,21 @@ def test_observation_transform_hand_values():
     # contrast 2 about 0.5: 0.25 -> 0, 0.5 -> 0.5 (127.5 -> 128), 1 -> 1
     u8, _ = oracle.observation(rgb, depth, (0.0, 2.0, 0.0))
     assert u8.tolist() == [[[0, 0, 255], [128, 0, 255]]]
+
+
+def test_contribution_sums_to_coverage():
+    """Per-Gaussian blending weights (the pruning rank): at every pixel the
+    added weights alpha_i T_i telescope to 1 - T_final, so summed over
+    Gaussians they equal the summed alpha image; brute and plain agree."""
+    w = synth.make_c0()
+    S = oracle.scene_arrays(w)
+    ref = oracle.render_env(w, 0, S=S, contrib=True)
+    c = ref["contrib"]
+    assert c.shape == (w.background.n,) and (c >= 0).all()
+    np.testing.assert_allclose(c.sum(), ref["alpha"].astype(np.float64).sum(), rtol=1e-6)
+    wt = synth.make_tiny()
+    St = oracle.scene_arrays(wt)
+    a = oracle.render_env(wt, 0, S=St, contrib=True)
+    b = oracle.render_env(wt, 0, S=St, contrib=True, mode="brute")
+    np.testing.assert_allclose(a["contrib"], b["contrib"], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(a["contrib"].sum(), a["alpha"].astype(np.float64).sum(), rtol=1e-6)
