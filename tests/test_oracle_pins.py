@@ -441,3 +441,91 @@ def test_contribution_sums_to_coverage():
     b = oracle.render_env(wt, 0, S=St, contrib=True, mode="brute")
     np.testing.assert_allclose(a["contrib"], b["contrib"], rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(a["contrib"].sum(), a["alpha"].astype(np.float64).sum(), rtol=1e-6)
+
+
+# ---------------------------------------------------------------- Batch-LiDAR oracle
+
+def _sensor(rows=8, cols=32, elev=(-0.3, 0.3), q=(1.0, 0.0, 0.0, 0.0), t=(0.0, 0.0, 0.0), near=0.05):
+    return dict(q_ws=np.array(q, float), t_ws=np.array(t, float), rows=rows, cols=cols, elev_min=elev[0],
+                elev_max=elev[1], near=near)
+
+
+def test_lidar_single_gaussian_closed_forms():
+    """A Gaussian centred on ray (i, j) at distance D: t* = D, q_min = 0, so
+    hit = o and range = D.  Moving it sideways by h (isotropic sigma): q_min =
+    h^2 / sigma^2 along that ray."""
+    from oracle import lidar
+
+    sen = _sensor()
+    d = lidar.ray_directions(8, 32, -0.3, 0.3)
+    j, i, D, sig, o = 5, 9, 3.0, 0.05, 0.7
+    mu = D * d[j, i]
+    out = lidar.render_lidar([mu], [[1, 0, 0, 0]], [[np.log(sig)] * 3], [o], [-1], None, sen)
+    assert abs(out["hit"][j, i] - o) < 1e-12 and abs(out["range"][j, i] - D) < 1e-12
+    # sideways offset perpendicular to the ray (z' axis of a local frame)
+    perp = np.cross(d[j, i], [0.0, 0.0, 1.0])
+    perp /= np.linalg.norm(perp)
+    h = 0.04
+    out = lidar.render_lidar([mu + h * perp], [[1, 0, 0, 0]], [[np.log(sig)] * 3], [o], [-1], None, sen)
+    assert abs(out["hit"][j, i] - o * np.exp(-0.5 * h * h / sig ** 2)) < 1e-12
+    # t* is the foot of the perpendicular: the range stays D
+    assert abs(out["range"][j, i] - D) < 1e-12
+
+
+def test_lidar_occlusion_and_order():
+    """Two Gaussians on one ray: the nearer one (o = 0.99) leaves T = 0.01;
+    range = (0.99 D1 + 0.01 o2 D2) / (1 - T_final)."""
+    from oracle import lidar
+
+    sen = _sensor()
+    d = lidar.ray_directions(8, 32, -0.3, 0.3)[3, 17]
+    D1, D2, o2 = 2.0, 4.0, 0.5
+    out = lidar.render_lidar([D2 * d, D1 * d], [[1, 0, 0, 0]] * 2, [[np.log(0.05)] * 3] * 2, [o2, 0.99], [-1, -1],
+                             None, sen)
+    T = 0.01 * (1 - o2)
+    assert abs(out["hit"][3, 17] - (1 - T)) < 1e-12
+    assert abs(out["range"][3, 17] - (0.99 * D1 + 0.01 * o2 * D2) / (1 - T)) < 1e-12
+
+
+def test_lidar_joint_rigid_motion_and_links():
+    """Moving the sensor and the whole scene (background and links) by one
+    rigid motion leaves the scan unchanged; a link Gaussian moves with its
+    link pose."""
+    from oracle import lidar
+    from scipy.spatial.transform import Rotation
+
+    rng = np.random.default_rng([3, 41])
+    n = 60
+    mean = rng.uniform(-1.5, 1.5, (n, 3)) + np.array([2.5, 0.0, 0.0])
+    quat = rng.normal(size=(n, 4))
+    ls = rng.uniform(-2.5, -1.5, (n, 3))
+    op = rng.uniform(0.2, 0.95, n)
+    link_of = np.full(n, -1)
+    link_of[40:] = 0
+    lp = np.array([[0.9, 0.1, -0.2, 0.3, 0.2, -0.1, 0.1]])
+    lp[0, :4] /= np.linalg.norm(lp[0, :4])
+    sen = _sensor(rows=6, cols=24)
+    base = lidar.render_lidar(mean, quat, ls, op, link_of, lp, sen)
+    assert base["hit"].max() > 0.5
+    # joint motion M: world points x -> R x + c for the background and the link pose; sensor pose composed
+    R = Rotation.from_euler("xyz", [0.3, -0.2, 0.5]).as_matrix()
+    c = np.array([0.4, -1.0, 2.0])
+    qR = Rotation.from_matrix(R).as_quat()[[3, 0, 1, 2]]
+    mean2 = mean.copy()
+    mean2[:40] = mean[:40] @ R.T + c
+    quat2 = quat.copy()
+    q_bg = Rotation.from_quat(quat[:40][:, [1, 2, 3, 0]])
+    quat2[:40] = (Rotation.from_matrix(R) * q_bg).as_quat()[:, [3, 0, 1, 2]]
+    RL = Rotation.from_quat(lp[0, [1, 2, 3, 0]])
+    lp2 = lp.copy()
+    lp2[0, :4] = (Rotation.from_matrix(R) * RL).as_quat()[[3, 0, 1, 2]]
+    lp2[0, 4:] = R @ lp[0, 4:] + c
+    # sensor: x_s = Rs x_w + ts with x_w = R^T (x_w' - c)
+    Rs = lidar.quat_to_mat(sen["q_ws"])
+    sen2 = dict(sen)
+    sen2["q_ws"] = Rotation.from_matrix(Rs @ R.T).as_quat()[[3, 0, 1, 2]]
+    sen2["t_ws"] = sen["t_ws"] - Rs @ R.T @ c
+    moved = lidar.render_lidar(mean2, quat2, ls, op, link_of, lp2, sen2)
+    np.testing.assert_allclose(moved["hit"], base["hit"], atol=1e-9)
+    np.testing.assert_allclose(moved["range"], base["range"], atol=1e-9)
+    del qR
