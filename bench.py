@@ -70,13 +70,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0,
                     help="CPU-baseline sample: oracle envs rendered one by one until this much time has passed")
-    ap.add_argument("--workload", choices=["c1", "c3", "c4", "prune"], default="c1",
+    ap.add_argument("--workload", choices=["c1", "c3", "c4", "prune", "lidar"], default="c1",
                     help="c1: uniform 640x480 batch (headline); c3: batched uneven form through a plan")
     ap.add_argument("--no-graph", action="store_true", help="c3: eager plan launches instead of a CUDA graph")
     ap.add_argument("--obs", action="store_true",
                     help="c1 in the observation form: 8-bit RGB after per-env appearance randomisation + half depth")
     ap.add_argument("--rates", default="1000,3000,10000,30000", help="c4: offered request rates (req/s)")
     ap.add_argument("--prune-envs", type=int, default=64, help="prune: envs whose cameras rank the Gaussians")
+    ap.add_argument("--beams", type=int, default=64, help="lidar: beams (rows)")
+    ap.add_argument("--azimuth", type=int, default=1024, help="lidar: azimuth steps per revolution (columns)")
     ap.add_argument("--duration", type=float, default=2.0, help="c4: seconds of arrivals per rate")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="c4: HBM budget of the request loop")
     ap.add_argument("--slots", type=int, default=4, help="c4: stream slots (batches in flight)")
@@ -678,6 +680,74 @@ def run_prune(a, rank, world, local_rank):
     scene.close()
 
 
+
+def run_lidar(a, rank, world, local_rank):
+    """Batch-LiDAR on the c1 scene: every env carries a rotating LiDAR of
+    --beams x --azimuth rays (elevation -0.4..0.3 rad) at its jittered head
+    position; a step scans all envs (range + hit per ray) with the links posed
+    per env.  Reported in rays/s."""
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2604_25459_gb300 import gsbatch, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    E = a.envs
+    w = synth.make_c1(n_envs=E)
+    scene = gsbatch.scene_from_workload(w)
+    poses = torch.from_numpy(w.link_poses).to(dev)
+    rng = np.random.default_rng([E, 53])
+    sens = np.zeros(E, dtype=gsbatch.LIDAR_DTYPE)
+    sens["q_ws"] = [1.0, 0.0, 0.0, 0.0]
+    sens["t_ws"] = -(np.array([-1.0, 0.0, 1.4]) + rng.uniform(-0.2, 0.2, (E, 3)))
+    sens["rows"], sens["cols"] = a.beams, a.azimuth
+    sens["elev_min"], sens["elev_max"], sens["near_range"] = -0.4, 0.3, 0.05
+    R, Cc = a.beams, a.azimuth
+    out_r = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)
+    out_h = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        scene.render_lidar(poses, sens, out_r, out_h, stream=stream)
+    torch.cuda.synchronize()
+    scene.sync_status()
+    scene.set_profile(True)
+    scene.timings(reset=True)
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        scene.render_lidar(poses, sens, out_r, out_h, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    tim = scene.timings(reset=True)
+    scene.set_profile(False)
+    scene.sync_status()
+    ms = e0.elapsed_time(e1) / a.steps
+    hit_frac = float((out_h > 0.5).float().mean())
+    if rank == 0:
+        rays = E * R * Cc
+        line = {"metric": f"LiDAR rays/s ({E} envs x {R}x{Cc} rays, c1 scene)", "value": world * rays / (ms / 1e3),
+                "unit": "rays/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"c1 scene (500k room-shell background + 20x5k robot), {E} envs, rotating "
+                                       f"LiDAR {R} beams x {Cc} azimuth steps, elevation -0.4..0.3 rad",
+                           "rays_hit_over_half": hit_frac},
+                "env_scans_per_s": world * E / (ms / 1e3),
+                "phase_ms_per_step": {k: v[0] / a.steps for k, v in tim.items()},
+                "clocks": ck, "gpu_launches": None, "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    scene.close()
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -701,6 +771,8 @@ def main():
         run_c4(a, rank, world, local_rank)
     elif a.workload == "prune":
         run_prune(a, rank, world, local_rank)
+    elif a.workload == "lidar":
+        run_lidar(a, rank, world, local_rank)
     else:
         run_ours(a, rank, world, local_rank)
     if world > 1:

@@ -159,6 +159,37 @@ gs_status gs_render_batch_obs_host(gs_scene s, int n_envs, const float* link_pos
                                    const gs_appearance* appearance, uint8_t* rgb8, uint16_t* depth16,
                                    void* cuda_stream);
 
+/* Batch-LiDAR (the paper's ray-casting LiDAR over the same Gaussians, with
+ * dynamic objects and self-occlusion, Sec. III-E and Table II).  A rotating
+ * LiDAR of `rows` beams x `cols` azimuth steps; sensor frame x forward, y
+ * left, z up; ray (i, j) has azimuth 2 pi (i + 1/2) / cols and elevation
+ * elev_min + (elev_max - elev_min) (j + 1/2) / rows.  Each ray is composited
+ * front to back like a camera pixel (alpha = min(0.99, o exp(-q/2)) >= 1/255,
+ * stop when T (1 - alpha) < 1e-4, order by distance of the Gaussian's centre
+ * from the sensor, ties by global index), the Gaussian evaluated at its
+ * closest approach along the ray: with G = diag(e^-s) R^T in the sensor
+ * frame, a = G d and b = G mu, q = |a x b|^2 / |a|^2 at t* = a.b / |a|^2;
+ * Gaussians with t* <= near_range are skipped.  48 bytes. */
+typedef struct {
+    float q_ws[4];     /* world -> sensor rotation (w,x,y,z) */
+    float t_ws[3];     /* world -> sensor translation */
+    int32_t rows;      /* beams */
+    int32_t cols;      /* azimuth steps per revolution */
+    float elev_min;    /* radians */
+    float elev_max;    /* radians, > elev_min, both within (-pi/2, pi/2) */
+    float near_range;  /* > 0 */
+} gs_lidar;
+
+/* Scan n_envs environments:
+ *   link_poses  DEVICE as for gs_render_batch
+ *   sensors     HOST gs_lidar [n_envs] (all with the same rows and cols)
+ *   range       DEVICE float32 [n_envs][rows][cols]: sum(alpha T t*) / (1 - T), 0 where nothing is hit
+ *   hit         DEVICE float32 [n_envs][rows][cols] (1 - T), or NULL
+ * Bins on 16x16 tiles of the (azimuth, beam) grid whatever the scene's tile
+ * setting.  Errors as gs_render_batch (GS_ERR_INVALID for a bad sensor). */
+gs_status gs_render_lidar(gs_scene s, int n_envs, const float* link_poses, const gs_lidar* sensors, float* range,
+                          float* hit, void* cuda_stream);
+
 /* Contribution pass (support for pruning, a scene transform that follows the
  * paper's Gaussian pruning for speed and memory, Sec. III-C): renders n_envs
  * environments like gs_render_batch (one resolution, 16x16 tiles whatever

@@ -142,6 +142,7 @@ struct gs_scene_s {
     int counters = 0;
     DevBuf neval;
     DevBuf appear;  // appearance parameters copied from the host (observation form)
+    DevBuf lidar_tab;  // the current wave's LiDAR sensors
     // host staging of tables
     std::vector<EnvInfo> h_envs;
     std::vector<ProjBlock> h_blocks;
@@ -395,6 +396,7 @@ struct WaveIO {
     uint16_t* depth16 = nullptr;
     const gs_appearance* appear = nullptr;  // device, indexed by the wave's env
     float* score = nullptr;      // contribution pass (no images)
+    const gs_lidar* lidars = nullptr;  // LiDAR scan: device table of the wave's sensors
 };
 
 // Where a render's images go: float RGB / depth / alpha, or the observation
@@ -517,8 +519,10 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     P.mask = sc.mask.as<uint32_t>();
     P.dbg_hxy = debug ? sc.dbg_hxy.as<float2>() : nullptr;
     P.nvis = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() + 1 : nullptr;
+    P.lidars = io.lidars;
     PhaseTimer t2(s, st, GS_PHASE_PROJECT, timers);
-    CK(launch_project(s->D, P, wt.n_blocks, st), "projection");
+    if (io.lidars) CK(launch_project_lidar(P, wt.n_blocks, st), "LiDAR projection");
+    else CK(launch_project(s->D, P, wt.n_blocks, st), "projection");
     t2.done(1);
     ++*launches;
     // A3: counts + scan
@@ -638,6 +642,8 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.appear = io.appear;
         C.score = io.score;
         C.nbp = (unsigned)bg_slots(s->D.n_bg);
+        C.lidars = io.lidars;
+        C.r3 = P.r3;
         C.status = status;
         CK(cudaMemsetAsync(sc.work.p, 0, 4, st), "memset work counter");
         int ctas = 0;
@@ -1093,6 +1099,72 @@ gs_status gs_render_batch(gs_scene s, int n_envs, const float* link_poses, const
 gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
                                float* depth, float* alpha, void* cuda_stream) {
     return render_uniform(s, n_envs, link_poses, cams, rgb, depth, alpha, cuda_stream, true);
+}
+
+gs_status gs_render_lidar(gs_scene s, int n_envs, const float* link_poses, const gs_lidar* sensors, float* range,
+                          float* hit, void* cuda_stream) {
+    if (!s) return fail(GS_ERR_INVALID, "null scene");
+    if (n_envs < 0) return fail(GS_ERR_INVALID, "negative n_envs");
+    if (n_envs == 0) return GS_OK;
+    if (!sensors || !range) return fail(GS_ERR_INVALID, "null sensors or range output");
+    const int L = s->D.n_links;
+    if (L > 0 && !link_poses) return fail(GS_ERR_INVALID, "null link_poses with %d links", L);
+    const int rows = sensors[0].rows, cols = sensors[0].cols;
+    std::vector<gs_camera> cams((size_t)n_envs);
+    for (int e = 0; e < n_envs; ++e) {
+        const gs_lidar& l = sensors[e];
+        if (l.rows != rows || l.cols != cols)
+            return fail(GS_ERR_INVALID, "sensor %d: %dx%d rays differ from sensor 0 (%dx%d)", e, l.rows, l.cols, rows,
+                        cols);
+        if (l.rows <= 0 || l.cols <= 0 || l.rows > 65535 || l.cols > 65535)
+            return fail(GS_ERR_INVALID, "sensor %d: bad ray grid %dx%d", e, l.rows, l.cols);
+        if (!(l.elev_min < l.elev_max) || !(l.elev_min > -1.5707963f) || !(l.elev_max < 1.5707963f))
+            return fail(GS_ERR_INVALID, "sensor %d: elevation range must lie in (-pi/2, pi/2)", e);
+        if (!(l.near_range > 0.0f) || !std::isfinite(l.near_range))
+            return fail(GS_ERR_INVALID, "sensor %d: near_range must be > 0", e);
+        // the pose travels to the link-table kernel as a camera of the grid's size
+        gs_camera& c = cams[e];
+        c.fx = c.fy = 1.0f;
+        c.cx = 0.5f * (float)cols;
+        c.cy = 0.5f * (float)rows;
+        c.width = cols;
+        c.height = rows;
+        for (int k = 0; k < 4; ++k) c.q_cw[k] = l.q_ws[k];
+        for (int k = 0; k < 3; ++k) c.t_cw[k] = l.t_ws[k];
+        c.near_plane = l.near_range;
+        ST(check_cam(c, e));
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    CK(cudaSetDevice(s->device), "set device");
+    const size_t px = (size_t)rows * cols;
+    if (s->D.n == 0) {
+        CK(cudaMemsetAsync(range, 0, (size_t)n_envs * px * 4, st), "clear range");
+        if (hit) CK(cudaMemsetAsync(hit, 0, (size_t)n_envs * px * 4, st), "clear hit");
+        return GS_OK;
+    }
+    const int tw = 16, th = 16;
+    std::vector<EnvSpec> specs((size_t)n_envs);
+    for (int e = 0; e < n_envs; ++e) specs[e] = EnvSpec{&cams[e], 0, L, (long long)e * L, (long long)e * (long long)px};
+    ST(check_specs(s, specs, tw, th));
+    std::vector<std::pair<int, int>> waves;
+    ST(plan_waves(s, specs, tw, th, false, s->max_wave, 0, &waves));
+    int64_t launches = 0;
+    for (auto& w : waves) {
+        const int We = w.second - w.first;
+        CK(s->lidar_tab.ensure(sizeof(gs_lidar) * (size_t)We), "alloc sensors");
+        CK(cudaMemcpyAsync(s->lidar_tab.p, sensors + w.first, sizeof(gs_lidar) * (size_t)We, cudaMemcpyHostToDevice,
+                           st),
+           "copy sensors");
+        WaveTables wt{};
+        ST(upload_tables(s, specs, w.first, w.second, tw, th, 0, s->sc.envs, s->sc.blocks, s->sc.cams, st, false,
+                         &wt));
+        WaveIO io{link_poses, nullptr, range, hit, 0};
+        io.lidars = s->lidar_tab.as<gs_lidar>();
+        ST(run_wave(s, s->sc, wt, io, tw, th, 1, 0, st, true, &launches, nullptr));
+        s->stats.waves++;
+    }
+    s->stats.kernel_launches = launches;
+    return GS_OK;
 }
 
 gs_status gs_scene_contribution(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
@@ -1572,7 +1644,7 @@ void gs_scene_destroy(gs_scene s) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&s->g0, &s->g1, &s->g2, &s->g3, &s->gsh, &s->stage_rgb[0], &s->stage_rgb[1],
                       &s->stage_depth[0], &s->stage_depth[1], &s->stage_alpha[0], &s->stage_alpha[1], &s->poses,
-                      &s->neval, &s->appear};
+                      &s->neval, &s->appear, &s->lidar_tab};
     for (DevBuf* b : bufs) b->release();
     s->sc.release();
     for (auto& m : s->marks) {

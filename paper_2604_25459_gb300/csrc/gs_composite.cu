@@ -345,7 +345,9 @@ __device__ __forceinline__ bool reaches_rect(const float4& A, const float4& B, f
 // SC: contribution pass (pruning support): instead of writing images, add
 // each blended (pixel, splat) weight alpha T to score[global index], summed
 // per warp and splat before one atomic add.
-template <int TW, int TH, bool SC = false>
+// MODE 1: LiDAR scan (records of k_project_lidar; each "pixel" is a ray of
+// the (azimuth, beam) grid, the Gaussian evaluated at its closest approach).
+template <int TW, int TH, bool SC = false, int MODE = 0>
 __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 256 ? 8 : 12))) k_composite(CompParams P) {
     constexpr int NT = TW * TH / 2;
     constexpr int NB = NT;  // splats staged per batch (one per thread)
@@ -374,6 +376,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     uint16_t* cnt = reinterpret_cast<uint16_t*>(cbuf);
     uint32_t* hist = reinterpret_cast<uint32_t*>(cbuf);
     __shared__ uint32_t sG[SC ? NB : 1];  // contribution pass: slot of each staged splat
+    __shared__ float4 sD[MODE == 1 ? NB : 1];  // LiDAR: third row of G of each staged splat
     uint32_t* bins = reinterpret_cast<uint32_t*>(kbuf);  // partition counters (between windows only)
 
     __shared__ unsigned int s_item;
@@ -413,6 +416,34 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     const int px = wx0 + (lane & 7), py0 = wy0 + (lane >> 3), py1 = py0 + 4;
     const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
     const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f, fpy1 = (float)py1 + 0.5f;
+    float3 dir0 = make_float3(0.f, 0.f, 0.f), dir1 = dir0;  // LiDAR: the lane's two rays
+    float near_range = 0.0f;
+    if constexpr (MODE == 1) {
+        const gs_lidar* Ld = P.lidars + el;
+        const float em = __ldg(&Ld->elev_min), eM = __ldg(&Ld->elev_max);
+        const float phi = 6.283185307179586f * fpx / (float)W;
+        const float th0 = em + (eM - em) * fpy0 / (float)H, th1 = em + (eM - em) * fpy1 / (float)H;
+        float sp, cp, s0, c0, s1, c1;
+        sincosf(phi, &sp, &cp);
+        sincosf(th0, &s0, &c0);
+        sincosf(th1, &s1, &c1);
+        dir0 = make_float3(c0 * cp, c0 * sp, s0);
+        dir1 = make_float3(c1 * cp, c1 * sp, s1);
+        near_range = __ldg(&Ld->near_range);
+    }
+    // LiDAR: alpha and t* of a staged Gaussian (b, o | g0 | g1 | g2) on ray d
+    auto ray_eval = [&](const float4& A, const float4& B, const float4& C, const float4& D, const float3& d,
+                        float& al, float& ts) {
+        const float u0 = B.x * d.x + B.y * d.y + B.z * d.z;
+        const float u1 = C.x * d.x + C.y * d.y + C.z * d.z;
+        const float u2 = D.x * d.x + D.y * d.y + D.z * d.z;
+        const float aa = u0 * u0 + u1 * u1 + u2 * u2;
+        const float ab = u0 * A.x + u1 * A.y + u2 * A.z;
+        const float c0 = u1 * A.z - u2 * A.y, c1 = u2 * A.x - u0 * A.z, c2 = u0 * A.y - u1 * A.x;
+        const float q = (c0 * c0 + c1 * c1 + c2 * c2) / aa;
+        ts = ab / aa;
+        al = ts > near_range ? fminf(0.99f, A.w * ex2_approx(-0.72134752044448170f * q)) : 0.0f;
+    };
     bool done0 = !in0, done1 = !in1;
     float T0 = 1.0f, r0 = 0.0f, g0 = 0.0f, b0 = 0.0f, d0 = 0.0f;
     float T1 = 1.0f, r1 = 0.0f, g1 = 0.0f, b1 = 0.0f, d1 = 0.0f;
@@ -456,7 +487,18 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                     const float4 q2 = P.r2[ri];
                     const uint32_t rx = __float_as_uint(q1.w), ry = __float_as_uint(q2.w);
                     sA[s] = q0;
-                    sB[s] = make_float4(q1.x, q1.y, q1.z, log2f(255.0f * q0.z));  // alpha >= 1/255 iff q <= w
+                    if constexpr (MODE == 1) {
+                        // g2 = |g2| (g0 x g1) / (|g0| |g1|): the rows of G are orthogonal
+                        const float glen2 = __uint_as_float(P.r3[ri].w);
+                        const float cx = q1.y * q2.z - q1.z * q2.y, cy = q1.z * q2.x - q1.x * q2.z,
+                                    cz = q1.x * q2.y - q1.y * q2.x;
+                        const float k = glen2 * rsqrtf((q1.x * q1.x + q1.y * q1.y + q1.z * q1.z) *
+                                                       (q2.x * q2.x + q2.y * q2.y + q2.z * q2.z));
+                        sB[s] = make_float4(q1.x, q1.y, q1.z, 0.0f);
+                        sD[s] = make_float4(cx * k, cy * k, cz * k, 0.0f);
+                    } else {
+                        sB[s] = make_float4(q1.x, q1.y, q1.z, log2f(255.0f * q0.z));  // alpha >= 1/255 iff q <= w
+                    }
                     sC[s] = q2;
                     sR[s] = make_int4((int)(rx & 0xffffu), (int)((rx >> 16) - (rx & 0xffffu)), (int)(ry & 0xffffu),
                                       (int)((ry >> 16) - (ry & 0xffffu)));
@@ -479,7 +521,8 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         ov = R.x <= wx1 && R.x + R.y >= wx0 && R.z <= wy1 && R.z + R.w >= wy0;
                         // large splats: their box overstates the ellipse most (a box
                         // under 24 px in width + height is kept as it is)
-                        if (ov && R.y + R.w >= 24) ov = reaches_rect(sA[j], sB[j], (float)wx0 + 0.5f, (float)wy0 + 0.5f);
+                        if (MODE == 0 && ov && R.y + R.w >= 24)
+                            ov = reaches_rect(sA[j], sB[j], (float)wx0 + 0.5f, (float)wy0 + 0.5f);
                     }
                     uint32_t m = __ballot_sync(0xffffffffu, ov);
                     float2 score_pair = make_float2(0.0f, 0.0f);  // contribution pass only
@@ -500,7 +543,32 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         const bool h11 = !done1 && x1 && (unsigned)(py1 - R1.z) <= (unsigned)R1.w;
                         const bool h20 = !done0 && x2 && (unsigned)(py0 - R2.z) <= (unsigned)R2.w;
                         const bool h21 = !done1 && x2 && (unsigned)(py1 - R2.z) <= (unsigned)R2.w;
-                        if (h10 || h11 || h20 || h21) {
+                        if (MODE == 1 && (h10 || h11 || h20 || h21)) {
+                            const float4 A1 = sA[j1], B1 = sB[j1], C1 = sC[j1], D1 = sD[MODE == 1 ? j1 : 0];
+                            const float4 A2 = sA[j2], B2 = sB[j2], C2 = sC[j2], D2 = sD[MODE == 1 ? j2 : 0];
+                            float a10, a11, a20, a21, t10, t11, t20, t21;
+                            ray_eval(A1, B1, C1, D1, dir0, a10, t10);
+                            ray_eval(A1, B1, C1, D1, dir1, a11, t11);
+                            ray_eval(A2, B2, C2, D2, dir0, a20, t20);
+                            ray_eval(A2, B2, C2, D2, dir1, a21, t21);
+                            const float4 none = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (h10 && a10 >= (1.0f / 255.0f)) {
+                                ++ncomp;
+                                blend(a10, none, t10, T0, r0, g0, b0, d0, done0);
+                            }
+                            if (h11 && a11 >= (1.0f / 255.0f)) {
+                                ++ncomp;
+                                blend(a11, none, t11, T1, r1, g1, b1, d1, done1);
+                            }
+                            if (h20 && !done0 && a20 >= (1.0f / 255.0f)) {
+                                ++ncomp;
+                                blend(a20, none, t20, T0, r0, g0, b0, d0, done0);
+                            }
+                            if (h21 && !done1 && a21 >= (1.0f / 255.0f)) {
+                                ++ncomp;
+                                blend(a21, none, t21, T1, r1, g1, b1, d1, done1);
+                            }
+                        } else if (MODE == 0 && (h10 || h11 || h20 || h21)) {
                             const float4 A1 = sA[j1], B1 = sB[j1];
                             const float4 A2 = sA[j2], B2 = sB[j2];
                             const float dx1 = fpx - A1.x, dx2 = fpx - A2.x;
@@ -831,7 +899,20 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         else if (P.depth) P.depth[pix] = dep;
         if (P.alpha) P.alpha[pix] = a;
     };
-    if (!SC) {
+    if (MODE == 1) {  // range and hit per ray
+        if (in0) {
+            const size_t pix = pix_base + (size_t)py0 * W + px;
+            const float a = 1.0f - T0;
+            P.depth[pix] = a > 0.0f ? d0 / a : 0.0f;
+            if (P.alpha) P.alpha[pix] = a;
+        }
+        if (in1) {
+            const size_t pix = pix_base + (size_t)py1 * W + px;
+            const float a = 1.0f - T1;
+            P.depth[pix] = a > 0.0f ? d1 / a : 0.0f;
+            if (P.alpha) P.alpha[pix] = a;
+        }
+    } else if (!SC) {
         if (in0) store(py0, T0, r0, g0, b0, d0);
         if (in1) store(py1, T1, r1, g1, b1, d1);
     }
@@ -842,7 +923,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     }  // claims
 }
 
-template <int TW, int TH, bool SC = false>
+template <int TW, int TH, bool SC = false, int MODE = 0>
 static cudaError_t resident_ctas(int* out) {
     constexpr int NT = TW * TH / 2;
     static int per_sm[64] = {0};  // resident CTAs per SM, per device
@@ -853,7 +934,7 @@ static cudaError_t resident_ctas(int* out) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (per_sm[dev] == 0) {
         int ps = 0, n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_composite<TW, TH, SC>, NT, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_composite<TW, TH, SC, MODE>, NT, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -864,11 +945,11 @@ static cudaError_t resident_ctas(int* out) {
     return cudaSuccess;
 }
 
-template <int TW, int TH, bool SC = false>
+template <int TW, int TH, bool SC = false, int MODE = 0>
 static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas) {
     constexpr int NT = TW * TH / 2;
     int full = 0;
-    cudaError_t e = resident_ctas<TW, TH, SC>(&full);
+    cudaError_t e = resident_ctas<TW, TH, SC, MODE>(&full);
     if (e != cudaSuccess) return e;
     const unsigned items = P.item_end - P.item_begin;
     unsigned grid = (unsigned)full;
@@ -877,7 +958,7 @@ static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas)
     if (P.spill && grid > P.spill_ctas) grid = P.spill_ctas;
     if (grid == 0) grid = 1;
     *ctas = (int)grid;
-    k_composite<TW, TH, SC><<<grid, NT, 0, st>>>(P);
+    k_composite<TW, TH, SC, MODE><<<grid, NT, 0, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -886,6 +967,10 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
     if (P.item_end <= P.item_begin) return cudaSuccess;
     if (P.spill && (P.spill_cap < (unsigned)kCompCap || P.spill_cap > (unsigned)kSpillMax || P.spill_ctas == 0))
         return cudaErrorInvalidValue;
+    if (P.lidars) {  // LiDAR scans run on 16x16 tiles only
+        if (P.tile_w != 16 || P.tile_h != 16 || P.score) return cudaErrorInvalidValue;
+        return launch_tiles<16, 16, false, 1>(P, st, ctas);
+    }
     if (P.score) {  // the contribution pass runs on 16x16 tiles only
         if (P.tile_w != 16 || P.tile_h != 16) return cudaErrorInvalidValue;
         return launch_tiles<16, 16, true>(P, st, ctas);

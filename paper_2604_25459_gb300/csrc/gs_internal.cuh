@@ -111,6 +111,7 @@ struct ProjParams {
     uint32_t* mask;
     float2* dbg_hxy;  // nullable, per record slot
     unsigned long long* nvis;  // nullable: visible (env, Gaussian) pair counter
+    const gs_lidar* lidars;    // LiDAR projection only: per env of the wave
 };
 
 struct BinParams {
@@ -159,6 +160,8 @@ struct CompParams {
     const gs_appearance* appear;  // nullable: per env (wave-local index) for rgb8
     float* score;         // nullable: contribution pass (no images): score[g] += sum of alpha T
     unsigned int nbp;     // background slots (slot j < nbp is background Gaussian j)
+    const gs_lidar* lidars;  // nullable: LiDAR scan (range in depth, hit in alpha), per env of the wave
+    const uint4* r3;         // LiDAR scan: records' fourth word (|g2|)
     uint32_t* status;
 };
 
@@ -170,6 +173,11 @@ cudaError_t launch_prep(const float* mean, const float* quat, const void* log_sc
 cudaError_t launch_link_table(const float* poses, const gs_camera* cams, const EnvInfo* envs, int We, int n_items,
                               LinkXf* out, uint32_t* status, cudaStream_t st);
 cudaError_t launch_project(const DevGaussians& D, const ProjParams& P, int n_blocks, cudaStream_t st);
+// LiDAR records: r0 = (b, o), r1 = (g0, x-range), r2 = (g1, y-range), r3 =
+// (x-range, y-range, distance bits, |g2| bits) with g_k the rows of
+// diag(e^-s) R^T in the sensor frame and b = G mu; ranges over the
+// (azimuth, beam) grid.
+cudaError_t launch_project_lidar(const ProjParams& P, int n_blocks, cudaStream_t st);
 // grid.x covers the largest env's mask words; max_T sizes the shared histogram
 cudaError_t launch_count(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st);
 cudaError_t launch_scan(const EnvInfo* envs, const uint32_t* counts, uint32_t* off_local,

@@ -1,0 +1,131 @@
+// Batch-LiDAR projection: every (env, Gaussian) of a wave against the env's
+// rotating LiDAR.  The paper's Batch-LiDAR ray-casts the 3DGS scene with its
+// moving links (Sec. III-E, Table II); here a scan is rendered like an image
+// over the (azimuth, beam) grid: this kernel writes, per visible pair, the
+// Gaussian's ray-space factors in the sensor frame and a conservative grid box
+// of the rays it can reach, and the binning kernels and the compositor (its
+// LiDAR form) do the rest.
+//
+// A Gaussian with covariance F F^T, F = R diag(e^s) (columns f_k = e^{s_k} r_k),
+// has q(x) = sum_k (g_k . (x - mu))^2 with g_k = f_k / |f_k|^2 = e^{-s_k} r_k.
+// Along a ray t d: a_k = g_k . d and b_k = g_k . mu give q(t) = |t a - b|^2.
+// Since q(x) >= |x - mu|^2 / max_k e^{2 s_k} >= |x - mu|^2 / tr(F F^T), every
+// point with alpha >= 1/255 (q <= q*) lies within r = sqrt(q* tr) of mu: the
+// rays that can reach it lie within the cone of half-angle asin(r / |mu|).
+#include "gs_internal.cuh"
+
+namespace gsb {
+
+namespace {
+
+constexpr float kTwoPi = 6.283185307179586f;
+constexpr float kHalfPi = 1.5707963267948966f;
+
+// Inclusive grid range [lo, hi] of the centres c_k = (k + 1/2) step + origin
+// within [a, b]; false if none.
+__device__ __forceinline__ bool grid_range(float a, float b, float origin, float step, int n, int& lo, int& hi) {
+    float l = ceilf((a - origin) / step - 0.5f);
+    float h = floorf((b - origin) / step - 0.5f);
+    l = fmaxf(l, 0.0f);
+    h = fminf(h, (float)(n - 1));
+    if (!(l <= h)) return false;
+    lo = (int)l;
+    hi = (int)h;
+    return true;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_project_lidar(ProjParams P) {
+    const ProjBlock blk = P.blocks[blockIdx.x];
+    const int t = threadIdx.x;
+    const bool act = t < blk.n;
+    const int lane = t & 31;
+    const long long g = blk.g_first + t;
+    const unsigned int local = blk.local_first + (unsigned)t;
+    const bool warp_live = (t - lane) < blk.n;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+    if (act) {
+        a0 = __ldg(P.p0 + g);
+        a1 = __ldg(P.p1 + g);
+        a2 = __ldg(P.p2 + g);
+        a3 = __ldg(P.p3 + g);
+    }
+    const int li = __float_as_int(a3.w) - blk.lb;
+    const float qstar = a3.y;
+    const bool live = act && qstar >= 0.0f;
+    const float reach = sqrtf(fmaxf(qstar, 0.0f) * a3.z) * 1.001f + 1e-6f;  // support radius (metres)
+    for (int el = blk.e0; el < blk.e1; ++el) {
+        bool vis = false;
+        const EnvInfo* E = P.envs + el;
+        if (live) {
+            const LinkXf* Xp = P.xf + __ldg(&E->xf_base) + li;
+            const float4 r0 = __ldg(&Xp->r0), r1 = __ldg(&Xp->r1), r2 = __ldg(&Xp->r2);
+            const float mx = r0.x * a0.x + r0.y * a0.y + r0.z * a0.z + r0.w;
+            const float my = r1.x * a0.x + r1.y * a0.y + r1.z * a0.z + r1.w;
+            const float mz = r2.x * a0.x + r2.y * a0.y + r2.z * a0.z + r2.w;
+            const float dist = sqrtf(mx * mx + my * my + mz * mz);
+            const gs_lidar* L = P.lidars + el;
+            const int rows = __ldg(&L->rows), cols = __ldg(&L->cols);
+            const float em = __ldg(&L->elev_min), eM = __ldg(&L->elev_max);
+            const float near = __ldg(&L->near_range);
+            if (dist + reach > near) {
+                int i0 = 0, i1 = cols - 1, j0 = 0, j1 = rows - 1;
+                bool any = true;
+                if (reach < dist) {
+                    const float rho = asinf(fminf(1.0f, reach / dist)) * 1.001f + 1e-5f;
+                    const float thc = asinf(fmaxf(-1.0f, fminf(1.0f, mz / dist)));
+                    any = grid_range(thc - rho, thc + rho, em, (eM - em) / (float)rows, rows, j0, j1);
+                    if (any && fabsf(thc) + rho < kHalfPi) {
+                        const float dphi = asinf(fminf(1.0f, sinf(rho) / cosf(thc))) * 1.001f + 1e-5f;
+                        float phc = atan2f(my, mx);
+                        if (phc < 0.0f) phc += kTwoPi;
+                        const float lo = phc - dphi, hi = phc + dphi;
+                        if (lo >= 0.0f && hi < kTwoPi)  // a box across the seam at 0 takes every column
+                            any = grid_range(lo, hi, 0.0f, kTwoPi / (float)cols, cols, i0, i1);
+                    }
+                }
+                if (any) {
+                    // sensor-frame columns of F, then g_k = f_k / |f_k|^2 and b = G mu
+                    float f[3][3];
+                    const float F[9] = {a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3.x};  // row-major
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        f[k][0] = r0.x * F[k] + r0.y * F[3 + k] + r0.z * F[6 + k];
+                        f[k][1] = r1.x * F[k] + r1.y * F[3 + k] + r1.z * F[6 + k];
+                        f[k][2] = r2.x * F[k] + r2.y * F[3 + k] + r2.z * F[6 + k];
+                    }
+                    float gk[3][3], b[3], glen2 = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float n2 = f[k][0] * f[k][0] + f[k][1] * f[k][1] + f[k][2] * f[k][2];
+                        const float inv = 1.0f / n2;
+                        gk[k][0] = f[k][0] * inv;
+                        gk[k][1] = f[k][1] * inv;
+                        gk[k][2] = f[k][2] * inv;
+                        b[k] = gk[k][0] * mx + gk[k][1] * my + gk[k][2] * mz;
+                        if (k == 2) glen2 = inv;  // |g_2|^2 = 1 / |f_2|^2
+                    }
+                    const uint32_t rx = (uint32_t)i0 | ((uint32_t)i1 << 16);
+                    const uint32_t ry = (uint32_t)j0 | ((uint32_t)j1 << 16);
+                    const size_t ri = (size_t)__ldg(&E->rec_base) + local;
+                    P.r0[ri] = make_float4(b[0], b[1], b[2], a0.w);
+                    P.r1[ri] = make_float4(gk[0][0], gk[0][1], gk[0][2], __uint_as_float(rx));
+                    P.r2[ri] = make_float4(gk[1][0], gk[1][1], gk[1][2], __uint_as_float(ry));
+                    P.r3[ri] = make_uint4(rx, ry, __float_as_uint(dist), __float_as_uint(sqrtf(glen2)));
+                    vis = true;
+                }
+            }
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, vis);
+        if (lane == 0 && warp_live) P.mask[(size_t)__ldg(&E->mask_base) + (local >> 5)] = m;
+    }
+}
+
+cudaError_t launch_project_lidar(const ProjParams& P, int n_blocks, cudaStream_t st) {
+    if (n_blocks == 0) return cudaSuccess;
+    k_project_lidar<<<n_blocks, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace gsb

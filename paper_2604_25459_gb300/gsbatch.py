@@ -61,6 +61,11 @@ ENV_DTYPE = np.dtype([("cam", CAMERA_DTYPE), ("link_begin", "<i4"), ("link_end",
 assert ENV_DTYPE.itemsize == 80
 PLAN_AUTOTUNE, PLAN_GRAPH = 1, 2
 
+# gs_lidar in include/gsbatch.h (48 bytes)
+LIDAR_DTYPE = np.dtype([("q_ws", "<f4", (4,)), ("t_ws", "<f4", (3,)), ("rows", "<i4"), ("cols", "<i4"),
+                        ("elev_min", "<f4"), ("elev_max", "<f4"), ("near_range", "<f4")])
+assert LIDAR_DTYPE.itemsize == 48
+
 
 class GsServerConfig(C.Structure):
     _fields_ = [("budget_bytes", C.c_int64), ("max_inflight", C.c_int), ("max_batch_envs", C.c_int),
@@ -90,6 +95,7 @@ _SIGS = {
     "gs_render_batch_v": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_render_batch_obs": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_scene_contribution": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 4),
+    "gs_render_lidar": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 5),
     "gs_render_batch_obs_host": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_plan_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "gs_plan_launch": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
@@ -334,6 +340,24 @@ class Scene:
         _check(lib().gs_render_batch_obs_host(self._h, E, _ptr(link_poses), _ptr(cams), _ptr(appearance), _ptr(rgb8),
                                               _ptr(depth16), _stream_handle(stream)))
         return rgb8, depth16
+
+    def render_lidar(self, link_poses, sensors: np.ndarray, rng=None, hit=None, want_hit: bool = True, stream=None):
+        """Batch-LiDAR scan (gs_render_lidar): sensors numpy LIDAR_DTYPE [E];
+        returns (range [E, rows, cols], hit [E, rows, cols] or None) CUDA tensors."""
+        import torch
+
+        sensors = np.ascontiguousarray(sensors, dtype=LIDAR_DTYPE)
+        E = int(sensors.shape[0])
+        R, Cc = (int(sensors["rows"][0]), int(sensors["cols"][0])) if E else (0, 0)
+        if rng is None:
+            rng = torch.empty((E, R, Cc), dtype=torch.float32, device="cuda")
+        if hit is None and want_hit:
+            hit = torch.empty((E, R, Cc), dtype=torch.float32, device="cuda")
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        _check(lib().gs_render_lidar(self._h, E, _ptr(link_poses), _ptr(sensors), _ptr(rng), _ptr(hit),
+                                     _stream_handle(stream)))
+        return rng, hit
 
     def contribution(self, link_poses, cams: np.ndarray, scores=None, stream=None):
         """Add each Gaussian's summed blending weight over the envs' pixels to
