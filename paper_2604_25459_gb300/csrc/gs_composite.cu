@@ -5,18 +5,21 @@
 // alpha = min(0.99, o exp(-q/2)) reaches 1/255, in depth order, until the
 // transmittance would drop below 1e-4; Sec. III-A asks for RGB and depth.
 //
-// One CTA renders one (env, tile); each warp owns an 8x8 pixel subtile and
-// each lane two of its pixels.
-// The tile's bucket of keys (depth bits << 32 | global index) is consumed in
-// depth windows of at most kCompCap keys: a window is chosen by a radix
-// histogram over the bucket (so the long buckets of dense robot tiles are
-// never sorted past the point where every pixel has terminated), gathered into
-// shared memory and sorted there by a block-wide LSD radix sort over only the
-// depth bits that vary inside the window (4-bit digits), followed by a fix-up
-// that orders the rare runs of equal depth by global index.  The window is
-// then composited in batches whose records are staged in shared memory;
-// warps test 32 splats at a time against their subtile with one ballot and
-// evaluate only the overlapping ones.
+// Persistent CTAs claim (env, tile) items; each warp owns an 8x8 pixel
+// subtile and each lane two of its pixels.  The tile's bucket of keys (depth
+// bits << 32 | record slot) is consumed in depth windows of at most kCompCap
+// keys: a short bucket is one window; a long one is first partitioned into
+// kBins key ranges through the CTA's spill region, and windows are runs of
+// ranges, so sorting stops at the window where every pixel has terminated.
+// Each window is sorted in shared memory (a counting sort by depth ranges,
+// or LSD radix passes when the depths crowd, then index order within equal
+// depths) and composited in batches whose records are staged in shared
+// memory; warps test 32 splats at a time against their subtile with one
+// ballot (box, then the exact ellipse for large splats) and evaluate only the
+// overlapping ones.  Besides the image form the kernel has an observation
+// form (8-bit colour after per-env appearance, half depth), a contribution
+// form (per-Gaussian blending weights, for pruning) and a LiDAR form (rays of
+// an (azimuth, beam) grid, Gaussians evaluated in ray space).
 #include "gs_internal.cuh"
 
 namespace gsb {
@@ -440,8 +443,9 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         const float aa = u0 * u0 + u1 * u1 + u2 * u2;
         const float ab = u0 * A.x + u1 * A.y + u2 * A.z;
         const float c0 = u1 * A.z - u2 * A.y, c1 = u2 * A.x - u0 * A.z, c2 = u0 * A.y - u1 * A.x;
-        const float q = (c0 * c0 + c1 * c1 + c2 * c2) / aa;
-        ts = ab / aa;
+        const float inv = 1.0f / aa;
+        const float q = (c0 * c0 + c1 * c1 + c2 * c2) * inv;
+        ts = ab * inv;
         al = ts > near_range ? fminf(0.99f, A.w * ex2_approx(-0.72134752044448170f * q)) : 0.0f;
     };
     bool done0 = !in0, done1 = !in1;
