@@ -1696,7 +1696,7 @@ struct gs_server_s {
         double admit = -1, done = -1;
         int status = 0;
     };
-    std::vector<Req> reqs;
+    std::deque<Req> reqs;  // element addresses stay valid while submit appends
     std::deque<int64_t> scheduled;  // not yet arrived, by arrival time
     std::deque<int64_t> pending;    // arrived, not admitted
     std::deque<int64_t> completed;  // done, not yet polled
@@ -1713,6 +1713,7 @@ struct gs_server_s {
         bool failed = false;          // its launch failed (requests carry the status)
         int scene = -1;
         std::vector<int64_t> batch;   // request ids, in launch order
+        std::vector<const Req*> rq;   // the same requests (taken under the lock: launches run without it)
         double bytes = 0;
         std::atomic<int> done{0};
         double t_done = 0;
@@ -1772,11 +1773,23 @@ gs_status server_launch(gs_server sv, gs_server_s::Slot& sl) {
     const int L = s->D.n_links;
     auto& batch = sl.batch;
     const size_t n = batch.size();
-    std::stable_sort(batch.begin(), batch.end(), [&](int64_t x, int64_t y) {
-        const gs_camera& a = sv->envs[sv->reqs[x].env].cam;
-        const gs_camera& b = sv->envs[sv->reqs[y].env].cam;
-        return (int64_t)a.width * a.height < (int64_t)b.width * b.height;
-    });
+    {
+        std::vector<size_t> ord(n);
+        for (size_t i = 0; i < n; ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) {
+            const gs_camera& a = sv->envs[sl.rq[x]->env].cam;
+            const gs_camera& b = sv->envs[sl.rq[y]->env].cam;
+            return (int64_t)a.width * a.height < (int64_t)b.width * b.height;
+        });
+        std::vector<int64_t> ids(n);
+        std::vector<const gs_server_s::Req*> rqs(n);
+        for (size_t i = 0; i < n; ++i) {
+            ids[i] = batch[ord[i]];
+            rqs[i] = sl.rq[ord[i]];
+        }
+        batch.swap(ids);
+        sl.rq.swap(rqs);
+    }
     const size_t pose_floats = std::max<size_t>(1, n * (size_t)L * 7);
     if (pose_floats > sl.h_cap) {
         if (sl.h_poses) cudaFreeHost(sl.h_poses);
@@ -1798,7 +1811,7 @@ gs_status server_launch(gs_server sv, gs_server_s::Slot& sl) {
     double est = 0, spread = 0;  // sum of the running averages; the largest (most seen - average)
     bool known = true;
     for (size_t i = 0; i < n; ++i) {
-        const auto& rq = sv->reqs[batch[i]];
+        const auto& rq = *sl.rq[i];
         const auto& ev = sv->envs[rq.env];
         const int nl = ev.link_end - ev.link_begin;
         if (nl > 0) memcpy(sl.h_poses + i * (size_t)L * 7, rq.poses.data(), sizeof(float) * nl * 7);
@@ -1887,6 +1900,7 @@ void server_loop(gs_server sv) {
                     sv->inflight_bytes -= sl->bytes;
                     sl->busy = false;
                     sl->batch.clear();
+                    sl->rq.clear();
                     worked = true;
                 }
             }
@@ -1938,6 +1952,8 @@ void server_loop(gs_server sv) {
                 slp->failed = false;
                 slp->scene = scene;
                 slp->batch = batch;
+                slp->rq.clear();
+                for (int64_t id : batch) slp->rq.push_back(&sv->reqs[id]);
                 slp->bytes = bytes;
                 sv->inflight_bytes += bytes;
                 sv->stats.batches++;
