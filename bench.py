@@ -86,6 +86,19 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over the ranks of the process group (x itself on one
+    rank): the job's time is that of its slowest rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -268,11 +281,7 @@ def run_ours(a, rank, world, local_rank):
     lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(a.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
     scene.sync_status()
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total_ms, world, dev)
     ms_step = t_max / a.steps
     value = world * E * a.steps / (t_max / 1e3)
 
@@ -342,11 +351,7 @@ def run_ours(a, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(a.e2e_steps):
             host_step()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
         e2e = {"value": world * E * a.e2e_steps / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(poses_h.nbytes + w.cams.nbytes),
                "d2h_bytes_per_step": int(rgb_h.nbytes + depth_h.nbytes),
@@ -440,11 +445,7 @@ def run_c3(a, rank, world, local_rank):
     ck = clocks.stop()
     scene.sync_status()
     lat = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(a.steps))
-    total_ms = evs[0].elapsed_time(evs[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), world, dev)
     info = plan.info()
     if rank == 0:
         value = world * E * a.steps / (total_ms / 1e3)
