@@ -9,9 +9,10 @@
 // A Gaussian with covariance F F^T, F = R diag(e^s) (columns f_k = e^{s_k} r_k),
 // has q(x) = sum_k (g_k . (x - mu))^2 with g_k = f_k / |f_k|^2 = e^{-s_k} r_k.
 // Along a ray t d: a_k = g_k . d and b_k = g_k . mu give q(t) = |t a - b|^2.
-// Since q(x) >= |x - mu|^2 / max_k e^{2 s_k} >= |x - mu|^2 / tr(F F^T), every
-// point with alpha >= 1/255 (q <= q*) lies within r = sqrt(q* tr) of mu: the
-// rays that can reach it lie within the cone of half-angle asin(r / |mu|).
+// Since q(x) >= |x - mu|^2 / max_k e^{2 s_k} = |x - mu|^2 / max_k |f_k|^2, every
+// point with alpha >= 1/255 (q <= q*) lies within r = sqrt(q*) max_k |f_k| of
+// mu: the rays that can reach it lie within the cone of half-angle
+// asin(r / |mu|).
 #include "gs_internal.cuh"
 
 namespace gsb {
@@ -54,7 +55,15 @@ __global__ void __launch_bounds__(256) k_project_lidar(ProjParams P) {
     const int li = __float_as_int(a3.w) - blk.lb;
     const float qstar = a3.y;
     const bool live = act && qstar >= 0.0f;
-    const float reach = sqrtf(fmaxf(qstar, 0.0f) * a3.z) * 1.001f + 1e-6f;  // support radius (metres)
+    // support radius (metres): sqrt(q*) times the largest scale (the longest column of F)
+    float fmax2 = 0.0f;
+    {
+        const float F[9] = {a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3.x};  // row-major
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            fmax2 = fmaxf(fmax2, F[k] * F[k] + F[3 + k] * F[3 + k] + F[6 + k] * F[6 + k]);
+    }
+    const float reach = sqrtf(fmaxf(qstar, 0.0f) * fmax2) * 1.001f + 1e-6f;
     for (int el = blk.e0; el < blk.e1; ++el) {
         bool vis = false;
         const EnvInfo* E = P.envs + el;
