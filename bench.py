@@ -39,9 +39,9 @@ UNIT = "env-frames/s"
 # summarised in profiles/k_composite_c1.md (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 32-env launch, divided by 32), valid only for
 # the compositor sources it was taken on.
-COMPOSITE_TRAFFIC_PER_ENV = (1.163138e9 + 0.592757e9) / 32
+COMPOSITE_TRAFFIC_PER_ENV = (1.165535e9 + 0.593543e9) / 32
 COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu", "paper_2604_25459_gb300/csrc/gs_internal.cuh")
-COMPOSITE_TRAFFIC_SHA = "8c888d3999262f12"
+COMPOSITE_TRAFFIC_SHA = "7588bec7e93458de"
 
 
 def _sources_sha(paths) -> str:
