@@ -120,10 +120,13 @@ gs_status gs_scene_attach_links(gs_scene s, int n_links, const int64_t* link_off
 gs_status gs_render_batch(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
                           float* depth, float* alpha, void* cuda_stream);
 
-/* As gs_render_batch, but link_poses, rgb, depth and alpha are HOST buffers
- * (pinned memory gives the fastest copies).  The library copies the poses in,
- * renders wave by wave and copies each wave's images out while the next wave
- * renders; the call returns when all images are on the host. */
+/* As gs_render_batch, but link_poses, rgb, depth and alpha are HOST buffers.
+ * The library copies the poses in.  Page-locked outputs (cudaHostAlloc /
+ * cudaMallocHost / registered memory) are mapped into the device's address
+ * space, so the compositor stores the images straight into them; other host
+ * memory is rendered wave by wave into device staging and each wave's images
+ * are copied out while the next wave renders.  The call returns when all
+ * images are on the host. */
 gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams, float* rgb,
                                float* depth, float* alpha, void* cuda_stream);
 

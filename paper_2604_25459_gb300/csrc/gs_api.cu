@@ -781,6 +781,24 @@ gs_status clear_outputs(float* rgb, float* depth, float* alpha, size_t px, cudaS
     return GS_OK;
 }
 
+// Device address of a page-locked host buffer (true, *dev set), true for
+// NULL (nothing to write), false for memory the device cannot address as is.
+template <typename T>
+bool device_view(T* host, T** dev) {
+    if (!host) {
+        *dev = nullptr;
+        return true;
+    }
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();  // pageable memory may report an error: not direct
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    *dev = static_cast<T*>(a.devicePointer);
+    return true;
+}
+
 // An empty scene in the observation form: every pixel of env e is the
 // appearance transform of black (the same value in all three channels), depth 0.
 gs_status clear_obs(const Outputs& o, int E, size_t px, const gs_appearance* appear_host, cudaStream_t st, bool host) {
@@ -853,6 +871,21 @@ gs_status render_uniform(gs_scene s, int E, const float* link_poses, const gs_ca
         CK(s->poses.ensure((size_t)E * L * 28), "alloc poses");
         CK(cudaMemcpyAsync(s->poses.p, link_poses, (size_t)E * L * 28, cudaMemcpyHostToDevice, st), "copy poses");
         poses_dev = s->poses.as<float>();
+    }
+    if (host_mode) {
+        // Pinned (page-locked) host outputs are mapped into the device's
+        // address space: the compositor then stores the images straight into
+        // them and no staging copy is needed; other host memory goes through
+        // device staging and copies.
+        Outputs m = o;
+        const bool direct = device_view(o.rgb, &m.rgb) && device_view(o.depth, &m.depth) &&
+                            device_view(o.alpha, &m.alpha) && device_view(o.rgb8, &m.rgb8) &&
+                            device_view(o.depth16, &m.depth16);
+        if (direct) {
+            ST(render_specs(s, specs, poses_dev, m, st, Out::Device, px));
+            CK(cudaStreamSynchronize(st), "sync render");
+            return GS_OK;
+        }
     }
     return render_specs(s, specs, poses_dev, o, st, host_mode ? Out::Host : Out::Device, px);
 }

@@ -53,12 +53,17 @@ def test_randomised_appearance_against_oracle_and_host_path():
     torch.cuda.synchronize()
     scene.sync_status()
     g8, gd = rgb8.cpu().numpy(), d16.cpu().numpy()
-    # host buffers: the same bytes
+    # host buffers (pageable: staged; page-locked: written directly): the same bytes
     h8 = np.zeros_like(g8)
     hd = np.zeros_like(gd)
     scene.render_obs_host(w.link_poses, w.cams, ap, h8, hd)
     np.testing.assert_array_equal(h8, g8)
     np.testing.assert_array_equal(hd, gd)
+    p8 = torch.zeros(g8.shape, dtype=torch.uint8).pin_memory().numpy()
+    pd = torch.zeros(gd.shape, dtype=torch.float16).pin_memory().numpy()
+    scene.render_obs_host(w.link_poses, w.cams, ap, p8, pd)
+    np.testing.assert_array_equal(p8, g8)
+    np.testing.assert_array_equal(pd, gd)
     # against the FP64 oracle: the colour differs by < 2e-3 before quantisation,
     # so the 8-bit value by at most one step (non-ambiguous pixels)
     S = oracle.scene_arrays(w)

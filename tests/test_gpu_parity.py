@@ -118,7 +118,11 @@ def test_tile_shape_and_batch_invariance_bit_exact():
         np.testing.assert_array_equal(alone[k][0], base[k][3])
 
 
-def test_host_buffers_match_device():
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffers_match_device(pinned):
+    """Host outputs: page-locked buffers are written by the compositor
+    directly, pageable ones through device staging and copies; both equal the
+    device render."""
     import torch
 
     w = synth.make_c1(n_envs=5, width=64, height=48, f=50.0, n_bg=20_000, per_link=500)
@@ -126,9 +130,14 @@ def test_host_buffers_match_device():
     scene = gsbatch.scene_from_workload(w)
     scene.set_wave(2)
     E, H, W = 5, 48, 64
-    rgb = torch.empty((E, H, W, 3)).pin_memory().numpy()
-    depth = torch.empty((E, H, W)).pin_memory().numpy()
-    alpha = torch.empty((E, H, W)).pin_memory().numpy()
+    if pinned:
+        rgb = torch.empty((E, H, W, 3)).pin_memory().numpy()
+        depth = torch.empty((E, H, W)).pin_memory().numpy()
+        alpha = torch.empty((E, H, W)).pin_memory().numpy()
+    else:
+        rgb = np.empty((E, H, W, 3), np.float32)
+        depth = np.empty((E, H, W), np.float32)
+        alpha = np.empty((E, H, W), np.float32)
     scene.render_host(np.ascontiguousarray(w.link_poses), w.cams, rgb, depth, alpha)
     scene.close()
     np.testing.assert_array_equal(rgb, base["rgb"])
