@@ -79,6 +79,7 @@ struct EnvInfo {
     int W, H, ntx, T;              // image and tile grid
     int pad;
     long long g_link0;             // global index of the env's first link Gaussian (slot bg_slots)
+    float lim[4];                  // camera guard band: 1.3 cx/fx, 1.3 (W-cx)/fx, 1.3 cy/fy, 1.3 (H-cy)/fy
 };
 
 // A projection block: up to 256 consecutive Gaussians (thread t takes global

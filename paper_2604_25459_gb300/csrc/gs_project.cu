@@ -385,19 +385,23 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                 const float fx = __ldg(&cam->fx), fy = __ldg(&cam->fy);
                 const float cx = __ldg(&cam->cx), cy = __ldg(&cam->cy);
                 const int W = __ldg(&cam->width), H = __ldg(&cam->height);
-                const float limxn = 1.3f * cx / fx, limxp = 1.3f * ((float)W - cx) / fx;
-                const float limyn = 1.3f * cy / fy, limyp = 1.3f * ((float)H - cy) / fy;
+                const float limxn = __ldg(&E->lim[0]), limxp = __ldg(&E->lim[1]);  // per env, from the tables
+                const float limyn = __ldg(&E->lim[2]), limyp = __ldg(&E->lim[3]);
                 const float iz = 1.0f / mz;
                 const float u = fx * mx * iz + cx;
                 const float v = fy * my * iz + cy;
                 // Conservative cull: the support half extent is at most
                 // sqrt(q* (|J_row|^2 tr(Sigma) + 0.3)) with |J_row|^2 <= (f/z)^2 (1 + lim^2).
+                // The test is on squares: a centre at distance d outside [0.5, W - 0.5]
+                // may reach the image when d <= 1 + 1.001 sqrt(S), i.e. when d <= 1 or
+                // (d - 1)^2 <= 1.002001 S (and likewise in y).
                 const float lx = fmaxf(limxn, limxp), ly = fmaxf(limyn, limyp);
                 const float fz = fx * iz, fzy = fy * iz;
-                const float hxb = sqrtf(qstar * (fz * fz * (1.0f + lx * lx) * trace + 0.3f)) * 1.001f + 1.0f;
-                const float hyb = sqrtf(qstar * (fzy * fzy * (1.0f + ly * ly) * trace + 0.3f)) * 1.001f + 1.0f;
-                const bool maybe = (u + hxb >= 0.5f) && (u - hxb <= (float)W - 0.5f) && (v + hyb >= 0.5f) &&
-                                   (v - hyb <= (float)H - 0.5f);
+                const float sx = qstar * (fz * fz * (1.0f + lx * lx) * trace + 0.3f);
+                const float sy = qstar * (fzy * fzy * (1.0f + ly * ly) * trace + 0.3f);
+                const float ex = fmaxf(fmaxf(0.5f - u, u - ((float)W - 0.5f)), 1.0f) - 1.0f;
+                const float ey = fmaxf(fmaxf(0.5f - v, v - ((float)H - 0.5f)), 1.0f) - 1.0f;
+                const bool maybe = ex * ex <= 1.002001f * sx && ey * ey <= 1.002001f * sy;
                 if (maybe) {
                     // Sigma_2 = M M^T + 0.3 I; det = K + 0.3 (A + C) + 0.09 is a sum of
                     // non-negative terms.  The conic enters the compositor as its

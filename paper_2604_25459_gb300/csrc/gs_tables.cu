@@ -94,6 +94,12 @@ void build_wave_tables(const DevGaussians& D, const int64_t* link_offsets, const
         ei.T = ntx * nty;
         ei.pad = 0;
         ei.g_link0 = D.n_bg + (link_offsets ? link_offsets[sp.link_begin] : 0);
+        // guard-band limits of the EWA Jacobian (IEEE float division, as on the device)
+        const gs_camera& c = *sp.cam;
+        ei.lim[0] = 1.3f * c.cx / c.fx;
+        ei.lim[1] = 1.3f * ((float)W - c.cx) / c.fx;
+        ei.lim[2] = 1.3f * c.cy / c.fy;
+        ei.lim[3] = 1.3f * ((float)H - c.cy) / c.fy;
         rec += ei.n_local;
         mask += (ei.n_local + 31) / 32;
         tiles += (unsigned)ei.T;
