@@ -40,8 +40,8 @@ UNIT = "env-frames/s"
 # dram__bytes_write.sum over a 32-env launch, divided by 32), valid only for
 # the compositor sources it was taken on.
 COMPOSITE_TRAFFIC_PER_ENV = (1.165535e9 + 0.593543e9) / 32
-COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu", "paper_2604_25459_gb300/csrc/gs_internal.cuh")
-COMPOSITE_TRAFFIC_SHA = "7588bec7e93458de"
+COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu",)
+COMPOSITE_TRAFFIC_SHA = "4629e3c9448ca308"
 
 
 def _sources_sha(paths) -> str:
