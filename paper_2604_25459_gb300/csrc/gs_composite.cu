@@ -350,6 +350,8 @@ __device__ __forceinline__ bool reaches_rect(const float4& A, const float4& B, f
 // per warp and splat before one atomic add.
 // MODE 1: LiDAR scan (records of k_project_lidar; each "pixel" is a ray of
 // the (azimuth, beam) grid, the Gaussian evaluated at its closest approach).
+// MODE 2: the camera form that also counts composited (pixel, splat) pairs
+// into P.neval (MODE 0 leaves the count out of its blend loop).
 template <int TW, int TH, bool SC = false, int MODE = 0>
 __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 256 ? 8 : 12))) k_composite(CompParams P) {
     constexpr int NT = TW * TH / 2;
@@ -359,6 +361,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     constexpr int UB = (CAP * 8 > NB * 64) ? CAP * 8 : NB * 64;
     constexpr int CB = (18 * NT * 2 > kSortBins * 4) ? 18 * NT * 2 : kSortBins * 4;  // >= selection histogram
     constexpr int NW = NT / 32;
+    constexpr bool CNT = MODE != 0 || SC;  // count composited pairs
     static_assert(CAP * 8 + UB >= kBins * 4, "bin counters alias the key and staging buffers");
     static_assert(kBins % NT == 0, "bins per thread");
     __shared__ __align__(16) unsigned char kbuf[CAP * 8 + UB];  // window keys | sort scratch, staged records
@@ -525,7 +528,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         ov = R.x <= wx1 && R.x + R.y >= wx0 && R.z <= wy1 && R.z + R.w >= wy0;
                         // large splats: their box overstates the ellipse most (a box
                         // under 24 px in width + height is kept as it is)
-                        if (MODE == 0 && ov && R.y + R.w >= 24)
+                        if (MODE != 1 && ov && R.y + R.w >= 24)
                             ov = reaches_rect(sA[j], sB[j], (float)wx0 + 0.5f, (float)wy0 + 0.5f);
                     }
                     uint32_t m = __ballot_sync(0xffffffffu, ov);
@@ -539,14 +542,22 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         const int k2 = two ? __ffs(m) - 1 : k1;
                         if (two) m &= m - 1u;
                         const int j1 = c + k1, j2 = c + k2;
-                        const int4 R1 = sR[j1];
-                        const int4 R2 = sR[j2];
-                        const bool x1 = (unsigned)(px - R1.x) <= (unsigned)R1.y;
-                        const bool x2 = two && (unsigned)(px - R2.x) <= (unsigned)R2.y;
-                        const bool h10 = !done0 && x1 && (unsigned)(py0 - R1.z) <= (unsigned)R1.w;
-                        const bool h11 = !done1 && x1 && (unsigned)(py1 - R1.z) <= (unsigned)R1.w;
-                        const bool h20 = !done0 && x2 && (unsigned)(py0 - R2.z) <= (unsigned)R2.w;
-                        const bool h21 = !done1 && x2 && (unsigned)(py1 - R2.z) <= (unsigned)R2.w;
+                        // Camera pixels skip the per-pixel box test: a pixel outside a
+                        // splat's support box has q > q* (1 + 2e-4), so its alpha falls
+                        // below 1/255 and the alpha test alone rejects it.  LiDAR rays
+                        // keep the test (their grid box is a looser cone bound and a ray
+                        // evaluation costs more).
+                        bool h10 = !done0, h11 = !done1, h20 = two && !done0, h21 = two && !done1;
+                        if constexpr (MODE == 1) {
+                            const int4 R1 = sR[j1];
+                            const int4 R2 = sR[j2];
+                            const bool x1 = (unsigned)(px - R1.x) <= (unsigned)R1.y;
+                            const bool x2 = (unsigned)(px - R2.x) <= (unsigned)R2.y;
+                            h10 = h10 && x1 && (unsigned)(py0 - R1.z) <= (unsigned)R1.w;
+                            h11 = h11 && x1 && (unsigned)(py1 - R1.z) <= (unsigned)R1.w;
+                            h20 = h20 && x2 && (unsigned)(py0 - R2.z) <= (unsigned)R2.w;
+                            h21 = h21 && x2 && (unsigned)(py1 - R2.z) <= (unsigned)R2.w;
+                        }
                         if (MODE == 1 && (h10 || h11 || h20 || h21)) {
                             const float4 A1 = sA[j1], B1 = sB[j1], C1 = sC[j1], D1 = sD[MODE == 1 ? j1 : 0];
                             const float4 A2 = sA[j2], B2 = sB[j2], C2 = sC[j2], D2 = sD[MODE == 1 ? j2 : 0];
@@ -557,22 +568,22 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             ray_eval(A2, B2, C2, D2, dir1, a21, t21);
                             const float4 none = make_float4(0.f, 0.f, 0.f, 0.f);
                             if (h10 && a10 >= (1.0f / 255.0f)) {
-                                ++ncomp;
+                                if constexpr (CNT) ++ncomp;
                                 blend(a10, none, t10, T0, r0, g0, b0, d0, done0);
                             }
                             if (h11 && a11 >= (1.0f / 255.0f)) {
-                                ++ncomp;
+                                if constexpr (CNT) ++ncomp;
                                 blend(a11, none, t11, T1, r1, g1, b1, d1, done1);
                             }
                             if (h20 && !done0 && a20 >= (1.0f / 255.0f)) {
-                                ++ncomp;
+                                if constexpr (CNT) ++ncomp;
                                 blend(a20, none, t20, T0, r0, g0, b0, d0, done0);
                             }
                             if (h21 && !done1 && a21 >= (1.0f / 255.0f)) {
-                                ++ncomp;
+                                if constexpr (CNT) ++ncomp;
                                 blend(a21, none, t21, T1, r1, g1, b1, d1, done1);
                             }
-                        } else if (MODE == 0 && (h10 || h11 || h20 || h21)) {
+                        } else if (MODE != 1 && (h10 || h11 || h20 || h21)) {
                             const float4 A1 = sA[j1], B1 = sB[j1];
                             const float4 A2 = sA[j2], B2 = sB[j2];
                             const float dx1 = fpx - A1.x, dx2 = fpx - A2.x;
@@ -586,11 +597,11 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             if (u10 || u11) {
                                 const float4 C1 = sC[j1];
                                 if (u10) {
-                                    ++ncomp;
+                                    if constexpr (CNT) ++ncomp;
                                     w1 += blend(a10, C1, A1.w, T0, r0, g0, b0, d0, done0);
                                 }
                                 if (u11) {
-                                    ++ncomp;
+                                    if constexpr (CNT) ++ncomp;
                                     w1 += blend(a11, C1, A1.w, T1, r1, g1, b1, d1, done1);
                                 }
                             }
@@ -599,11 +610,11 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             if (u20 || u21) {
                                 const float4 C2 = sC[j2];
                                 if (u20) {
-                                    ++ncomp;
+                                    if constexpr (CNT) ++ncomp;
                                     w2 += blend(a20, C2, A2.w, T0, r0, g0, b0, d0, done0);
                                 }
                                 if (u21) {
-                                    ++ncomp;
+                                    if constexpr (CNT) ++ncomp;
                                     w2 += blend(a21, C2, A2.w, T1, r1, g1, b1, d1, done1);
                                 }
                             }
@@ -864,7 +875,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         before += wn;
     }
 
-    if (P.neval) {
+    if (CNT && P.neval) {
         uint32_t c = ncomp;
         for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
         if (lane == 0 && c) atomicAdd(P.neval, (unsigned long long)c);
@@ -978,6 +989,13 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
     if (P.score) {  // the contribution pass runs on 16x16 tiles only
         if (P.tile_w != 16 || P.tile_h != 16) return cudaErrorInvalidValue;
         return launch_tiles<16, 16, true>(P, st, ctas);
+    }
+    if (P.neval) {  // counting pass
+        if (P.tile_w == 16 && P.tile_h == 16) return launch_tiles<16, 16, false, 2>(P, st, ctas);
+        if (P.tile_w == 32 && P.tile_h == 16) return launch_tiles<32, 16, false, 2>(P, st, ctas);
+        if (P.tile_w == 8 && P.tile_h == 8) return launch_tiles<8, 8, false, 2>(P, st, ctas);
+        if (P.tile_w == 16 && P.tile_h == 8) return launch_tiles<16, 8, false, 2>(P, st, ctas);
+        return launch_tiles<32, 8, false, 2>(P, st, ctas);
     }
     if (P.tile_w == 16 && P.tile_h == 16) return launch_tiles<16, 16>(P, st, ctas);
     if (P.tile_w == 32 && P.tile_h == 16) return launch_tiles<32, 16>(P, st, ctas);
