@@ -20,7 +20,8 @@ along the ray in ray space instead of through a 2D projection:
   b = G mu its minimum is at t* = a.b / |a|^2 and equals |a x b|^2 / |a|^2;
 * alpha = min(0.99, o exp(-q_min / 2)); Gaussians with alpha < 1/255 or
   t* <= the near range are skipped; order: distance |mu| ascending, ties by
-  global index; T' = T (1 - alpha), stop before adding when T' < 1e-4;
+  global index (or a given rank); T' = T (1 - alpha), stop before adding
+  when T' < 1e-4;
 * outputs: hit = 1 - T and range = sum(alpha T t*) / (1 - T) (0 where
   1 - T = 0).
 
@@ -59,12 +60,13 @@ def ray_directions(rows: int, cols: int, elev_min: float, elev_max: float) -> np
     return np.stack([ct * np.cos(phi)[None, :], ct * np.sin(phi)[None, :], np.broadcast_to(st, (rows, cols))], -1)
 
 
-def render_lidar(mean, quat, log_scale, opacity, link_of, link_poses, sensor) -> dict:
+def render_lidar(mean, quat, log_scale, opacity, link_of, link_poses, sensor, rank=None) -> dict:
     """One env.  mean/quat/log_scale/opacity: the scene's Gaussians (background
     then link-major); link_of [n]: -1 for background, else the link index whose
     pose (link_poses [L][7], link -> world) moves it; sensor: dict with q_ws,
-    t_ws (world -> sensor), rows, cols, elev_min, elev_max, near.  Returns
-    range [rows, cols], hit [rows, cols]."""
+    t_ws (world -> sensor), rows, cols, elev_min, elev_max, near; rank [n]
+    (optional): the order among Gaussians at equal distance (default: global
+    index).  Returns range [rows, cols], hit [rows, cols]."""
     mean = np.asarray(mean, np.float64)
     Rg = quat_to_mat(quat)
     s = np.asarray(log_scale, np.float64)
@@ -87,7 +89,8 @@ def render_lidar(mean, quat, log_scale, opacity, link_of, link_poses, sensor) ->
     G = np.exp(-s)[:, :, None] * np.transpose(Rsg, (0, 2, 1))  # rows e^-s_k (R column k)
     b = np.einsum("nij,nj->ni", G, mu)
     dist = np.linalg.norm(mu, axis=1)
-    order = np.lexsort((np.arange(len(dist)), dist))
+    tie = np.arange(len(dist)) if rank is None else np.asarray(rank)
+    order = np.lexsort((tie, dist))
     D = ray_directions(sensor["rows"], sensor["cols"], sensor["elev_min"], sensor["elev_max"])
     rows, cols = D.shape[:2]
     rng = np.zeros((rows, cols))

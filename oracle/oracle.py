@@ -79,7 +79,7 @@ def lib():
                 f.argtypes = [C.POINTER(_Scene), C.c_void_p, C.POINTER(_Camera), C.POINTER(_Proj)]
                 f.restype = C.c_int
                 f = getattr(L, f"or_render_{sfx}")
-                f.argtypes = [C.POINTER(_Proj), C.c_int64, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                f.argtypes = [C.POINTER(_Proj), C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                               C.POINTER(_Image)]
                 f.restype = C.c_int
                 f = getattr(L, f"or_sh_basis_{sfx}")
@@ -174,10 +174,12 @@ def project(S: SceneArrays, link_poses_env, cam, precision: str = "f64") -> dict
 
 
 def render_projected(proj: dict, width: int, height: int, mode: str = "plain", precision: str = "f64",
-                     zkey=None, contrib: bool = False) -> dict:
+                     zkey=None, contrib: bool = False, rank=None) -> dict:
     """Composite projected Gaussians; with ``contrib`` also each Gaussian's
     summed blending weight sum_p alpha T over the pixels where it was added
-    (the contribution that ranks Gaussians for pruning)."""
+    (the contribution that ranks Gaussians for pruning).  Gaussians of equal
+    depth composite in global-index order, or in ascending ``rank`` [n] when
+    given (the tie order of a renderer that stores the scene in another order)."""
     img = dict(rgb=np.zeros((height, width, 3), np.float32), depth=np.zeros((height, width), np.float32),
                alpha=np.zeros((height, width), np.float32), amb=np.zeros((height, width), np.uint8),
                neval=np.zeros((height, width), np.int32))
@@ -187,19 +189,22 @@ def render_projected(proj: dict, width: int, height: int, mode: str = "plain", p
     I = _Image(*[_ptr(img[k]) for k in ("rgb", "depth", "alpha", "amb", "neval")],
                _ptr(img["contrib"]) if contrib else None)
     zk = _f32(zkey) if zkey is not None else None
-    rc = getattr(lib(), f"or_render_{precision}")(C.byref(proj["_P"]), n, _ptr(zk), width, height,
+    rk = np.ascontiguousarray(rank, dtype=np.int64) if rank is not None else None
+    if rk is not None and rk.shape != (n,):
+        raise ValueError(f"rank must hold one entry per Gaussian ({n})")
+    rc = getattr(lib(), f"or_render_{precision}")(C.byref(proj["_P"]), n, _ptr(zk), _ptr(rk), width, height,
                                                    1 if mode == "brute" else 0, C.byref(I))
     assert rc == 0
     return img
 
 
 def render_env(w, e: int = 0, mode: str = "plain", precision: str = "f64", sh_degree: int = 3, S=None,
-               zkey=None, contrib: bool = False) -> dict:
+               zkey=None, contrib: bool = False, rank=None) -> dict:
     """Render env ``e`` of workload ``w``: rgb [H,W,3], depth, alpha, amb (ambiguous-pixel mask), neval."""
     S = S or scene_arrays(w, sh_degree)
     cam = w.cams[e]
     proj = project(S, w.link_poses[e], cam, precision)
-    img = render_projected(proj, int(cam["width"]), int(cam["height"]), mode, precision, zkey, contrib)
+    img = render_projected(proj, int(cam["width"]), int(cam["height"]), mode, precision, zkey, contrib, rank)
     img["proj"] = proj
     return img
 

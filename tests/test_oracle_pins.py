@@ -292,6 +292,22 @@ def test_depth_order_ties_by_global_index():
     np.testing.assert_allclose(img["rgb"][12, 15], exp, atol=2e-7)
 
 
+def test_depth_order_ties_by_given_rank():
+    """Equal depth with a tie rank that reverses the indices: the higher
+    global index composites first (the order a renderer's storage imposes)."""
+    ca, cb = [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]
+    w = _front_splats([2.0, 2.0], [0.5, 0.5], [ca, cb])
+    S = oracle.scene_arrays(w)
+    proj = oracle.project(S, w.link_poses[0], w.cams[0])
+    img = oracle.render_projected(proj, 32, 32, rank=np.array([1, 0]))
+    rgb = proj["rgb"]
+    assert img["alpha"][12, 15] == pytest.approx(0.75, abs=1e-6)
+    np.testing.assert_allclose(img["rgb"][12, 15], 0.5 * rgb[1] + 0.25 * rgb[0], atol=2e-7)
+    # a rank that keeps the index order changes nothing
+    same = oracle.render_projected(proj, 32, 32, rank=np.array([5, 9]))
+    np.testing.assert_array_equal(same["rgb"], oracle.render_projected(proj, 32, 32)["rgb"])
+
+
 def test_p4_invariants_c0():
     w = synth.make_c0()
     img = _render(w)
@@ -485,6 +501,34 @@ def test_lidar_occlusion_and_order():
     T = 0.01 * (1 - o2)
     assert abs(out["hit"][3, 17] - (1 - T)) < 1e-12
     assert abs(out["range"][3, 17] - (0.99 * D1 + 0.01 * o2 * D2) / (1 - T)) < 1e-12
+
+
+def test_lidar_equal_distance_order_by_rank():
+    """Two Gaussians at the same distance: one on the ray (t* = D), one off it
+    by the angle th with a wide footprint (t* = D cos th).  They composite in
+    index order, or in the order of a given rank; the range weights follow."""
+    from oracle import lidar
+
+    sen = _sensor()
+    dirs = lidar.ray_directions(8, 32, -0.3, 0.3)
+    d = dirs[3, 17]
+    side = np.cross(d, [0.0, 0.0, 1.0])
+    side /= np.linalg.norm(side)
+    D, th, o1, o2, s1, s2 = 3.0, 0.1, 0.6, 0.3, 0.05, 1.0
+    m2 = D * (math.cos(th) * d + math.sin(th) * side)
+    args = ([D * d, m2], [[1, 0, 0, 0]] * 2, [[np.log(s1)] * 3, [np.log(s2)] * 3], [o1, o2], [-1, -1], None, sen)
+    a1 = o1
+    a2 = o2 * math.exp(-0.5 * (D * math.sin(th)) ** 2 / s2 ** 2)
+    t1, t2 = D, D * math.cos(th)
+    T = (1 - a1) * (1 - a2)
+    for rank, first in ((None, 1), (np.array([1, 0]), 2)):
+        out = lidar.render_lidar(*args, rank=rank)
+        if first == 1:
+            r = (a1 * t1 + (1 - a1) * a2 * t2) / (1 - T)
+        else:
+            r = (a2 * t2 + (1 - a2) * a1 * t1) / (1 - T)
+        assert abs(out["hit"][3, 17] - (1 - T)) < 1e-12
+        assert abs(out["range"][3, 17] - r) < 1e-12
 
 
 def test_lidar_joint_rigid_motion_and_links():
