@@ -97,8 +97,58 @@ size_t elem_size(gs_dtype d) { return d == GS_F32 ? 4 : 2; }
 
 // Copy a view's arrays to the device (if they are host arrays) and run the
 // preparation kernel into D[dst, dst + n).
+// Storage order of a background: the Morton (Z-order) position of each mean
+// in the set's bounding box, 10 bits per axis, equal codes in the caller's
+// order.  The projection runs one thread per Gaussian, so a warp then holds
+// Gaussians that lie close together and mostly agree on which environments
+// see them (in the caller's order a warp mixes a few visible Gaussians with
+// many culled ones in nearly every environment).  Returns order[k] = caller's
+// index of the Gaussian stored at position k.
+std::vector<long long> spatial_order(const float* mean, int64_t n) {
+    float lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = INFINITY;
+        hi[k] = -INFINITY;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const float t = mean[3 * i + k];
+            if (std::isfinite(t)) {
+                lo[k] = std::min(lo[k], t);
+                hi[k] = std::max(hi[k], t);
+            }
+        }
+    auto spread = [](uint32_t x) {  // bit b of x to bit 3b
+        x &= 0x3ffu;
+        x = (x | (x << 16)) & 0x030000ffu;
+        x = (x | (x << 8)) & 0x0300f00fu;
+        x = (x | (x << 4)) & 0x030c30c3u;
+        x = (x | (x << 2)) & 0x09249249u;
+        return x;
+    };
+    std::vector<uint32_t> code((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t c = 0;
+        for (int k = 0; k < 3; ++k) {
+            const float t = mean[3 * i + k];
+            uint32_t q = 0;
+            if (std::isfinite(t) && hi[k] > lo[k]) {
+                const double f = (double)(t - lo[k]) / ((double)hi[k] - (double)lo[k]) * 1023.0;
+                q = (uint32_t)std::min(1023.0, std::max(0.0, f));
+            }
+            c |= spread(q) << k;
+        }
+        code[(size_t)i] = c;
+    }
+    std::vector<long long> order((size_t)n);
+    for (int64_t i = 0; i < n; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](long long a, long long b) { return code[(size_t)a] < code[(size_t)b]; });
+    return order;
+}
+
 gs_status prep_view(gs_scene s, const gs_gaussians* g, int64_t dst, int link_mode, const int64_t* link_offsets_host,
-                    int n_links) {
+                    int n_links, const int64_t* place_host = nullptr) {
     const int64_t n = g->n;
     if (n == 0) return GS_OK;
     const size_t es = elem_size(g->dtype);
@@ -133,9 +183,19 @@ gs_status prep_view(gs_scene s, const gs_gaussians* g, int64_t dst, int link_mod
             offs = static_cast<const int64_t*>(d);
         }
     }
+    const int64_t* place = nullptr;
+    if (e == cudaSuccess && place_host) {
+        void* d = nullptr;
+        e = cudaMalloc(&d, sizeof(int64_t) * (size_t)n);
+        if (e == cudaSuccess) {
+            tmp.push_back(d);
+            e = cudaMemcpy(d, place_host, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice);
+            place = static_cast<const int64_t*>(d);
+        }
+    }
     if (e == cudaSuccess)
-        e = launch_prep(static_cast<const float*>(mean), static_cast<const float*>(quat), ls, op, sh, n, dst, link_mode,
-                        offs, n_links, s->D, s->status, 0);
+        e = launch_prep(static_cast<const float*>(mean), static_cast<const float*>(quat), ls, op, sh, n, dst, place,
+                        link_mode, offs, n_links, s->D, s->status, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     for (void* p : tmp) cudaFree(p);
     if (e != cudaSuccess) return cuda_fail(e, "scene upload");
@@ -145,6 +205,29 @@ gs_status prep_view(gs_scene s, const gs_gaussians* g, int64_t dst, int link_mod
         CK(cudaMemset(s->status, 0, 4), "status clear");
         return fail(GS_ERR_INVALID, "Gaussian set holds a zero or non-finite quaternion or scale");
     }
+    return GS_OK;
+}
+
+// Uploads a background in its storage order (spatial_order) and keeps the order.
+gs_status place_background(gs_scene s, const gs_gaussians* g) {
+    const int64_t n = g->n;
+    s->bg_order.clear();
+    if (n == 0) return GS_OK;
+    std::vector<float> host_mean;
+    const float* mean = g->mean;
+    if (g->on_device) {
+        host_mean.resize((size_t)n * 3);
+        CK(cudaMemcpy(host_mean.data(), g->mean, (size_t)n * 12, cudaMemcpyDeviceToHost), "copy means");
+        mean = host_mean.data();
+    }
+    std::vector<long long> order = spatial_order(mean, n);
+    std::vector<int64_t> place((size_t)n);
+    for (int64_t k = 0; k < n; ++k) place[(size_t)order[(size_t)k]] = k;
+    CK(s->bg_order_dev.ensure(sizeof(long long) * (size_t)n), "alloc storage order");
+    CK(cudaMemcpy(s->bg_order_dev.p, order.data(), sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice),
+       "copy storage order");
+    ST(prep_view(s, g, 0, 0, nullptr, 0, place.data()));
+    s->bg_order.swap(order);
     return GS_OK;
 }
 
@@ -519,6 +602,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.appear = io.appear;
         C.score = io.score;
         C.nbp = (unsigned)bg_slots(s->D.n_bg);
+        C.bg_order = s->bg_order.empty() ? nullptr : s->bg_order_dev.as<long long>();
         C.lidars = io.lidars;
         C.r3 = P.r3;
         C.status = status;
@@ -908,7 +992,7 @@ gs_status gs_scene_create(const gs_gaussians* background, gs_scene* out) {
         s->D.p2 = s->g2.as<float4>();
         s->D.p3 = s->g3.as<float4>();
         s->D.sh = s->gsh.p;
-        r = prep_view(s, background, 0, 0, nullptr, 0);
+        r = place_background(s, background);
     }
     if (r != GS_OK) {
         std::string msg = g_err;
@@ -1477,7 +1561,7 @@ gs_status gs_debug_copy_records(gs_scene s, int env, uint8_t* visible, float* u,
     if (visible) memset(visible, 0, (size_t)s->D.n);
     for (int64_t j = 0; j < n_local; ++j) {
         if (j >= s->D.n_bg && j < nbp) continue;  // padding slots
-        const int64_t g = j < s->D.n_bg ? j : lg0 + (j - nbp);
+        const int64_t g = j < s->D.n_bg ? s->bg_order[(size_t)j] : lg0 + (j - nbp);
         const bool vis = (mask[j >> 5] >> (j & 31)) & 1u;
         if (visible) visible[g] = vis ? 1 : 0;
         if (!vis) continue;
@@ -1543,8 +1627,18 @@ gs_status gs_debug_copy_tiles(gs_scene s, int env, uint32_t* counts, int64_t n_c
     const int64_t nbp = bg_slots(s->D.n_bg), lg0 = s->D.n_bg + s->link_offsets[E.link_begin];
     for (unsigned long long i = 0; i < total; ++i) {
         const int64_t j = (int64_t)(keys[i] & 0xffffffffull);
-        lists[i] = (uint32_t)(j < s->D.n_bg ? j : lg0 + (j - nbp));
+        lists[i] = (uint32_t)(j < s->D.n_bg ? s->bg_order[(size_t)j] : lg0 + (j - nbp));
     }
+    return GS_OK;
+}
+
+gs_status gs_scene_get_order(gs_scene s, int64_t* order, int64_t n) {
+    if (!s) return fail(GS_ERR_INVALID, "null scene");
+    const int64_t nb = s->D.n_bg;
+    if (nb == 0) return GS_OK;
+    if (!order) return fail(GS_ERR_INVALID, "null order");
+    if (n < nb) return fail(GS_ERR_INVALID, "order holds %lld < %lld entries", (long long)n, (long long)nb);
+    for (int64_t k = 0; k < nb; ++k) order[k] = (int64_t)s->bg_order[(size_t)k];
     return GS_OK;
 }
 
@@ -1554,7 +1648,7 @@ void gs_scene_destroy(gs_scene s) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&s->g0, &s->g1, &s->g2, &s->g3, &s->gsh, &s->stage_rgb[0], &s->stage_rgb[1],
                       &s->stage_depth[0], &s->stage_depth[1], &s->stage_alpha[0], &s->stage_alpha[1], &s->poses,
-                      &s->neval, &s->appear, &s->lidar_tab};
+                      &s->neval, &s->appear, &s->lidar_tab, &s->bg_order_dev};
     for (DevBuf* b : bufs) b->release();
     s->sc.release();
     for (auto& m : s->marks) {

@@ -467,7 +467,8 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     // contribution pass: record slot -> global Gaussian index
     const long long g_link0 = SC ? __ldg(&Ep->g_link0) : 0ll;
     auto score_index = [&](uint32_t j) -> long long {
-        return j < P.nbp ? (long long)j : g_link0 + (long long)(j - P.nbp);
+        if (j < P.nbp) return P.bg_order ? P.bg_order[j] : (long long)j;
+        return g_link0 + (long long)(j - P.nbp);
     };
     bool finished = false;
 

@@ -160,16 +160,19 @@ struct CompParams {
     uint16_t* depth16;    // nullable: observation depth, IEEE half bits, at pix_base
     const gs_appearance* appear;  // nullable: per env (wave-local index) for rgb8
     float* score;         // nullable: contribution pass (no images): score[g] += sum of alpha T
-    unsigned int nbp;     // background slots (slot j < nbp is background Gaussian j)
+    unsigned int nbp;     // background slots (slot j < nbp is the background Gaussian stored at j)
+    const long long* bg_order;  // contribution pass: caller's index of the background Gaussian stored at j
     const gs_lidar* lidars;  // nullable: LiDAR scan (range in depth, hit in alpha), per env of the wave
     const uint4* r3;         // LiDAR scan: records' fourth word (|g2|)
     uint32_t* status;
 };
 
 // Launchers (return cudaGetLastError()).
+// Input Gaussian i is stored at dst_offset + (place ? place[i] : i).
 cudaError_t launch_prep(const float* mean, const float* quat, const void* log_scale, const void* opacity,
-                        const void* sh, int64_t n, int64_t dst_offset, int link_of_first, const int64_t* link_offsets,
-                        int n_links, const DevGaussians& D, uint32_t* status, cudaStream_t st);
+                        const void* sh, int64_t n, int64_t dst_offset, const int64_t* place, int link_mode,
+                        const int64_t* link_offsets, int n_links, const DevGaussians& D, uint32_t* status,
+                        cudaStream_t st);
 // n_items = sum over envs of (1 + n_links); envs[We].xf_base must hold n_items.
 cudaError_t launch_link_table(const float* poses, const gs_camera* cams, const EnvInfo* envs, int We, int n_items,
                               LinkXf* out, uint32_t* status, cudaStream_t st);

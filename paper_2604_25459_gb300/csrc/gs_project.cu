@@ -51,6 +51,7 @@ struct PrepArgs {
     const void* sh;
     int64_t n;
     int64_t dst;          // first destination index
+    const int64_t* place;  // nullable: input i goes to dst + place[i] (the scene's storage order)
     int link_mode;        // 0: background (link 0), 1: binary search in link_offsets
     const int64_t* link_offsets;
     int n_links;
@@ -69,7 +70,7 @@ template <int DT>
 __global__ void k_prep(PrepArgs A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    const int64_t g = A.dst + i;
+    const int64_t g = A.dst + (A.place ? A.place[i] : i);
     float R[9];
     bool ok = quat_rot<float>(A.quat[4 * i], A.quat[4 * i + 1], A.quat[4 * i + 2], A.quat[4 * i + 3], R);
     float sc[3];
@@ -118,10 +119,11 @@ __global__ void k_prep(PrepArgs A) {
 }
 
 cudaError_t launch_prep(const float* mean, const float* quat, const void* log_scale, const void* opacity,
-                        const void* sh, int64_t n, int64_t dst_offset, int link_mode, const int64_t* link_offsets,
-                        int n_links, const DevGaussians& D, uint32_t* status, cudaStream_t st) {
+                        const void* sh, int64_t n, int64_t dst_offset, const int64_t* place, int link_mode,
+                        const int64_t* link_offsets, int n_links, const DevGaussians& D, uint32_t* status,
+                        cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    PrepArgs A{mean, quat, log_scale, opacity, sh, n, dst_offset, link_mode, link_offsets, n_links, D.n,
+    PrepArgs A{mean, quat, log_scale, opacity, sh, n, dst_offset, place, link_mode, link_offsets, n_links, D.n,
                D.p0, D.p1, D.p2, D.p3, D.sh, sh_values(D.sh_degree), D.sh_planes, status};
     dim3 grid((unsigned)((n + 255) / 256));
     switch (D.dtype) {

@@ -112,6 +112,7 @@ _SIGS = {
     "gs_scene_get_timings": (C.c_int, [C.c_void_p, C.POINTER(GsTimings), C.c_int]),
     "gs_debug_copy_records": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 10),
     "gs_debug_copy_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
+    "gs_scene_get_order": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "gs_scene_destroy": (None, [C.c_void_p]),
     "gs_server_create": (C.c_int, [C.POINTER(GsServerConfig), C.POINTER(C.c_void_p)]),
     "gs_server_add_scene": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
@@ -204,6 +205,7 @@ class Scene:
         self.sh_degree = sh_degree
         v, keep = self._make_view(background, dtype, sh_degree, stored)
         _check(lib().gs_scene_create(C.byref(v), C.byref(self._h)))
+        self.n_background = int(v.n)
         self.n_links = 0
         self._alive = True
 
@@ -387,6 +389,21 @@ class Scene:
 
     def plan(self, envs: np.ndarray, autotune: bool = True, graph: bool = True) -> "Plan":
         return Plan(self, envs, (PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0))
+
+    def storage_order(self) -> np.ndarray:
+        """order[k] = the caller's index of the background Gaussian stored at
+        position k (the scene's Morton order; equal depths composite in it)."""
+        order = np.zeros(max(self.n_background, 1), np.int64)
+        _check(lib().gs_scene_get_order(self._h, _ptr(order), len(order)))
+        return order[:self.n_background]
+
+    def tie_rank(self, n_links_total: int = 0) -> np.ndarray:
+        """Per Gaussian in the caller's global order (background, then link
+        Gaussians), its position in the order that breaks depth ties."""
+        nb = self.n_background
+        rank = np.arange(nb + n_links_total, dtype=np.int64)
+        rank[self.storage_order()] = np.arange(nb, dtype=np.int64)
+        return rank
 
     def debug_records(self, env: int, n: int) -> dict:
         out = dict(visible=np.zeros(n, np.uint8), u=np.zeros(n, np.float32), v=np.zeros(n, np.float32),

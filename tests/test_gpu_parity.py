@@ -30,7 +30,8 @@ def _keyed_check(w, e, out, sh_degree=3):
     zk = keyed_zkey(proj, rec)
     W, H = int(w.cams[e]["width"]), int(w.cams[e]["height"])
     ind = oracle.render_projected(proj, W, H)
-    key = oracle.render_projected(proj, W, H, zkey=zk)
+    # keyed: the GPU's depth keys and its tie order (the scene's storage order)
+    key = oracle.render_projected(proj, W, H, zkey=zk, rank=scene.tie_rank(w.links.n))
     st_i = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], ind)
     st_k = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], key, amb_bits=AMB_ALPHA | AMB_T)
     return st_i, st_k, rec, proj
@@ -79,14 +80,16 @@ def test_binning_keyed_bit_exact(tile):
     scene = out["scene"]
     W, H = 160, 120
     ntiles = (-(-W // tile[0])) * (-(-H // tile[1]))
+    rank = scene.tie_rank(w.links.n)
     for e in range(w.n_envs):
         rec = scene.debug_records(e, w.background.n + w.links.n)
         vis = np.nonzero(rec["visible"])[0]
         counts, lists = scene.debug_tiles(e, ntiles)
+        # the oracle orders equal depths by the index it is given: the GPU's tie rank
         oc, ol = oracle.bin_records(rec["u"][vis], rec["v"][vis], rec["hx"][vis], rec["hy"][vis],
-                                    rec["z"][vis].view(np.uint32), vis.astype(np.uint32), W, H, *tile)
+                                    rec["z"][vis].view(np.uint32), rank[vis].astype(np.uint32), W, H, *tile)
         np.testing.assert_array_equal(counts.astype(np.int64), oc)
-        np.testing.assert_array_equal(lists, ol)
+        np.testing.assert_array_equal(rank[lists.astype(np.int64)], ol.astype(np.int64))
         assert counts.max() > 2048  # the windowed depth selection was exercised
     scene.close()
 
@@ -237,3 +240,55 @@ def test_scene_with_zero_quaternion_rejected():
     with pytest.raises(gsbatch.GsError) as ei:
         gsbatch.Scene(bad)
     assert ei.value.status == gsbatch.GS_ERR_INVALID
+
+
+def test_background_storage_order():
+    """The scene stores its background in Morton order of the means (a layout
+    choice of the library): the order is a permutation whose codes do not
+    decrease, and a caller-side shuffle of the background changes neither the
+    images (up to pixels where two splats of exactly equal depth swap) nor the
+    per-Gaussian contribution scores, which stay in the caller's order."""
+    import torch
+
+    w = synth.make_c1(n_envs=2, width=160, height=120, f=125.0, n_bg=60_000, per_link=2000)
+    scene = gsbatch.scene_from_workload(w)
+    order = scene.storage_order()
+    nb = w.background.n
+    assert sorted(order.tolist()) == list(range(nb))
+    m = w.background.mean.astype(np.float32)
+    lo, hi = m.min(0), m.max(0)
+    t = (m - lo).astype(np.float64) / (hi.astype(np.float64) - lo.astype(np.float64)) * 1023.0
+    q = np.clip(t, 0.0, 1023.0).astype(np.int64)
+    code = np.zeros(nb, np.int64)
+    for b in range(10):
+        for k in range(3):
+            code |= ((q[:, k] >> b) & 1) << (3 * b + k)
+    assert np.all(np.diff(code[order]) >= 0)
+    poses = torch.from_numpy(w.link_poses).cuda()
+    rgb, depth, _ = scene.render(poses, w.cams)
+    sc = scene.contribution(poses, w.cams)
+    torch.cuda.synchronize()
+    scene.sync_status()
+    rgb, depth, sc = rgb.cpu().numpy(), depth.cpu().numpy(), sc.cpu().numpy()
+    scene.close()
+
+    perm = np.random.default_rng(5).permutation(nb)
+    bg = w.background
+    shuffled = synth.Gaussians(*[np.ascontiguousarray(getattr(bg, f)[perm])
+                                 for f in ("mean", "quat", "log_scale", "opacity", "sh")])
+    w2 = synth.Workload(w.name, shuffled, w.link_offsets, w.links, w.link_poses, w.cams)
+    scene2 = gsbatch.scene_from_workload(w2)
+    rgb2, depth2, _ = scene2.render(poses, w.cams)
+    sc2 = scene2.contribution(poses, w.cams)
+    torch.cuda.synchronize()
+    scene2.sync_status()
+    rgb2, depth2, sc2 = rgb2.cpu().numpy(), depth2.cpu().numpy(), sc2.cpu().numpy()
+    scene2.close()
+    same = np.all(rgb == rgb2, axis=-1) & (depth == depth2)
+    print("pixels bit-identical after a caller-side shuffle:", same.mean())
+    assert same.mean() >= 0.999
+    back = np.empty(nb, sc2.dtype)
+    back[perm] = sc2[:nb]
+    # (equal scores up to the order of the float atomic adds)
+    np.testing.assert_allclose(back, sc[:nb], rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(sc2[nb:], sc[nb:], rtol=1e-4, atol=1e-5)
