@@ -91,7 +91,7 @@ struct ProjBlock {
     int n;
     int e0, e1;
     int lb;
-    int pad;
+    int frame0;  // 1: every Gaussian of the block is background (link frame 0)
 };
 
 struct ProjParams {

@@ -345,6 +345,8 @@ __device__ __forceinline__ bool pixel_range(float c, float h, int n, int& lo, in
     return true;
 }
 
+constexpr int kProjStageEnvs = 256;  // envs per shared-memory chunk of a background block
+
 template <int D, int DT>
 __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
     constexpr int NV = 3 * (D + 1) * (D + 1);
@@ -366,18 +368,44 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
     const float qstar = a3.y;
     const bool live = act && qstar >= 0.0f;
     const float trace = a3.z;  // trace(Sigma) >= its largest eigenvalue (rotation-invariant)
-    for (int el = blk.e0; el < blk.e1; ++el) {
+    // Background blocks (one link frame for every thread) stage, per env of a
+    // chunk, what the depth test needs (the frame's z row, the near plane) and
+    // the env's visibility-word base in shared memory, so that the many culled
+    // (env, Gaussian) pairs wait on one shared load instead of a chain of two
+    // table loads.
+    __shared__ float4 s_r2[kProjStageEnvs];
+    __shared__ float s_near[kProjStageEnvs];
+    __shared__ unsigned long long s_mb[kProjStageEnvs];
+    const bool staged = blk.frame0 != 0;
+    for (int c0 = blk.e0; c0 < blk.e1; c0 += kProjStageEnvs) {
+    const int c1 = min(c0 + kProjStageEnvs, blk.e1);
+    if (staged) {  // block-uniform
+        __syncthreads();  // the previous chunk's entries are no longer read
+        for (int i = t; i < c1 - c0; i += blockDim.x) {
+            const EnvInfo* Ei = P.envs + c0 + i;
+            s_r2[i] = __ldg(&P.xf[__ldg(&Ei->xf_base)].r2);
+            s_near[i] = __ldg(&P.cams[c0 + i].near_plane);
+            s_mb[i] = __ldg(&Ei->mask_base);
+        }
+        __syncthreads();
+    }
+    for (int el = c0; el < c1; ++el) {
         bool vis = false;
         const EnvInfo* E = P.envs + el;
-        const int xfb = __ldg(&E->xf_base);
         if (live) {
-            const LinkXf* Xp = P.xf + xfb + li;
+            const LinkXf* Xp = P.xf + __ldg(&E->xf_base) + li;
             // depth first: most (env, Gaussian) pairs stop at the near-plane test,
             // so only the z row of the transform and the near plane are loaded here
             LinkXf X;
-            X.r2 = __ldg(&Xp->r2);
             const gs_camera* cam = P.cams + el;
-            const float near = __ldg(&cam->near_plane);
+            float near;
+            if (staged) {
+                X.r2 = s_r2[el - c0];
+                near = s_near[el - c0];
+            } else {
+                X.r2 = __ldg(&Xp->r2);
+                near = __ldg(&cam->near_plane);
+            }
             const float mz = X.r2.x * a0.x + X.r2.y * a0.y + X.r2.z * a0.z + X.r2.w;
             if (mz > near) {
                 X.r0 = __ldg(&Xp->r0);
@@ -456,10 +484,12 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
         }
         const uint32_t m = __ballot_sync(0xffffffffu, vis);
         if (lane == 0 && warp_live) {
-            P.mask[(size_t)__ldg(&E->mask_base) + (local >> 5)] = m;
+            const unsigned long long mb = staged ? s_mb[el - c0] : __ldg(&E->mask_base);
+            P.mask[(size_t)mb + (local >> 5)] = m;
             if (P.nvis && m) atomicAdd(P.nvis, (unsigned long long)__popc(m));
         }
     }
+    }  // env chunks
 }
 
 template <int D>

@@ -30,7 +30,7 @@ void walk_blocks(const DevGaussians& D, const int64_t* link_offsets, const EnvSp
             const int e1 = e0 + eg < n ? e0 + eg : n;
             for (int64_t c = 0; c < chunks; ++c) {
                 const int64_t rem = D.n_bg - c * 256;
-                emit(ProjBlock{c * 256, (unsigned)(c * 256), (int)(rem < 256 ? rem : 256), e0, e1, 0, 0});
+                emit(ProjBlock{c * 256, (unsigned)(c * 256), (int)(rem < 256 ? rem : 256), e0, e1, 0, 1});
             }
         }
     }
