@@ -446,9 +446,11 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                         cA = A + 0.3f;
                         cC = C + 0.3f;
                         const float det = K + 0.3f * (A + C) + 0.09f;
-                        const float rc = 1.0f / sqrtf(cC);
-                        l00 = kS * sqrtf(cC / det);
-                        l01 = -kS * B * rc / sqrtf(det);
+                        // reciprocal square roots (MUFU, <= 2 ulp): the support box below
+                        // keeps its IEEE square roots and a 1e-4 margin over this ellipse
+                        const float rc = rsqrtf(cC), rd = rsqrtf(det);
+                        l00 = kS * (cC * rc) * rd;
+                        l01 = -kS * B * rc * rd;
                         l11 = kS * rc;
                     } else {
                         conic_factor_fp64(X, a0, a1, a2, a3, fx, fy, limxn, limxp, limyn, limyp, l00, l01, l11, cA,
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                         // streamed into the colour sums
                         const float4 O = __ldg(&Xp->o);
                         float dx = a0.x - O.x, dy = a0.y - O.y, dz = a0.z - O.z;
-                        const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+                        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
                         dx *= inv;
                         dy *= inv;
                         dz *= inv;
