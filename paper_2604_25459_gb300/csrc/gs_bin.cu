@@ -8,7 +8,7 @@
 // a shared-memory histogram per (env, block of Gaussians), so global atomics
 // are one per touched tile per block rather than one per intersection.  The
 // order inside a bucket is arbitrary; the compositor orders each bucket by the
-// unique key (depth bits << 32 | global index).
+// unique key (depth bits << 32 | record slot, i.e. storage position).
 #include "gs_internal.cuh"
 
 namespace gsb {

@@ -1,7 +1,8 @@
 // Internal declarations shared by the CUDA translation units of libgsbatch.
 //
 // Device data layout (all in HBM):
-//   Gaussians (scene-owned), background first then link-major (global index g):
+//   Gaussians (scene-owned), background first (in the scene's Morton storage
+//   order of the means) then link-major (storage index g):
 //     p0[g] = {mean.x, mean.y, mean.z, opacity}
 //     p1[g] = {F00, F01, F02, F10}      F = R diag(exp(s)), the factor of the 3D
 //     p2[g] = {F11, F12, F20, F21}      covariance F F^T in the frame the mean lives
@@ -13,10 +14,10 @@
 //     of the flattened [coefficient][channel] vector, for every g: sh[p][g].
 //   Per wave of envs (scratch), env el described by EnvInfo envs[el]:
 //     record slots: local index j = g for background Gaussians (padded to a
-//       multiple of 32), then the env's link Gaussians in global order; slot
+//       multiple of 32), then the env's link Gaussians in storage order; slot
 //       (el, j) is at envs[el].rec_base + j in r0..r3, valid where bit j%32 of
-//       mask[envs[el].mask_base + j/32] is set.  Local order = global order, so
-//       the key (depth bits << 32 | j) orders ties by global index.
+//       mask[envs[el].mask_base + j/32] is set.  Local order = storage order,
+//       so the key (depth bits << 32 | j) orders ties by storage position.
 //     xf[envs[el].xf_base + f]  frame f = 0 background, f = 1 + (l - link_begin)
 //     counts/off_local/cursor[envs[el].tile_base + t]  per (env, tile)
 //     env_base[el]              exclusive scan of per-env intersection totals
@@ -78,7 +79,7 @@ struct EnvInfo {
     int link_begin, n_links;       // links of the scene rendered in this env
     int W, H, ntx, T;              // image and tile grid
     int pad;
-    long long g_link0;             // global index of the env's first link Gaussian (slot bg_slots)
+    long long g_link0;             // storage (= caller's) index of the env's first link Gaussian (slot bg_slots)
     float lim[4];                  // camera guard band: 1.3 cx/fx, 1.3 (W-cx)/fx, 1.3 cy/fy, 1.3 (H-cy)/fy
 };
 
