@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--azimuth", type=int, default=1024, help="lidar: azimuth steps per revolution (columns)")
     ap.add_argument("--duration", type=float, default=2.0, help="c4: seconds of arrivals per rate")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="c4: HBM budget of the request loop")
+    ap.add_argument("--scene-budget-gb", type=float, default=0.0,
+                    help="c1: the scene's scratch budget in GiB (0: the library default of 64 GiB)")
     ap.add_argument("--slots", type=int, default=4, help="c4: stream slots (batches in flight)")
     ap.add_argument("--max-batch", type=int, default=512, help="c4: requests per batch")
     return ap.parse_args()
@@ -224,6 +226,8 @@ def run_ours(a, rank, world, local_rank):
     E, H, W = a.envs, a.height, a.width
     scene = gsbatch.scene_from_workload(w, a.dtype)
     scene.set_tile(tw, th)
+    if a.scene_budget_gb > 0:
+        scene.set_budget(int(a.scene_budget_gb * (1 << 30)))
     poses = torch.from_numpy(w.link_poses).to(dev)
     stream = torch.cuda.current_stream()
     if a.obs:  # observation form: per-env exposure, contrast, brightness
