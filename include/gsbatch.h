@@ -15,9 +15,9 @@
  *   pixel (i,j) has its centre at (i+0.5, j+0.5);
  *   near plane per camera, 1.3 frustum guard band, 0.3 px^2 low-pass,
  *   alpha = min(0.99, o exp(-q/2)), alpha floor 1/255, stop when
- *   T (1 - alpha) < 1e-4, depth order ties broken by ascending storage
- *   position (the background in the scene's spatial storage order, see
- *   gs_scene_create, then link Gaussians in link-major order),
+ *   T (1 - alpha) < 1e-4, depth order ties broken by ascending global index
+ *   (background 0..N_b-1 in the caller's order, then link Gaussians in
+ *   link-major order),
  *   black background, rgb clamped to [0,1], depth = sum(alpha T z)/(1-T)
  *   (0 where 1-T = 0), SH colour max(0, sum sh_k Y_k(d) + 0.5) with the view
  *   direction d taken in the link frame for link Gaussians.
@@ -92,10 +92,10 @@ typedef struct {
  * coefficient-plane-major order) and in its own order: the background is
  * stored in Morton (Z-order) order of the means within their bounding box (10
  * bits per axis; equal codes keep the caller's order), so that neighbouring
- * Gaussians, which mostly share their visibility, are projected together.
- * Equal depths composite in that storage order (gs_scene_get_order gives it);
- * every per-Gaussian output (contribution scores, debug copies) is indexed
- * by the caller's order.  Uses the current CUDA device; synchronises that
+ * Gaussians, which mostly share their visibility, are projected together
+ * (gs_scene_get_order gives it).  The order is internal: equal depths still
+ * composite by the caller's global index, and every per-Gaussian output
+ * (contribution scores, debug copies) is indexed by the caller's order.  Uses the current CUDA device; synchronises that
  * device.  Errors: GS_ERR_INVALID (null/negative/ill-formed view, zero
  * quaternion), GS_ERR_OOM, GS_ERR_CUDA. */
 gs_status gs_scene_create(const gs_gaussians* background, gs_scene* out);
@@ -182,7 +182,7 @@ gs_status gs_render_batch_obs_host(gs_scene s, int n_envs, const float* link_pos
  * elev_min + (elev_max - elev_min) (j + 1/2) / rows.  Each ray is composited
  * front to back like a camera pixel (alpha = min(0.99, o exp(-q/2)) >= 1/255,
  * stop when T (1 - alpha) < 1e-4, order by distance of the Gaussian's centre
- * from the sensor, ties by storage position), the Gaussian evaluated at its
+ * from the sensor, ties by global index), the Gaussian evaluated at its
  * closest approach along the ray: with G = diag(e^-s) R^T in the sensor
  * frame, a = G d and b = G mu, q = |a x b|^2 / |a|^2 at t* = a.b / |a|^2;
  * Gaussians with t* <= near_range are skipped.  48 bytes. */
@@ -367,8 +367,7 @@ gs_status gs_debug_copy_records(gs_scene s, int env, uint8_t* visible, float* u,
 
 /* Copy env `env`'s per-tile intersection counts (u32 [tiles], row-major tile
  * grid) and, if lists is non-NULL, the depth-ordered per-tile lists of global
- * indices in the caller's order (u32 [sum counts], tiles in order; equal
- * depths in storage order).  Lists are available only when
+ * indices in the caller's order (u32 [sum counts], tiles in order).  Lists are available only when
  * debug was enabled for that render.  Synchronises. */
 gs_status gs_debug_copy_tiles(gs_scene s, int env, uint32_t* counts, int64_t n_counts, uint32_t* lists,
                               int64_t n_lists);

@@ -222,9 +222,17 @@ gs_status place_background(gs_scene s, const gs_gaussians* g) {
     }
     std::vector<long long> order = spatial_order(mean, n);
     std::vector<int64_t> place((size_t)n);
-    for (int64_t k = 0; k < n; ++k) place[(size_t)order[(size_t)k]] = k;
-    CK(s->bg_order_dev.ensure(sizeof(long long) * (size_t)n), "alloc storage order");
-    CK(cudaMemcpy(s->bg_order_dev.p, order.data(), sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice),
+    std::vector<int> index32((size_t)n), slot32((size_t)n);
+    for (int64_t k = 0; k < n; ++k) {
+        place[(size_t)order[(size_t)k]] = k;
+        index32[(size_t)k] = (int)order[(size_t)k];
+        slot32[(size_t)order[(size_t)k]] = (int)k;
+    }
+    CK(s->bg_index.ensure(sizeof(int) * (size_t)n), "alloc storage order");
+    CK(s->bg_slot.ensure(sizeof(int) * (size_t)n), "alloc storage order");
+    CK(cudaMemcpy(s->bg_index.p, index32.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice),
+       "copy storage order");
+    CK(cudaMemcpy(s->bg_slot.p, slot32.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice),
        "copy storage order");
     ST(prep_view(s, g, 0, 0, nullptr, 0, place.data()));
     s->bg_order.swap(order);
@@ -480,6 +488,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     P.dbg_hxy = debug ? sc.dbg_hxy.as<float2>() : nullptr;
     P.nvis = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() + 1 : nullptr;
     P.lidars = io.lidars;
+    P.bg_index = s->bg_order.empty() ? nullptr : s->bg_index.as<int>();
     PhaseTimer t2(s, st, GS_PHASE_PROJECT, timers);
     if (io.lidars) CK(launch_project_lidar(P, wt.n_blocks, st), "LiDAR projection");
     else CK(launch_project(s->D, P, wt.n_blocks, st), "projection");
@@ -500,6 +509,9 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     B.env_base = sc.env_base.as<unsigned long long>();
     B.cursor = sc.cursor.as<uint32_t>();
     B.status = status;
+    B.index_in_r3 = io.lidars ? 0 : 1;  // LiDAR records keep |g2| in r3.w
+    B.bg_index = s->bg_order.empty() ? nullptr : s->bg_index.as<int>();
+    B.n_bg = (unsigned)s->D.n_bg;
     PhaseTimer t3(s, st, GS_PHASE_COUNT, timers);
     CK(launch_count(B, We, wt.max_words, wt.max_T, st), "count");
     t3.done(1);
@@ -602,7 +614,9 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.appear = io.appear;
         C.score = io.score;
         C.nbp = (unsigned)bg_slots(s->D.n_bg);
-        C.bg_order = s->bg_order.empty() ? nullptr : s->bg_order_dev.as<long long>();
+        C.bg_index = s->bg_order.empty() ? nullptr : s->bg_index.as<int>();
+        C.bg_slot = s->bg_order.empty() ? nullptr : s->bg_slot.as<int>();
+        C.n_bg = (unsigned)s->D.n_bg;
         C.lidars = io.lidars;
         C.r3 = P.r3;
         C.status = status;
@@ -952,7 +966,11 @@ gs_status plan_enqueue(gs_plan p, const std::vector<EnvSpec>& specs, const float
 
 }  // namespace gsb
 
-gsb::SceneView gsb::scene_view(gs_scene s) { return SceneView{s->device, s->D, s->status, s->tile_w, s->tile_h}; }
+gsb::SceneView gsb::scene_view(gs_scene s) {
+    const bool perm = !s->bg_order.empty();
+    return SceneView{s->device, s->D, s->status, s->tile_w, s->tile_h, perm ? s->bg_index.as<int>() : nullptr,
+                     perm ? s->bg_slot.as<int>() : nullptr};
+}
 
 gs_status gsb::report(gs_status st, const char* msg) {
     g_err = msg;
@@ -1627,7 +1645,7 @@ gs_status gs_debug_copy_tiles(gs_scene s, int env, uint32_t* counts, int64_t n_c
     const int64_t nbp = bg_slots(s->D.n_bg), lg0 = s->D.n_bg + s->link_offsets[E.link_begin];
     for (unsigned long long i = 0; i < total; ++i) {
         const int64_t j = (int64_t)(keys[i] & 0xffffffffull);
-        lists[i] = (uint32_t)(j < s->D.n_bg ? s->bg_order[(size_t)j] : lg0 + (j - nbp));
+        lists[i] = (uint32_t)(j < s->D.n_bg ? j : lg0 + (j - nbp));  // keys carry the caller's index
     }
     return GS_OK;
 }
@@ -1648,7 +1666,7 @@ void gs_scene_destroy(gs_scene s) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&s->g0, &s->g1, &s->g2, &s->g3, &s->gsh, &s->stage_rgb[0], &s->stage_rgb[1],
                       &s->stage_depth[0], &s->stage_depth[1], &s->stage_alpha[0], &s->stage_alpha[1], &s->poses,
-                      &s->neval, &s->appear, &s->lidar_tab, &s->bg_order_dev};
+                      &s->neval, &s->appear, &s->lidar_tab, &s->bg_index, &s->bg_slot};
     for (DevBuf* b : bufs) b->release();
     s->sc.release();
     for (auto& m : s->marks) {

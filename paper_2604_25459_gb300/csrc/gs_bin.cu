@@ -8,7 +8,7 @@
 // a shared-memory histogram per (env, block of Gaussians), so global atomics
 // are one per touched tile per block rather than one per intersection.  The
 // order inside a bucket is arbitrary; the compositor orders each bucket by the
-// unique key (depth bits << 32 | record slot, i.e. storage position).
+// unique key (depth bits << 32 | the caller's local index of the Gaussian).
 #include "gs_internal.cuh"
 
 namespace gsb {
@@ -225,7 +225,9 @@ __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
     bool dropped = false;
     for_each_visible(mask, w0, w1, wbuf, [&](int64_t j) {
         const uint4 q = r3[j];
-        const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)(uint32_t)j;
+        const uint32_t i = P.index_in_r3 ? q.w
+                           : ((P.bg_index && j < (int64_t)P.n_bg) ? (uint32_t)__ldg(P.bg_index + j) : (uint32_t)j);
+        const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)i;
         int tx0, tx1, ty0, ty1;
         tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
         const int n = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);

@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     // contribution pass: record slot -> global Gaussian index
     const long long g_link0 = SC ? __ldg(&Ep->g_link0) : 0ll;
     auto score_index = [&](uint32_t j) -> long long {
-        if (j < P.nbp) return P.bg_order ? P.bg_order[j] : (long long)j;
+        if (j < P.nbp) return P.bg_index ? (long long)__ldg(P.bg_index + j) : (long long)j;
         return g_link0 + (long long)(j - P.nbp);
     };
     bool finished = false;
@@ -477,12 +477,19 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     // pixel of the tile has terminated.
     auto run_window = [&](uint32_t wn, uint32_t before) {
         const unsigned long long* sorted = window_sort<NT>(keys, tmp, cnt, red, (int)wn);
-        if (sorted != keys) {  // the sorted window sits in the scratch half: move it home
-            for (uint32_t i = tid; i < wn; i += NT) keys[i] = sorted[i];
+        if (dbg)
+            for (uint32_t i = tid; i < wn; i += NT) P.dbg_sorted[start + before + i] = sorted[i];
+        // Move the sorted window home (from the scratch half) and, where keys
+        // carry the caller's background index, swap in the record slot.
+        if (sorted != keys || P.bg_slot) {
+            for (uint32_t i = tid; i < wn; i += NT) {
+                unsigned long long k = sorted[i];
+                const uint32_t g = (uint32_t)(k & 0xffffffffull);
+                if (P.bg_slot && g < P.n_bg) k = (k & 0xffffffff00000000ull) | (uint32_t)__ldg(P.bg_slot + g);
+                keys[i] = k;
+            }
             __syncthreads();
         }
-        if (dbg)
-            for (uint32_t i = tid; i < wn; i += NT) P.dbg_sorted[start + before + i] = keys[i];
 
         for (uint32_t b = 0; b < wn; b += NB) {
             const int cnt_b = (int)min((uint32_t)NB, wn - b);

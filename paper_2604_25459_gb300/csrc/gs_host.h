@@ -112,10 +112,10 @@ struct gs_scene_s {
     gsb::DevBuf appear;  // appearance parameters copied from the host (observation form)
     gsb::DevBuf lidar_tab;  // the current wave's LiDAR sensors
     // storage order of the background: bg_order[k] is the caller's index of
-    // the background Gaussian stored at position k (device copy for the
-    // contribution pass, which reports scores by the caller's index)
+    // the background Gaussian stored at position k; device copies of it
+    // (bg_index) and of its inverse (bg_slot), int32
     std::vector<long long> bg_order;
-    gsb::DevBuf bg_order_dev;
+    gsb::DevBuf bg_index, bg_slot;
     // host staging of tables
     std::vector<gsb::EnvInfo> h_envs;
     std::vector<gsb::ProjBlock> h_blocks;

@@ -16,8 +16,10 @@
 //     record slots: local index j = g for background Gaussians (padded to a
 //       multiple of 32), then the env's link Gaussians in storage order; slot
 //       (el, j) is at envs[el].rec_base + j in r0..r3, valid where bit j%32 of
-//       mask[envs[el].mask_base + j/32] is set.  Local order = storage order,
-//       so the key (depth bits << 32 | j) orders ties by storage position.
+//       mask[envs[el].mask_base + j/32] is set.  Keys are (depth bits << 32 |
+//       i) with i the caller's local index (background: its index before the
+//       Morton reordering; links: j), so equal depths order by global index;
+//       the compositor maps i back to the record slot j.
 //     xf[envs[el].xf_base + f]  frame f = 0 background, f = 1 + (l - link_begin)
 //     counts/off_local/cursor[envs[el].tile_base + t]  per (env, tile)
 //     env_base[el]              exclusive scan of per-env intersection totals
@@ -114,6 +116,7 @@ struct ProjParams {
     float2* dbg_hxy;  // nullable, per record slot
     unsigned long long* nvis;  // nullable: visible (env, Gaussian) pair counter
     const gs_lidar* lidars;    // LiDAR projection only: per env of the wave
+    const int* bg_index;       // nullable: caller's index of the background Gaussian in slot j (into r3.w)
 };
 
 struct BinParams {
@@ -131,6 +134,13 @@ struct BinParams {
     uint32_t* cursor;
     unsigned long long* pairs;
     uint32_t* status;
+    // Keys carry the caller's local index of the Gaussian, so equal depths
+    // order by it: camera records hold it in r3.w (index_in_r3), LiDAR
+    // records are mapped through bg_index (nullable: caller's index of the
+    // background Gaussian in storage slot j < n_bg)
+    int index_in_r3;
+    const int* bg_index;
+    unsigned int n_bg;
 };
 
 struct CompParams {
@@ -162,7 +172,9 @@ struct CompParams {
     const gs_appearance* appear;  // nullable: per env (wave-local index) for rgb8
     float* score;         // nullable: contribution pass (no images): score[g] += sum of alpha T
     unsigned int nbp;     // background slots (slot j < nbp is the background Gaussian stored at j)
-    const long long* bg_order;  // contribution pass: caller's index of the background Gaussian stored at j
+    const int* bg_index;  // nullable: caller's index of the background Gaussian in slot j (contribution pass)
+    const int* bg_slot;   // nullable: keys carry the caller's background index i < n_bg; its record slot is bg_slot[i]
+    unsigned int n_bg;
     const gs_lidar* lidars;  // nullable: LiDAR scan (range in depth, hit in alpha), per env of the wave
     const uint4* r3;         // LiDAR scan: records' fourth word (|g2|)
     uint32_t* status;
@@ -210,6 +222,8 @@ struct SceneView {
     DevGaussians D;
     uint32_t* status;
     int tile_w, tile_h;
+    const int* bg_index;  // nullable: caller's index of the background Gaussian in storage slot j
+    const int* bg_slot;   // nullable: storage slot of the caller's background Gaussian i
 };
 SceneView scene_view(gs_scene s);
 // Set the thread-local message returned by gs_last_error and return st.

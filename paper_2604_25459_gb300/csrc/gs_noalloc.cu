@@ -215,6 +215,7 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
         P.r3 = reinterpret_cast<uint4*>(base + y.r3);
         P.mask = reinterpret_cast<uint32_t*>(base + y.mask);
         P.dbg_hxy = nullptr;
+        P.bg_index = v.bg_index;
         NA_CK(launch_project(v.D, P, nb, st), "projection");
         uint32_t* counts = reinterpret_cast<uint32_t*>(base + y.counts);
         uint32_t* off = reinterpret_cast<uint32_t*>(base + y.off);
@@ -229,6 +230,9 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
         B.e_begin = 0;
         B.tile_w = tw;
         B.tile_h = th;
+        B.index_in_r3 = 1;
+        B.bg_index = v.bg_index;
+        B.n_bg = (unsigned)v.D.n_bg;
         B.words_per_block = kWordsPerBlock;
         B.counts = counts;
         B.off_local = off;
@@ -259,6 +263,8 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
         C.item_begin = 0;
         C.item_end = sen.tile_base;
         C.chunk = 1;
+        C.bg_slot = v.bg_slot;
+        C.n_bg = (unsigned)v.D.n_bg;
         C.work = reinterpret_cast<unsigned int*>(base + y.work);
         C.r0 = P.r0;
         C.r1 = P.r1;

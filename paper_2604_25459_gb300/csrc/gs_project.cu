@@ -368,6 +368,9 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
     const float qstar = a3.y;
     const bool live = act && qstar >= 0.0f;
     const float trace = a3.z;  // trace(Sigma) >= its largest eigenvalue (rotation-invariant)
+    // the caller's local index (the key's tie order): background slots map
+    // through the storage order, link slots are their own
+    const uint32_t key_index = (blk.frame0 && P.bg_index && act) ? (uint32_t)__ldg(P.bg_index + local) : local;
     // Background blocks (one link frame for every thread) stage, per env of a
     // chunk, what the depth test needs (the frame's z row, the near plane) and
     // the env's visibility-word base in shared memory, so that the many culled
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                         P.r0[ri] = make_float4(u, v, a0.w, mz);
                         P.r1[ri] = make_float4(l00, l01, l11, __uint_as_float(rx));
                         P.r2[ri] = make_float4(r, gg, b, __uint_as_float(ry));
-                        P.r3[ri] = make_uint4(rx, ry, __float_as_uint(mz), 0u);
+                        P.r3[ri] = make_uint4(rx, ry, __float_as_uint(mz), key_index);
                         if (P.dbg_hxy) P.dbg_hxy[ri] = make_float2(hx, hy);
                         vis = true;
                     }

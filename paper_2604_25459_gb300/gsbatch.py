@@ -392,18 +392,10 @@ class Scene:
 
     def storage_order(self) -> np.ndarray:
         """order[k] = the caller's index of the background Gaussian stored at
-        position k (the scene's Morton order; equal depths composite in it)."""
+        position k (the scene's Morton order of the means)."""
         order = np.zeros(max(self.n_background, 1), np.int64)
         _check(lib().gs_scene_get_order(self._h, _ptr(order), len(order)))
         return order[:self.n_background]
-
-    def tie_rank(self, n_links_total: int = 0) -> np.ndarray:
-        """Per Gaussian in the caller's global order (background, then link
-        Gaussians), its position in the order that breaks depth ties."""
-        nb = self.n_background
-        rank = np.arange(nb + n_links_total, dtype=np.int64)
-        rank[self.storage_order()] = np.arange(nb, dtype=np.int64)
-        return rank
 
     def debug_records(self, env: int, n: int) -> dict:
         out = dict(visible=np.zeros(n, np.uint8), u=np.zeros(n, np.float32), v=np.zeros(n, np.float32),

@@ -21,7 +21,7 @@ def _sensors(E, rows=16, cols=128, seed=4):
     return s
 
 
-def _oracle_scan(w, e, sen, rank=None):
+def _oracle_scan(w, e, sen):
     bg, lk = w.background, w.links
     mean = np.concatenate([bg.mean, lk.mean])
     quat = np.concatenate([bg.quat, lk.quat])
@@ -31,7 +31,7 @@ def _oracle_scan(w, e, sen, rank=None):
     return lidar.render_lidar(mean, quat, ls, op, link_of, w.link_poses[e],
                               dict(q_ws=sen["q_ws"].astype(float), t_ws=sen["t_ws"].astype(float),
                                    rows=int(sen["rows"]), cols=int(sen["cols"]), elev_min=float(sen["elev_min"]),
-                                   elev_max=float(sen["elev_max"]), near=float(sen["near_range"])), rank=rank)
+                                   elev_max=float(sen["elev_max"]), near=float(sen["near_range"])))
 
 
 def test_lidar_scan_matches_oracle():
@@ -45,9 +45,8 @@ def test_lidar_scan_matches_oracle():
     torch.cuda.synchronize()
     scene.sync_status()
     g_r, g_h = rng.cpu().numpy(), hit.cpu().numpy()
-    rank = scene.tie_rank(w.links.n)
     for e in range(w.n_envs):
-        ref = _oracle_scan(w, e, sens[e], rank)
+        ref = _oracle_scan(w, e, sens[e])
         dh = np.abs(g_h[e] - ref["hit"])
         both = (ref["hit"] >= 0.5) & (g_h[e] >= 0.5)
         rel = np.abs(g_r[e] - ref["range"])[both] / ref["range"][both]

@@ -30,8 +30,7 @@ def _keyed_check(w, e, out, sh_degree=3):
     zk = keyed_zkey(proj, rec)
     W, H = int(w.cams[e]["width"]), int(w.cams[e]["height"])
     ind = oracle.render_projected(proj, W, H)
-    # keyed: the GPU's depth keys and its tie order (the scene's storage order)
-    key = oracle.render_projected(proj, W, H, zkey=zk, rank=scene.tie_rank(w.links.n))
+    key = oracle.render_projected(proj, W, H, zkey=zk)
     st_i = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], ind)
     st_k = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], key, amb_bits=AMB_ALPHA | AMB_T)
     return st_i, st_k, rec, proj
@@ -80,16 +79,14 @@ def test_binning_keyed_bit_exact(tile):
     scene = out["scene"]
     W, H = 160, 120
     ntiles = (-(-W // tile[0])) * (-(-H // tile[1]))
-    rank = scene.tie_rank(w.links.n)
     for e in range(w.n_envs):
         rec = scene.debug_records(e, w.background.n + w.links.n)
         vis = np.nonzero(rec["visible"])[0]
         counts, lists = scene.debug_tiles(e, ntiles)
-        # the oracle orders equal depths by the index it is given: the GPU's tie rank
         oc, ol = oracle.bin_records(rec["u"][vis], rec["v"][vis], rec["hx"][vis], rec["hy"][vis],
-                                    rec["z"][vis].view(np.uint32), rank[vis].astype(np.uint32), W, H, *tile)
+                                    rec["z"][vis].view(np.uint32), vis.astype(np.uint32), W, H, *tile)
         np.testing.assert_array_equal(counts.astype(np.int64), oc)
-        np.testing.assert_array_equal(rank[lists.astype(np.int64)], ol.astype(np.int64))
+        np.testing.assert_array_equal(lists, ol)
         assert counts.max() > 2048  # the windowed depth selection was exercised
     scene.close()
 
@@ -246,8 +243,9 @@ def test_background_storage_order():
     """The scene stores its background in Morton order of the means (a layout
     choice of the library): the order is a permutation whose codes do not
     decrease, and a caller-side shuffle of the background changes neither the
-    images (up to pixels where two splats of exactly equal depth swap) nor the
-    per-Gaussian contribution scores, which stay in the caller's order."""
+    images (up to pixels where two splats of exactly equal depth swap: ties
+    follow the caller's global index) nor the per-Gaussian contribution
+    scores, which stay in the caller's order."""
     import torch
 
     w = synth.make_c1(n_envs=2, width=160, height=120, f=125.0, n_bg=60_000, per_link=2000)
@@ -292,3 +290,39 @@ def test_background_storage_order():
     # (equal scores up to the order of the float atomic adds)
     np.testing.assert_allclose(back, sc[:nb], rtol=1e-4, atol=1e-5)
     np.testing.assert_allclose(sc2[nb:], sc[nb:], rtol=1e-4, atol=1e-5)
+
+
+def test_equal_depth_ties_follow_global_index():
+    """Two background splats at exactly the same camera depth, overlapping,
+    whose Morton storage order (left one first) is the reverse of their global
+    order: where both are blended, the lower global index composites first,
+    as in the oracle."""
+    import math
+
+    import torch
+
+    z, W, H, f = 2.0, 32, 32, 40.0
+    mean = np.array([[0.06, 0.0, z], [-0.06, 0.0, z]], np.float32)  # index 0 right, index 1 left
+    n = 2
+    sh = np.zeros((n, 16, 3), np.float32)
+    y0 = 0.5 / math.sqrt(math.pi)
+    sh[0, 0, :] = (np.array([1.0, 0.0, 0.0]) - 0.5) / y0  # red
+    sh[1, 0, :] = (np.array([0.0, 0.0, 1.0]) - 0.5) / y0  # blue
+    bg = synth.Gaussians(mean, np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                         np.full((n, 3), math.log(0.08), np.float32), np.full(n, 0.6, np.float32), sh)
+    cams = synth.make_cameras(1, f, f, W / 2, H / 2, W, H, [[1, 0, 0, 0]], [[0, 0, 0]])
+    w = synth.Workload("ties", bg, np.zeros(1, np.int64), bg.slice(0, 0), np.zeros((1, 0, 7), np.float32), cams)
+    scene = gsbatch.Scene(w.background)
+    assert scene.storage_order().tolist() == [1, 0]  # the left splat is stored first
+    rgb, depth, alpha = scene.render(None, w.cams)
+    torch.cuda.synchronize()
+    scene.sync_status()
+    rgb = rgb.cpu().numpy()[0]
+    scene.close()
+    ref = oracle.render_env(w, 0)
+    both = ref["alpha"] > 0.6  # pixels where both splats blend
+    assert both.sum() > 4
+    np.testing.assert_allclose(rgb[both], ref["rgb"][both], atol=2e-3)
+    # red (index 0) first: at the centre pixel red carries more weight than blue
+    j, i = H // 2, W // 2
+    assert rgb[j, i, 0] > rgb[j, i, 2] + 0.1

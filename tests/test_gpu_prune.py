@@ -18,17 +18,16 @@ def _scores(w):
     sc = scene.contribution(poses, w.cams)
     torch.cuda.synchronize()
     scene.sync_status()
-    rank = scene.tie_rank(w.links.n)
     scene.close()
-    return sc.cpu().numpy().astype(np.float64), rank
+    return sc.cpu().numpy().astype(np.float64)
 
 
-def _oracle_scores(w, rank=None):
+def _oracle_scores(w):
     S = oracle.scene_arrays(w)
     tot = np.zeros(S.n, np.float64)
     alpha = 0.0
     for e in range(w.n_envs):
-        ref = oracle.render_env(w, e, S=S, contrib=True, rank=rank)
+        ref = oracle.render_env(w, e, S=S, contrib=True)
         tot += ref["contrib"]
         alpha += ref["alpha"].astype(np.float64).sum()
     return tot, alpha
@@ -41,8 +40,8 @@ def test_contribution_matches_oracle(name):
         w = synth.make_c0()
     else:
         w = synth.make_c1(n_envs=3, width=96, height=72, f=75.0, n_bg=20_000, per_link=500)
-    got, rank = _scores(w)
-    ref, alpha_sum = _oracle_scores(w, rank)
+    got = _scores(w)
+    ref, alpha_sum = _oracle_scores(w)
     assert got.shape == ref.shape
     # the weights telescope: their total is the covered area
     assert abs(got.sum() - alpha_sum) <= 1e-4 * alpha_sum
@@ -64,7 +63,7 @@ def test_pruned_scene_renders_and_reports_error():
 
     ensure_built()
     w = synth.make_c1(n_envs=4, width=96, height=72, f=75.0, n_bg=40_000, per_link=1000)
-    scores, _ = _scores(w)
+    scores = _scores(w)
     p = gsbatch.prune_workload(w, scores, keep_bg=0.3, keep_links=0.1)
     assert p.background.n == int(np.ceil(0.3 * w.background.n))
     assert p.links.n == sum(int(np.ceil(0.1 * 1000)) for _ in range(w.n_links))
