@@ -39,9 +39,9 @@ UNIT = "env-frames/s"
 # summarised in profiles/k_composite_c1.md (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 32-env launch, divided by 32), valid only for
 # the compositor sources it was taken on.
-COMPOSITE_TRAFFIC_PER_ENV = (0.703232e9 + 0.531031e9) / 32
+COMPOSITE_TRAFFIC_PER_ENV = (0.716937e9 + 0.536204e9) / 32
 COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu",)
-COMPOSITE_TRAFFIC_SHA = "880e32f8e485f9cb"
+COMPOSITE_TRAFFIC_SHA = "d6a9ca750a240ee3"
 
 
 def _sources_sha(paths) -> str:
