@@ -345,7 +345,7 @@ __device__ __forceinline__ bool pixel_range(float c, float h, int n, int& lo, in
     return true;
 }
 
-constexpr int kProjStageEnvs = 256;  // envs per shared-memory chunk of a background block
+constexpr int kProjStageEnvs = 256;  // envs per shared-memory chunk of a projection block
 
 template <int D, int DT>
 __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
@@ -371,55 +371,55 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
     // the caller's local index (the key's tie order): background slots map
     // through the storage order, link slots are their own
     const uint32_t key_index = (blk.frame0 && P.bg_index && act) ? (uint32_t)__ldg(P.bg_index + local) : local;
-    // Background blocks (one link frame for every thread) stage, per env of a
-    // chunk, what the depth test needs (the frame's z row, the near plane) and
-    // the env's visibility-word base in shared memory, so that the many culled
-    // (env, Gaussian) pairs wait on one shared load instead of a chain of two
-    // table loads.
-    __shared__ float4 s_r2[kProjStageEnvs];
-    __shared__ float s_near[kProjStageEnvs];
-    __shared__ unsigned long long s_mb[kProjStageEnvs];
-    const bool staged = blk.frame0 != 0;
+    // Every block stages, per env of a chunk, the camera, guard-band limits
+    // and table offsets in shared memory; background blocks (one link frame
+    // for every thread) also stage the frame's z row.  The many culled (env,
+    // Gaussian) pairs then wait on shared loads instead of chains of table
+    // loads, and the visible ones read their camera from shared memory.
+    __shared__ float4 s_r2[kProjStageEnvs];     // background blocks: frame 0's z row
+    __shared__ float4 s_cam[kProjStageEnvs];    // fx, fy, cx, cy
+    __shared__ float4 s_lim[kProjStageEnvs];    // guard-band limits
+    __shared__ int4 s_misc[kProjStageEnvs];     // W, H, xf_base, near plane (bits)
+    __shared__ unsigned long long s_mb[kProjStageEnvs];  // visibility-word base
+    __shared__ unsigned long long s_rb[kProjStageEnvs];  // record base
+    const bool frame0 = blk.frame0 != 0;
     for (int c0 = blk.e0; c0 < blk.e1; c0 += kProjStageEnvs) {
     const int c1 = min(c0 + kProjStageEnvs, blk.e1);
-    if (staged) {  // block-uniform
-        __syncthreads();  // the previous chunk's entries are no longer read
-        for (int i = t; i < c1 - c0; i += blockDim.x) {
-            const EnvInfo* Ei = P.envs + c0 + i;
-            s_r2[i] = __ldg(&P.xf[__ldg(&Ei->xf_base)].r2);
-            s_near[i] = __ldg(&P.cams[c0 + i].near_plane);
-            s_mb[i] = __ldg(&Ei->mask_base);
-        }
-        __syncthreads();
+    __syncthreads();  // the previous chunk's entries are no longer read
+    for (int i = t; i < c1 - c0; i += blockDim.x) {
+        const EnvInfo* Ei = P.envs + c0 + i;
+        const gs_camera* ci = P.cams + c0 + i;
+        const int xb = __ldg(&Ei->xf_base);
+        if (frame0) s_r2[i] = __ldg(&P.xf[xb].r2);
+        s_cam[i] = make_float4(__ldg(&ci->fx), __ldg(&ci->fy), __ldg(&ci->cx), __ldg(&ci->cy));
+        s_lim[i] = make_float4(__ldg(&Ei->lim[0]), __ldg(&Ei->lim[1]), __ldg(&Ei->lim[2]), __ldg(&Ei->lim[3]));
+        s_misc[i] = make_int4(__ldg(&ci->width), __ldg(&ci->height), xb, __float_as_int(__ldg(&ci->near_plane)));
+        s_mb[i] = __ldg(&Ei->mask_base);
+        s_rb[i] = __ldg(&Ei->rec_base);
     }
+    __syncthreads();
     for (int el = c0; el < c1; ++el) {
         bool vis = false;
-        const EnvInfo* E = P.envs + el;
+        const int ei = el - c0;
         if (live) {
-            const LinkXf* Xp = P.xf + __ldg(&E->xf_base) + li;
+            const int4 misc = s_misc[ei];
+            const LinkXf* Xp = P.xf + misc.z + li;
             // depth first: most (env, Gaussian) pairs stop at the near-plane test,
-            // so only the z row of the transform and the near plane are loaded here
+            // so only the z row of the transform and the near plane are read here
             LinkXf X;
-            const gs_camera* cam = P.cams + el;
-            float near;
-            if (staged) {
-                X.r2 = s_r2[el - c0];
-                near = s_near[el - c0];
-            } else {
-                X.r2 = __ldg(&Xp->r2);
-                near = __ldg(&cam->near_plane);
-            }
+            const float near = __int_as_float(misc.w);
+            X.r2 = frame0 ? s_r2[ei] : __ldg(&Xp->r2);
             const float mz = X.r2.x * a0.x + X.r2.y * a0.y + X.r2.z * a0.z + X.r2.w;
             if (mz > near) {
                 X.r0 = __ldg(&Xp->r0);
                 X.r1 = __ldg(&Xp->r1);
                 const float mx = X.r0.x * a0.x + X.r0.y * a0.y + X.r0.z * a0.z + X.r0.w;
                 const float my = X.r1.x * a0.x + X.r1.y * a0.y + X.r1.z * a0.z + X.r1.w;
-                const float fx = __ldg(&cam->fx), fy = __ldg(&cam->fy);
-                const float cx = __ldg(&cam->cx), cy = __ldg(&cam->cy);
-                const int W = __ldg(&cam->width), H = __ldg(&cam->height);
-                const float limxn = __ldg(&E->lim[0]), limxp = __ldg(&E->lim[1]);  // per env, from the tables
-                const float limyn = __ldg(&E->lim[2]), limyp = __ldg(&E->lim[3]);
+                const float4 cam = s_cam[ei], lim = s_lim[ei];
+                const float fx = cam.x, fy = cam.y, cx = cam.z, cy = cam.w;
+                const int W = misc.x, H = misc.y;
+                const float limxn = lim.x, limxp = lim.y;  // per env, from the tables
+                const float limyn = lim.z, limyp = lim.w;
                 const float iz = 1.0f / mz;
                 const float u = fx * mx * iz + cx;
                 const float v = fy * my * iz + cy;
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                         sh_colour<D, DT>(P.sh, P.n_gauss, g, dx, dy, dz, r, gg, b);
                         const uint32_t rx = (uint32_t)i0 | ((uint32_t)i1 << 16);
                         const uint32_t ry = (uint32_t)j0 | ((uint32_t)j1 << 16);
-                        const size_t ri = (size_t)__ldg(&E->rec_base) + local;
+                        const size_t ri = (size_t)s_rb[ei] + local;
                         P.r0[ri] = make_float4(u, v, a0.w, mz);
                         P.r1[ri] = make_float4(l00, l01, l11, __uint_as_float(rx));
                         P.r2[ri] = make_float4(r, gg, b, __uint_as_float(ry));
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
         }
         const uint32_t m = __ballot_sync(0xffffffffu, vis);
         if (lane == 0 && warp_live) {
-            const unsigned long long mb = staged ? s_mb[el - c0] : __ldg(&E->mask_base);
+            const unsigned long long mb = s_mb[ei];
             P.mask[(size_t)mb + (local >> 5)] = m;
             if (P.nvis && m) atomicAdd(P.nvis, (unsigned long long)__popc(m));
         }
