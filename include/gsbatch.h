@@ -48,7 +48,7 @@ typedef enum {
     GS_ERR_OOM = -2,         /* device allocation failed or the scratch budget is too small */
     GS_ERR_CUDA = -3,        /* a CUDA runtime call failed (message in gs_last_error) */
     GS_ERR_TIMEOUT = -4,     /* a bounded device wait gave up */
-    GS_ERR_UNSUPPORTED = -5, /* valid request outside what this build implements */
+    GS_ERR_UNSUPPORTED = -5, /* valid request outside what the library implements */
     GS_ERR_DEVICE = -6       /* the device status word reports a fault (see gs_scene_sync_status) */
 } gs_status;
 

@@ -50,7 +50,7 @@ def test_max_over_ranks_gloo_two_ranks():
 
 
 def test_reference_arm_under_torchrun_two_ranks():
-    """bench.py --impl reference launched as the driver launches N > 1 runs:
+    """bench.py --impl reference launched under torchrun with 2 processes:
     rank 0 prints one JSON line, the other rank exits 0 without work."""
     pytest.importorskip("torch.distributed.run")
     port = _free_port()
