@@ -39,9 +39,9 @@ UNIT = "env-frames/s"
 # summarised in profiles/k_composite_c1.md (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 32-env launch, divided by 32), valid only for
 # the compositor sources it was taken on.
-COMPOSITE_TRAFFIC_PER_ENV = (0.716937e9 + 0.536204e9) / 32
+COMPOSITE_TRAFFIC_PER_ENV = (0.718516e9 + 0.537122e9) / 32
 COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu",)
-COMPOSITE_TRAFFIC_SHA = "d6a9ca750a240ee3"
+COMPOSITE_TRAFFIC_SHA = "0fd58c558cf37fe0"
 
 
 def _sources_sha(paths) -> str:
@@ -713,6 +713,7 @@ def run_lidar(a, rank, world, local_rank):
     sens["t_ws"] = -(np.array([-1.0, 0.0, 1.4]) + rng.uniform(-0.2, 0.2, (E, 3)))
     sens["rows"], sens["cols"] = a.beams, a.azimuth
     sens["elev_min"], sens["elev_max"], sens["near_range"] = -0.4, 0.3, 0.05
+    sens["az_min"], sens["az_max"] = 0.0, 2.0 * np.pi  # rotating: a full revolution
     R, Cc = a.beams, a.azimuth
     out_r = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)
     out_h = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)

@@ -176,24 +176,28 @@ gs_status gs_render_batch_obs_host(gs_scene s, int n_envs, const float* link_pos
                                    void* cuda_stream);
 
 /* Batch-LiDAR (the paper's ray-casting LiDAR over the same Gaussians, with
- * dynamic objects and self-occlusion, Sec. III-E and Table II).  A rotating
- * LiDAR of `rows` beams x `cols` azimuth steps; sensor frame x forward, y
- * left, z up; ray (i, j) has azimuth 2 pi (i + 1/2) / cols and elevation
- * elev_min + (elev_max - elev_min) (j + 1/2) / rows.  Each ray is composited
+ * dynamic objects and self-occlusion, Sec. III-E and Table II).  A LiDAR of
+ * `rows` beams x `cols` azimuth steps over the azimuth window [az_min,
+ * az_max): a rotating LiDAR covers a full revolution (0, 2 pi), a solid-state
+ * one a narrower field of view; sensor frame x forward, y left, z up; ray
+ * (i, j) has azimuth az_min + (az_max - az_min) (i + 1/2) / cols and
+ * elevation elev_min + (elev_max - elev_min) (j + 1/2) / rows.  Each ray is composited
  * front to back like a camera pixel (alpha = min(0.99, o exp(-q/2)) >= 1/255,
  * stop when T (1 - alpha) < 1e-4, order by distance of the Gaussian's centre
  * from the sensor, ties by global index), the Gaussian evaluated at its
  * closest approach along the ray: with G = diag(e^-s) R^T in the sensor
  * frame, a = G d and b = G mu, q = |a x b|^2 / |a|^2 at t* = a.b / |a|^2;
- * Gaussians with t* <= near_range are skipped.  48 bytes. */
+ * Gaussians with t* <= near_range are skipped.  56 bytes. */
 typedef struct {
     float q_ws[4];     /* world -> sensor rotation (w,x,y,z) */
     float t_ws[3];     /* world -> sensor translation */
     int32_t rows;      /* beams */
-    int32_t cols;      /* azimuth steps per revolution */
+    int32_t cols;      /* azimuth steps across the window */
     float elev_min;    /* radians */
     float elev_max;    /* radians, > elev_min, both within (-pi/2, pi/2) */
     float near_range;  /* > 0 */
+    float az_min;      /* radians, finite */
+    float az_max;      /* radians, az_min < az_max <= az_min + 2 pi */
 } gs_lidar;
 
 /* Scan n_envs environments:

@@ -11,10 +11,12 @@ states a reading: every ray is composited front to back over the Gaussians
 like a camera pixel, with each Gaussian evaluated at its closest approach
 along the ray in ray space instead of through a 2D projection:
 
-* rotating LiDAR of ``rows`` beams x ``cols`` azimuth steps, sensor frame
-  x forward, y left, z up; ray (i, j) has azimuth phi = 2 pi (i + 1/2) / cols
-  and elevation theta = elev_min + (elev_max - elev_min) (j + 1/2) / rows,
-  direction d = (cos theta cos phi, cos theta sin phi, sin theta);
+* a LiDAR of ``rows`` beams x ``cols`` azimuth steps over the azimuth window
+  [az_min, az_max) (a rotating LiDAR covers [0, 2 pi); a solid-state one a
+  narrower field of view), sensor frame x forward, y left, z up; ray (i, j)
+  has azimuth phi = az_min + (az_max - az_min) (i + 1/2) / cols and elevation
+  theta = elev_min + (elev_max - elev_min) (j + 1/2) / rows, direction
+  d = (cos theta cos phi, cos theta sin phi, sin theta);
 * a Gaussian with sensor-frame mean mu and covariance Sigma = R diag(e^2s) R^T
   has q(t) = |G (t d - mu)|^2 with G = diag(e^-s) R^T; with a = G d and
   b = G mu its minimum is at t* = a.b / |a|^2 and equals |a x b|^2 / |a|^2;
@@ -52,9 +54,10 @@ def quat_to_mat(q) -> np.ndarray:
     return R
 
 
-def ray_directions(rows: int, cols: int, elev_min: float, elev_max: float) -> np.ndarray:
+def ray_directions(rows: int, cols: int, elev_min: float, elev_max: float, az_min: float = 0.0,
+                   az_max: float = 2.0 * np.pi) -> np.ndarray:
     """Unit ray directions [rows, cols, 3] in the sensor frame."""
-    phi = 2.0 * np.pi * (np.arange(cols) + 0.5) / cols
+    phi = az_min + (az_max - az_min) * (np.arange(cols) + 0.5) / cols
     theta = elev_min + (elev_max - elev_min) * (np.arange(rows) + 0.5) / rows
     ct, st = np.cos(theta)[:, None], np.sin(theta)[:, None]
     return np.stack([ct * np.cos(phi)[None, :], ct * np.sin(phi)[None, :], np.broadcast_to(st, (rows, cols))], -1)
@@ -64,7 +67,8 @@ def render_lidar(mean, quat, log_scale, opacity, link_of, link_poses, sensor, ra
     """One env.  mean/quat/log_scale/opacity: the scene's Gaussians (background
     then link-major); link_of [n]: -1 for background, else the link index whose
     pose (link_poses [L][7], link -> world) moves it; sensor: dict with q_ws,
-    t_ws (world -> sensor), rows, cols, elev_min, elev_max, near; rank [n]
+    t_ws (world -> sensor), rows, cols, elev_min, elev_max, near and
+    optionally az_min, az_max (default: a full revolution); rank [n]
     (optional): the order among Gaussians at equal distance (default: global
     index).  Returns range [rows, cols], hit [rows, cols]."""
     mean = np.asarray(mean, np.float64)
@@ -91,7 +95,8 @@ def render_lidar(mean, quat, log_scale, opacity, link_of, link_poses, sensor, ra
     dist = np.linalg.norm(mu, axis=1)
     tie = np.arange(len(dist)) if rank is None else np.asarray(rank)
     order = np.lexsort((tie, dist))
-    D = ray_directions(sensor["rows"], sensor["cols"], sensor["elev_min"], sensor["elev_max"])
+    D = ray_directions(sensor["rows"], sensor["cols"], sensor["elev_min"], sensor["elev_max"],
+                       sensor.get("az_min", 0.0), sensor.get("az_max", 2.0 * np.pi))
     rows, cols = D.shape[:2]
     rng = np.zeros((rows, cols))
     hit = np.zeros((rows, cols))

@@ -1134,6 +1134,9 @@ gs_status gs_render_lidar(gs_scene s, int n_envs, const float* link_poses, const
             return fail(GS_ERR_INVALID, "sensor %d: elevation range must lie in (-pi/2, pi/2)", e);
         if (!(l.near_range > 0.0f) || !std::isfinite(l.near_range))
             return fail(GS_ERR_INVALID, "sensor %d: near_range must be > 0", e);
+        if (!std::isfinite(l.az_min) || !std::isfinite(l.az_max) || !(l.az_min < l.az_max) ||
+            !((double)l.az_max - (double)l.az_min <= 6.283186))  // 2 pi, with the rounding of float(2 pi)
+            return fail(GS_ERR_INVALID, "sensor %d: azimuth window must satisfy az_min < az_max <= az_min + 2 pi", e);
         // the pose travels to the link-table kernel as a camera of the grid's size
         gs_camera& c = cams[e];
         c.fx = c.fy = 1.0f;

@@ -427,7 +427,8 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     if constexpr (MODE == 1) {
         const gs_lidar* Ld = P.lidars + el;
         const float em = __ldg(&Ld->elev_min), eM = __ldg(&Ld->elev_max);
-        const float phi = 6.283185307179586f * fpx / (float)W;
+        const float az0 = __ldg(&Ld->az_min), span = __ldg(&Ld->az_max) - az0;
+        const float phi = az0 + span * fpx / (float)W;
         const float th0 = em + (eM - em) * fpy0 / (float)H, th1 = em + (eM - em) * fpy1 / (float)H;
         float sp, cp, s0, c0, s1, c1;
         sincosf(phi, &sp, &cp);

@@ -1,5 +1,5 @@
 // Batch-LiDAR projection: every (env, Gaussian) of a wave against the env's
-// rotating LiDAR.  The paper's Batch-LiDAR ray-casts the 3DGS scene with its
+// LiDAR (a rotating one, or a solid-state one with a narrower azimuth window).  The paper's Batch-LiDAR ray-casts the 3DGS scene with its
 // moving links (Sec. III-E, Table II); here a scan is rendered like an image
 // over the (azimuth, beam) grid: this kernel writes, per visible pair, the
 // Gaussian's ray-space factors in the sensor frame and a conservative grid box
@@ -87,11 +87,31 @@ __global__ void __launch_bounds__(256) k_project_lidar(ProjParams P) {
                     any = grid_range(thc - rho, thc + rho, em, (eM - em) / (float)rows, rows, j0, j1);
                     if (any && fabsf(thc) + rho < kHalfPi) {
                         const float dphi = asinf(fminf(1.0f, sinf(rho) / cosf(thc))) * 1.001f + 1e-5f;
-                        float phc = atan2f(my, mx);
-                        if (phc < 0.0f) phc += kTwoPi;
-                        const float lo = phc - dphi, hi = phc + dphi;
-                        if (lo >= 0.0f && hi < kTwoPi)  // a box across the seam at 0 takes every column
-                            any = grid_range(lo, hi, 0.0f, kTwoPi / (float)cols, cols, i0, i1);
+                        // azimuth relative to the window start, within one turn: [0, 2 pi)
+                        const float az0 = __ldg(&L->az_min), step = (__ldg(&L->az_max) - az0) / (float)cols;
+                        float rel = atan2f(my, mx) - az0;
+                        rel -= kTwoPi * floorf(rel / kTwoPi);
+                        const float lo = rel - dphi, hi = rel + dphi;
+                        // the cone's azimuths in this turn, and their copy one turn away
+                        // when the cone crosses 0 (a full revolution then takes the
+                        // columns between the two ranges as well)
+                        int a0, a1, b0 = 0, b1 = -1;
+                        const bool ina = grid_range(lo, hi, 0.0f, step, cols, a0, a1);
+                        bool inb = false;
+                        if (lo < 0.0f) inb = grid_range(lo + kTwoPi, hi + kTwoPi, 0.0f, step, cols, b0, b1);
+                        else if (hi >= kTwoPi) inb = grid_range(lo - kTwoPi, hi - kTwoPi, 0.0f, step, cols, b0, b1);
+                        if (ina && inb) {
+                            i0 = min(a0, b0);
+                            i1 = max(a1, b1);
+                        } else if (ina) {
+                            i0 = a0;
+                            i1 = a1;
+                        } else if (inb) {
+                            i0 = b0;
+                            i1 = b1;
+                        } else {
+                            any = false;
+                        }
                     }
                 }
                 if (any) {

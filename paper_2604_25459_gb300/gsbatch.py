@@ -63,8 +63,9 @@ PLAN_AUTOTUNE, PLAN_GRAPH = 1, 2
 
 # gs_lidar in include/gsbatch.h (48 bytes)
 LIDAR_DTYPE = np.dtype([("q_ws", "<f4", (4,)), ("t_ws", "<f4", (3,)), ("rows", "<i4"), ("cols", "<i4"),
-                        ("elev_min", "<f4"), ("elev_max", "<f4"), ("near_range", "<f4")])
-assert LIDAR_DTYPE.itemsize == 48
+                        ("elev_min", "<f4"), ("elev_max", "<f4"), ("near_range", "<f4"), ("az_min", "<f4"),
+                        ("az_max", "<f4")])
+assert LIDAR_DTYPE.itemsize == 56
 
 
 class GsServerConfig(C.Structure):

@@ -503,6 +503,44 @@ def test_lidar_occlusion_and_order():
     assert abs(out["range"][3, 17] - (0.99 * D1 + 0.01 * o2 * D2) / (1 - T)) < 1e-12
 
 
+def test_lidar_solid_state_window_matches_rotating_columns():
+    """A solid-state LiDAR whose azimuth window [0, pi/2) is cut into 9 steps
+    casts exactly the rays of columns 0..8 of a rotating LiDAR with 36 steps
+    (both at 10-degree spacing, centres at 5, 15, ... degrees), so its scan
+    equals those columns; a Gaussian on the axis of one of its rays is hit
+    with the single-Gaussian closed form, and one outside the window is not
+    hit by any ray."""
+    from oracle import lidar
+
+    d = lidar.ray_directions(4, 9, -0.3, 0.3, 0.0, 0.5 * np.pi)
+    phi = np.radians(5.0 + 10.0 * np.arange(9))
+    np.testing.assert_allclose(np.arctan2(d[0, :, 1], d[0, :, 0]), phi, atol=1e-12)
+    rng = np.random.default_rng([3, 77])
+    n = 40
+    mean = rng.uniform(-2.0, 2.0, (n, 3)) + np.array([0.0, 0.0, 0.0])
+    mean[:, :2] += 2.5  # mostly in the first quadrant
+    quat = rng.normal(size=(n, 4))
+    ls = rng.uniform(-2.5, -1.2, (n, 3))
+    op = rng.uniform(0.2, 0.95, n)
+    rot = lidar.render_lidar(mean, quat, ls, op, np.full(n, -1), None, _sensor(rows=4, cols=36))
+    solid = dict(_sensor(rows=4, cols=9), az_min=0.0, az_max=0.5 * np.pi)
+    sol = lidar.render_lidar(mean, quat, ls, op, np.full(n, -1), None, solid)
+    np.testing.assert_allclose(sol["range"], rot["range"][:, :9], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(sol["hit"], rot["hit"][:, :9], rtol=1e-12, atol=1e-12)
+    assert sol["hit"].max() > 0.3
+    # one Gaussian on the axis of ray (1, 4) of a window off the x axis
+    win = dict(_sensor(rows=4, cols=8, elev=(-0.2, 0.2)), az_min=0.6, az_max=1.4)
+    dw = lidar.ray_directions(4, 8, -0.2, 0.2, 0.6, 1.4)
+    D, o, sig = 3.0, 0.7, 0.05
+    out = lidar.render_lidar([D * dw[1, 4]], [[1, 0, 0, 0]], [[np.log(sig)] * 3], [o], [-1], None, win)
+    assert abs(out["hit"][1, 4] - o) < 1e-12 and abs(out["range"][1, 4] - D) < 1e-12
+    # the same Gaussian turned by -1 rad about z (azimuth outside [0.6, 1.4)) is seen by no ray
+    c, s_ = np.cos(-1.0), np.sin(-1.0)
+    Rz = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+    out = lidar.render_lidar([Rz @ (D * dw[1, 4])], [[1, 0, 0, 0]], [[np.log(sig)] * 3], [o], [-1], None, win)
+    assert out["hit"].max() == 0.0
+
+
 def test_lidar_equal_distance_order_by_rank():
     """Two Gaussians at the same distance: one on the ray (t* = D), one off it
     by the angle th with a wide footprint (t* = D cos th).  They composite in
