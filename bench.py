@@ -78,7 +78,9 @@ def parse():
     ap.add_argument("--rates", default="1000,3000,10000,30000", help="c4: offered request rates (req/s)")
     ap.add_argument("--prune-envs", type=int, default=64, help="prune: envs whose cameras rank the Gaussians")
     ap.add_argument("--beams", type=int, default=64, help="lidar: beams (rows)")
-    ap.add_argument("--azimuth", type=int, default=1024, help="lidar: azimuth steps per revolution (columns)")
+    ap.add_argument("--azimuth", type=int, default=1024, help="lidar: azimuth steps across the window (columns)")
+    ap.add_argument("--az-window", default="0,6.283185307179586",
+                    help="lidar: azimuth window az_min,az_max in radians (a full turn: rotating; narrower: solid-state)")
     ap.add_argument("--duration", type=float, default=2.0, help="c4: seconds of arrivals per rate")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="c4: HBM budget of the request loop")
     ap.add_argument("--scene-budget-gb", type=float, default=0.0,
@@ -713,7 +715,8 @@ def run_lidar(a, rank, world, local_rank):
     sens["t_ws"] = -(np.array([-1.0, 0.0, 1.4]) + rng.uniform(-0.2, 0.2, (E, 3)))
     sens["rows"], sens["cols"] = a.beams, a.azimuth
     sens["elev_min"], sens["elev_max"], sens["near_range"] = -0.4, 0.3, 0.05
-    sens["az_min"], sens["az_max"] = 0.0, 2.0 * np.pi  # rotating: a full revolution
+    az0, az1 = (float(x) for x in a.az_window.split(","))
+    sens["az_min"], sens["az_max"] = az0, az1  # a full turn: rotating; narrower: solid-state
     R, Cc = a.beams, a.azimuth
     out_r = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)
     out_h = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)
@@ -747,8 +750,10 @@ def run_lidar(a, rank, world, local_rank):
                 "unit": "rays/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"c1 scene (500k room-shell background + 20x5k robot), {E} envs, rotating "
-                                       f"LiDAR {R} beams x {Cc} azimuth steps, elevation -0.4..0.3 rad",
+                "config": {"workload": f"c1 scene (500k room-shell background + 20x5k robot), {E} envs, "
+                                       f"{'rotating' if az1 - az0 >= 6.28318 else 'solid-state'} LiDAR {R} beams x "
+                                       f"{Cc} azimuth steps over azimuth {az0:.3f}..{az1:.3f} rad, elevation "
+                                       f"-0.4..0.3 rad",
                            "rays_hit_over_half": hit_frac},
                 "env_scans_per_s": world * E / (ms / 1e3),
                 "phase_ms_per_step": {k: v[0] / a.steps for k, v in tim.items()},
