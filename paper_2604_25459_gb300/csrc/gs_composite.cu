@@ -513,7 +513,9 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         sB[s] = make_float4(q1.x, q1.y, q1.z, 0.0f);
                         sD[s] = make_float4(cx * k, cy * k, cz * k, 0.0f);
                     } else {
-                        sB[s] = make_float4(q1.x, q1.y, q1.z, log2f(255.0f * q0.z));  // alpha >= 1/255 iff q <= w
+                        // alpha >= 1/255 iff q <= w (w only feeds the subtile cull, whose
+                        // 1e-3 margin dwarfs the error of the fast logarithm)
+                        sB[s] = make_float4(q1.x, q1.y, q1.z, __log2f(255.0f * q0.z));
                     }
                     sC[s] = q2;
                     sR[s] = make_int4((int)(rx & 0xffffu), (int)((rx >> 16) - (rx & 0xffffu)), (int)(ry & 0xffffu),
