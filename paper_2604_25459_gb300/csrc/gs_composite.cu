@@ -319,10 +319,12 @@ __device__ __forceinline__ bool reaches_rect(const float4& A, const float4& B, f
         const float u = l11 * dy;
         return fmaf(t, t, u * u);
     };
-    // vertical edges dx = const: stationary dy = -l00 l01 dx / (l01^2 + l11^2)
-    const float kv = -l00 * l01 / fmaf(l01, l01, l11 * l11);
-    // horizontal edges dy = const: stationary dx = -l01 dy / l00
-    const float kh = -l01 / l00;
+    // vertical edges dx = const: stationary dy = -l00 l01 dx / (l01^2 + l11^2);
+    // horizontal edges dy = const: stationary dx = -l01 dy / l00.  Fast
+    // divisions: q is evaluated exactly at whatever point is used, and a
+    // stationary point off by a few ulp raises q only to second order.
+    const float kv = __fdividef(-l00 * l01, fmaf(l01, l01, l11 * l11));
+    const float kh = __fdividef(-l01, l00);
     const float q1 = q(ax, fminf(fmaxf(kv * ax, ay), by));
     const float q2 = q(bx, fminf(fmaxf(kv * bx, ay), by));
     const float q3 = q(fminf(fmaxf(kh * ay, ax), bx), ay);
