@@ -39,9 +39,9 @@ UNIT = "env-frames/s"
 # summarised in profiles/k_composite_c1.md (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 32-env launch, divided by 32), valid only for
 # the compositor sources it was taken on.
-COMPOSITE_TRAFFIC_PER_ENV = (0.719003e9 + 0.535910e9) / 32
+COMPOSITE_TRAFFIC_PER_ENV = (0.717772e9 + 0.535197e9) / 32
 COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu",)
-COMPOSITE_TRAFFIC_SHA = "82ee7c554287b1c0"
+COMPOSITE_TRAFFIC_SHA = "60dd69d518dec947"
 
 
 def _sources_sha(paths) -> str:
