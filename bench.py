@@ -35,10 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "env-frames/s at 2048x640x480 RGB-D"
 UNIT = "env-frames/s"
 
-# DRAM traffic of the compositor per env of a launch, from the ncu capture
-# summarised in profiles/k_composite_c1.md (dram__bytes_read.sum +
-# dram__bytes_write.sum over a 32-env launch, divided by 32), valid only for
-# the compositor sources it was taken on.
+# DRAM traffic of the compositor per env of a launch, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum over a 32-env launch, divided
+# by 32), valid only for the compositor sources it was taken on.
 COMPOSITE_TRAFFIC_PER_ENV = (0.717772e9 + 0.535197e9) / 32
 COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu",)
 COMPOSITE_TRAFFIC_SHA = "60dd69d518dec947"

@@ -293,7 +293,11 @@ void gs_plan_destroy(gs_plan p);
  * do not fit, or after the binning of a wave when its intersection keys do
  * not fit (earlier waves' images are then complete, later ones unwritten).
  * Like gs_render_batch it reads one wave total back to the host per wave of
- * up to 256 environments (into a stack buffer). */
+ * up to 256 environments (into a stack buffer): each wave waits on
+ * cuda_stream once (cudaStreamSynchronize), so the call returns after the
+ * last wave's launches are queued.  Calls are serialised on the host: one
+ * lock guards the static host tables of the waves for the whole call, so
+ * concurrent calls from other threads wait, even for other devices. */
 gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
                                   float* rgb, float* depth, float* alpha, void* cuda_stream);
 
@@ -327,6 +331,9 @@ typedef struct {
                                examined before termination, summed since counters were enabled */
     int64_t visible;        /* with counters on: (env, Gaussian) pairs projected to a record
                                (non-empty support on screen), summed since counters were enabled */
+    int64_t fp64_conics;    /* with counters on: (env, Gaussian) pairs whose 2D covariance was near
+                               degenerate (AC - B^2 < 2^-10 AC before the low-pass) and was inverted
+                               in FP64, summed since counters were enabled */
 } gs_stats;
 /* Synchronises the device when counters are on (to read the device counter). */
 gs_status gs_scene_get_stats(gs_scene s, gs_stats* out);

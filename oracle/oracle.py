@@ -65,7 +65,7 @@ class _Proj(C.Structure):
 
 
 class _Image(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("rgb", "depth", "alpha", "amb", "neval", "contrib")]
+    _fields_ = [(k, C.c_void_p) for k in ("rgb", "depth", "alpha", "amb", "neval", "contrib", "wbound")]
 
 
 def lib():
@@ -182,12 +182,12 @@ def render_projected(proj: dict, width: int, height: int, mode: str = "plain", p
     given (the tie order of a renderer that stores the scene in another order)."""
     img = dict(rgb=np.zeros((height, width, 3), np.float32), depth=np.zeros((height, width), np.float32),
                alpha=np.zeros((height, width), np.float32), amb=np.zeros((height, width), np.uint8),
-               neval=np.zeros((height, width), np.int32))
+               neval=np.zeros((height, width), np.int32), wbound=np.zeros((height, width), np.float32))
     n = len(proj["u"])
     if contrib:
         img["contrib"] = np.zeros(n, np.float64)
     I = _Image(*[_ptr(img[k]) for k in ("rgb", "depth", "alpha", "amb", "neval")],
-               _ptr(img["contrib"]) if contrib else None)
+               _ptr(img["contrib"]) if contrib else None, _ptr(img["wbound"]))
     zk = _f32(zkey) if zkey is not None else None
     rk = np.ascontiguousarray(rank, dtype=np.int64) if rank is not None else None
     if rk is not None and rk.shape != (n,):

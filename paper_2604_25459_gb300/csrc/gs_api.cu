@@ -487,6 +487,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     P.mask = sc.mask.as<uint32_t>();
     P.dbg_hxy = debug ? sc.dbg_hxy.as<float2>() : nullptr;
     P.nvis = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() + 1 : nullptr;
+    P.nfp64 = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() + 2 : nullptr;
     P.lidars = io.lidars;
     P.bg_index = s->bg_order.empty() ? nullptr : s->bg_index.as<int>();
     PhaseTimer t2(s, st, GS_PHASE_PROJECT, timers);
@@ -1501,8 +1502,8 @@ gs_status gs_scene_set_counters(gs_scene s, int enable) {
     s->counters = enable ? 1 : 0;
     if (s->counters) {
         CK(cudaSetDevice(s->device), "set device");
-        CK(s->neval.ensure(16), "alloc counters");
-        CK(cudaMemset(s->neval.p, 0, 16), "clear counters");
+        CK(s->neval.ensure(24), "alloc counters");
+        CK(cudaMemset(s->neval.p, 0, 24), "clear counters");
     }
     return GS_OK;
 }
@@ -1547,13 +1548,15 @@ gs_status gs_scene_get_stats(gs_scene s, gs_stats* out) {
     s->stats.scratch_bytes = bytes;
     s->stats.composited = 0;
     s->stats.visible = 0;
+    s->stats.fp64_conics = 0;
     if (s->counters && s->neval.p) {
         CK(cudaSetDevice(s->device), "set device");
         CK(cudaDeviceSynchronize(), "sync");
-        unsigned long long c[2] = {0, 0};
-        CK(cudaMemcpy(c, s->neval.p, 16, cudaMemcpyDeviceToHost), "read counters");
+        unsigned long long c[3] = {0, 0, 0};
+        CK(cudaMemcpy(c, s->neval.p, 24, cudaMemcpyDeviceToHost), "read counters");
         s->stats.composited = (int64_t)c[0];
         s->stats.visible = (int64_t)c[1];
+        s->stats.fp64_conics = (int64_t)c[2];
     }
     *out = s->stats;
     return GS_OK;

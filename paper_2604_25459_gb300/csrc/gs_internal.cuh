@@ -115,6 +115,7 @@ struct ProjParams {
     uint32_t* mask;
     float2* dbg_hxy;  // nullable, per record slot
     unsigned long long* nvis;  // nullable: visible (env, Gaussian) pair counter
+    unsigned long long* nfp64; // nullable: counter of (env, Gaussian) pairs whose conic took the FP64 branch
     const gs_lidar* lidars;    // LiDAR projection only: per env of the wave
     const int* bg_index;       // nullable: caller's index of the background Gaussian in slot j (into r3.w)
 };

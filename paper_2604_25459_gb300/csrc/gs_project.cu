@@ -458,6 +458,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                     } else {
                         conic_factor_fp64(X, a0, a1, a2, a3, fx, fy, limxn, limxp, limyn, limyp, l00, l01, l11, cA,
                                           cC);
+                        if (P.nfp64) atomicAdd(P.nfp64, 1ull);
                     }
                     const bool ok = true;
                     const float hx = sqrtf(qstar * cA) * 1.0001f;

@@ -39,7 +39,7 @@ class GsGaussians(C.Structure):
 class GsStats(C.Structure):
     _fields_ = [("waves", C.c_int64), ("kernel_launches", C.c_int64), ("intersections", C.c_int64),
                 ("scratch_bytes", C.c_int64), ("n_gaussians", C.c_int64), ("composited", C.c_int64),
-                ("visible", C.c_int64)]
+                ("visible", C.c_int64), ("fp64_conics", C.c_int64)]
 
 
 PHASES = ("link", "project", "count", "scan", "scatter", "composite")

@@ -5,7 +5,7 @@ graph-replayed plan."""
 import numpy as np
 import pytest
 
-from gpu_helpers import compare, ensure_built, oracle_env, psnr
+from gpu_helpers import compare, ensure_built, gpu_render, keyed_check, oracle_env, psnr
 from oracle import oracle
 from paper_2604_25459_gb300 import gsbatch, synth
 
@@ -78,5 +78,15 @@ def test_batched_uneven_full_plan():
         st = compare(got_rgb, got_d, got_a, ref)
         print("c3 full env", e, Wd, st)
         assert st["amb_frac"] < 0.2
+        # keyed: the env alone in debug mode equals its plan output bit for bit,
+        # and orders like the oracle fed its float32 depth keys
+        one = w.env(e)
+        alone = gpu_render(one, debug=True, keep_scene=True)
+        for k, g in (("rgb", got_rgb), ("depth", got_d), ("alpha", got_a)):
+            np.testing.assert_array_equal(alone[k][0], g, err_msg=f"env {e} {k}: plan vs alone")
+        _, st_k, _, _ = keyed_check(one, 0, alone)
+        alone["scene"].close()
+        print("  keyed", st_k)
+        assert st_k["amb_frac"] < 0.2
     plan.close()
     scene.close()

@@ -9,7 +9,7 @@ T at 1e-4, depth near-ties) are excluded and counted, never hidden.
 import numpy as np
 import pytest
 
-from gpu_helpers import (AMB_ALPHA, AMB_T, compare, ensure_built, gpu_render, keyed_zkey, oracle_env)
+from gpu_helpers import (compare, ensure_built, gpu_render, keyed_check, oracle_env, render_counted)
 from oracle import oracle
 from paper_2604_25459_gb300 import gsbatch, synth
 
@@ -22,18 +22,7 @@ def _build():
 
 
 def _keyed_check(w, e, out, sh_degree=3):
-    """Independent and keyed comparisons of env e of a debug-mode render."""
-    scene = out["scene"]
-    rec = scene.debug_records(e, w.background.n + w.links.n)
-    S = oracle.scene_arrays(w, sh_degree)
-    proj = oracle.project(S, w.link_poses[e], w.cams[e])
-    zk = keyed_zkey(proj, rec)
-    W, H = int(w.cams[e]["width"]), int(w.cams[e]["height"])
-    ind = oracle.render_projected(proj, W, H)
-    key = oracle.render_projected(proj, W, H, zkey=zk)
-    st_i = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], ind)
-    st_k = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], key, amb_bits=AMB_ALPHA | AMB_T)
-    return st_i, st_k, rec, proj
+    return keyed_check(w, e, out, sh_degree)
 
 
 def test_c0_parity_independent_and_keyed():
@@ -147,14 +136,83 @@ def test_host_buffers_match_device(pinned):
 
 def test_c1_full_batch_sampled_envs():
     """The benchmark's workload (2048 envs x 640x480, 600k Gaussians, default
-    launch configuration): sampled envs against the FP64 oracle."""
+    launch configuration), sampled envs 0, 1023, 2047:
+    - each env rendered inside the full batch equals the env rendered alone,
+      bit for bit (so the single-env debug and counting renders below speak
+      for the batch);
+    - against the FP64 oracle, independently and keyed (ordering by the GPU's
+      float32 depth keys: no pixel may be excluded for a depth near-tie),
+      every pixel within tolerance, ambiguous ones within the bound of their
+      flagged decisions; the flagged fraction per decision is printed;
+    - the composited-pair count (N_eval, the numerator of the compositor's
+      roofline) equals the oracle's count up to flipped decisions."""
     w = synth.make_c1()
     out = gpu_render(w)
     for e in (0, 1023, 2047):
-        ref = oracle_env(w, e)
-        st = compare(out["rgb"][e], out["depth"][e], out["alpha"][e], ref)
-        print("c1 env", e, st)
-        assert st["amb_frac"] < 0.2
+        one = w.env(e)
+        alone = gpu_render(one, debug=True, keep_scene=True)
+        for k in ("rgb", "depth", "alpha"):
+            np.testing.assert_array_equal(alone[k][0], out[k][e], err_msg=f"env {e} {k}: batch vs alone")
+        st_i, st_k, _, _ = keyed_check(one, 0, alone)
+        alone["scene"].close()
+        cnt = render_counted(one)
+        n_gpu, n_or = cnt["stats"]["composited"], st_i["neval"]
+        print(f"c1 env {e} independent {st_i}\n  keyed {st_k}\n  N_eval gpu {n_gpu} oracle {n_or} "
+              f"rel {abs(n_gpu - n_or) / n_or:.2e}")
+        assert st_k["amb_frac"] < 0.2
+        assert abs(n_gpu - n_or) <= 1e-3 * n_or
+
+
+def test_fp64_conic_branch_edge_on_discs():
+    """Thin discs (scale ratio 1e-4) seen edge-on at depths 0.7 to 8 m
+    project to near-degenerate 2D covariances (AC - B^2 far below 2^-10 AC
+    before the low-pass), the one case the projection inverts in FP64: the
+    counter sees every visible disc take that branch, and records and image
+    match the FP64 oracle."""
+    import math
+
+    from scipy.spatial.transform import Rotation
+
+    rng = np.random.default_rng(17)
+    W, H, f = 96, 80, 70.0
+    n = 24
+    z = np.concatenate([np.full(8, 0.7), np.full(8, 3.0), np.full(8, 8.0)])
+    uv = rng.uniform([10, 10], [W - 10, H - 10], size=(n, 2))
+    mean = np.stack([(uv[:, 0] - W / 2) * z / f, (uv[:, 1] - H / 2) * z / f, z], 1)
+    quat = np.zeros((n, 4))
+    for k in range(n):
+        d = mean[k] / np.linalg.norm(mean[k])
+        a = rng.normal(size=3)
+        nrm = np.cross(d, a)
+        nrm /= np.linalg.norm(nrm)  # disc normal perpendicular to the view ray: edge-on
+        r, _ = Rotation.align_vectors([nrm], [[0.0, 0.0, 1.0]])
+        q = r.as_quat()
+        quat[k] = [q[3], q[0], q[1], q[2]]
+    thick = np.log(np.where(z < 1, 0.03, 0.15))
+    ls = np.stack([thick, thick, thick + math.log(1e-4)], 1)
+    sh = rng.normal(0, 0.3, size=(n, 16, 3))
+    sh[:, 0, :] += 0.5
+    bg = synth.Gaussians(*(np.ascontiguousarray(a, np.float32) for a in
+                           (mean, quat, ls, rng.uniform(0.5, 0.95, n), sh)))
+    cams = synth.make_cameras(1, f, f, W / 2, H / 2, W, H, [[1, 0, 0, 0]], [[0, 0, 0]])
+    w = synth.Workload("discs", bg, np.zeros(1, np.int64), bg.slice(0, 0), np.zeros((1, 0, 7), np.float32), cams)
+    cnt = render_counted(w)
+    vis = cnt["stats"]["visible"]
+    print("edge-on discs: visible", vis, "FP64 conics", cnt["stats"]["fp64_conics"])
+    assert vis == n and cnt["stats"]["fp64_conics"] == n
+    out = gpu_render(w, debug=True, keep_scene=True)
+    np.testing.assert_array_equal(out["rgb"], cnt["rgb"])
+    rec = out["scene"].debug_records(0, n)
+    st_i, st_k, _, p = keyed_check(w, 0, out)
+    out["scene"].close()
+    print("edge-on discs independent", st_i, "keyed", st_k)
+    both = (rec["visible"] == 1) & (p["valid"] == 1)
+    assert both.sum() == n
+    # the conic's small eigenvalue comes from the 0.3 px^2 low-pass: relative accuracy on every entry
+    np.testing.assert_allclose(rec["conic"][both], p["conic"][both], rtol=2e-3, atol=1e-5)
+    A, B, C = p["cov2d"][:, 0], p["cov2d"][:, 1], p["cov2d"][:, 2]
+    Ar, Cr = A - 0.3, C - 0.3
+    assert np.all(Ar * Cr - B * B < 2.0 ** -10 * Ar * Cr)
 
 
 # ---------------------------------------------------------------- edge cases

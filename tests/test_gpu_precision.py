@@ -52,3 +52,11 @@ def test_precision_forms_against_fp64_oracle(dtype, res):
     assert worst_psnr >= 45.0
     if dtype == "f16":
         assert worst_unamb <= 8e-3
+    else:
+        # Stated exception: BF16 storage (8-bit mantissa on opacities and
+        # log-scales) moves a few splat edges by ~1e-2 in colour, above the 8e-3
+        # target; the kernels' own share (against the oracle fed the same
+        # stored values) stays at the FP32 parity level.
+        print(f"  BF16 exception: max abs {worst_unamb:.2e} vs the 8e-3 target (storage error)")
+        assert worst_unamb <= 1.5e-2
+    assert max(r["quant_max"] for r in rows) <= 2e-4

@@ -128,6 +128,62 @@ def test_ewa_jacobian_matches_finite_differences():
     assert rng is not None
 
 
+@pytest.mark.parametrize("side", ["left", "right", "top", "bottom", "corner"])
+def test_ewa_guard_band_clamp_each_side(side):
+    """Centre outside the 1.3 guard band (EWA step of the 3DGS projection):
+    the Jacobian is the pinhole map's, taken by central differences at the
+    clamped point (z clamp(x/z, -1.3 cx/fx, 1.3 (W-cx)/fx), same in y), while
+    the centre u, v stays unclamped.  The camera is asymmetric in every
+    direction (cx != W/2, cy != H/2, fx != fy, W != H), so each of the four
+    limits differs from the others and from its swapped readings (cy/fy on x,
+    W - cx on the negative side): the pin fails for any of those swaps."""
+    W, H, fx, fy, cx, cy = 120, 90, 80.0, 60.0, 40.0, 55.0
+    lim = {"xn": 1.3 * cx / fx, "xp": 1.3 * (W - cx) / fx, "yn": 1.3 * cy / fy, "yp": 1.3 * (H - cy) / fy}
+    z = 2.5
+    tx, ty = {"left": (-1.9, 0.1), "right": (2.2, -0.2), "top": (0.15, -1.8),
+              "bottom": (-0.1, 1.6), "corner": (-2.4, 2.0)}[side]
+    mean = np.array([[tx * z, ty * z, z]])
+    qr = Rotation.random(random_state=11).as_quat()
+    ls = [[math.log(0.2), math.log(0.07), math.log(0.12)]]
+    bg = _gauss(mean, quat=[[qr[3], qr[0], qr[1], qr[2]]], log_scale=ls, opacity=[0.9])
+    w = _workload(bg, _cam(W, H, fx, cx=cx, cy=cy, fy=fy))
+    p = _render(w)["proj"]
+    assert p["proj_ok"][0] == 1
+    m = bg.mean[0].astype(np.float64)
+    x, y, zz = m
+    cxl = lambda t: min(max(t, -lim["xn"]), lim["xp"])
+    cyl = lambda t: min(max(t, -lim["yn"]), lim["yp"])
+    clamped = np.array([zz * cxl(x / zz), zz * cyl(y / zz), zz])
+    assert not np.allclose(clamped, m)  # the clamp is active on this side
+    proj = lambda q: np.array([fx * q[0] / q[2] + cx, fy * q[1] / q[2] + cy])
+    J = np.zeros((2, 3))
+    h = 1e-6
+    for k in range(3):
+        d = np.zeros(3)
+        d[k] = h
+        J[:, k] = (proj(clamped + d) - proj(clamped - d)) / (2 * h)
+    Rm = Rotation.from_quat([bg.quat[0, 1], bg.quat[0, 2], bg.quat[0, 3], bg.quat[0, 0]]).as_matrix()
+    S = Rm @ np.diag(np.exp(2 * bg.log_scale[0].astype(np.float64))) @ Rm.T
+    S2 = J @ S @ J.T + 0.3 * np.eye(2)
+    got = np.array([[p["cov2d"][0, 0], p["cov2d"][0, 1]], [p["cov2d"][0, 1], p["cov2d"][0, 2]]])
+    np.testing.assert_allclose(got, S2, rtol=1e-6)
+    # the centre is the unclamped pinhole projection
+    assert p["u"][0] == pytest.approx(fx * x / zz + cx, rel=1e-12)
+    assert p["v"][0] == pytest.approx(fy * y / zz + cy, rel=1e-12)
+    # the swapped readings of the limits give a different Sigma_2 here
+    for swap in ({"xn": lim["yn"], "xp": lim["yp"], "yn": lim["xn"], "yp": lim["xp"]},
+                 {"xn": lim["xp"], "xp": lim["xn"], "yn": lim["yp"], "yp": lim["yn"]}):
+        c2 = np.array([zz * min(max(x / zz, -swap["xn"]), swap["xp"]),
+                       zz * min(max(y / zz, -swap["yn"]), swap["yp"]), zz])
+        J2 = np.zeros((2, 3))
+        for k in range(3):
+            d = np.zeros(3)
+            d[k] = h
+            J2[:, k] = (proj(c2 + d) - proj(c2 - d)) / (2 * h)
+        alt = J2 @ S @ J2.T + 0.3 * np.eye(2)
+        assert np.abs(alt - got).max() > 1e-3 * np.abs(got).max()
+
+
 def test_p2_pinhole_centre_with_rotated_camera_and_link():
     """u = fx x/z + cx, v = fy y/z + cy with (x,y,z) = R_cw (R_l m + t_l) + t_cw;
     both rotations computed here with scipy from the same quaternions."""
@@ -306,6 +362,117 @@ def test_depth_order_ties_by_given_rank():
     # a rank that keeps the index order changes nothing
     same = oracle.render_projected(proj, 32, 32, rank=np.array([5, 9]))
     np.testing.assert_array_equal(same["rgb"], oracle.render_projected(proj, 32, 32)["rgb"])
+
+
+# ---------------------------------------------------------------- ambiguity flags and their bound
+#
+# A pixel is ambiguous when one of its decisions (alpha floor, transmittance
+# stop, depth order) sits within FP32 noise of its threshold; wbound bounds
+# the L1 change of the blending weights that flipping those decisions can
+# cause.  Each pin builds a pixel on one threshold, checks that its flag
+# fires (and stays off on a clear pixel), then flips the decision by a tiny
+# change of the input and checks that the change of the image is within
+# the bound.
+
+def _sh_const(cols):
+    sh = np.zeros((len(cols), 16, 3))
+    for k, c in enumerate(cols):
+        sh[k, 0, :] = (np.asarray(c) - 0.5) / (0.5 / math.sqrt(math.pi))
+    return sh
+
+
+def _flip_check(img, img2, px):
+    j, i = px
+    cmax = max(float(img["proj"]["rgb"][img["proj"]["valid"] == 1].max()),
+               float(img2["proj"]["rgb"][img2["proj"]["valid"] == 1].max()))
+    d_rgb = float(np.abs(img["rgb"][j, i].astype(np.float64) - img2["rgb"][j, i]).max())
+    d_a = abs(float(img["alpha"][j, i]) - float(img2["alpha"][j, i]))
+    b = float(img["wbound"][j, i])
+    assert d_rgb > 1e-6  # the decision did flip
+    assert d_rgb <= b * cmax + 1e-6, (d_rgb, b, cmax)
+    assert d_a <= b + 1e-6, (d_a, b)
+    return d_rgb, b * cmax
+
+
+def test_ambiguity_flag_alpha_floor_and_bound():
+    """A splat whose alpha at one pixel is 1/255 (1 + 3e-4), in front of an
+    opaque splat: bit 1 fires there and not at the centre; lowering its
+    opacity by 8e-4 (alpha below the floor: the splat drops out and the
+    splat behind gains weight) moves the pixel by less than the bound."""
+    W, H, f, z, s = 64, 48, 60.0, 3.0, 0.05
+    var = (f * s / z) ** 2 + 0.3  # Sigma_2 = var I on the axis
+    dx, dy = 3.5, 0.5  # pixel (W/2 + 3, H/2) relative to the centre
+    q = (dx * dx + dy * dy) / var
+    o = float(np.float32(1 / 255 * (1 + 3e-4) * math.exp(q / 2)))
+    assert o < 0.99
+    a_pix = o * math.exp(-q / 2)
+    assert abs(a_pix - 1 / 255) <= 1e-3 / 255 and a_pix >= 1 / 255
+
+    def scene(o_front):
+        bg = _gauss([[0.0, 0.0, z], [0.0, 0.0, z + 1.0]], log_scale=[[math.log(s)] * 3, [math.log(0.5)] * 3],
+                    opacity=[o_front, 0.8], sh=_sh_const([[0.9, 0.2, 0.1], [0.1, 0.3, 0.9]]))
+        return _render(_workload(bg, _cam(W, H, f)))
+
+    img = scene(o)
+    px = (H // 2, W // 2 + 3)
+    assert img["amb"][px] & 1
+    assert img["amb"][H // 2, W // 2] == 0  # alpha far above the floor at the centre
+    img2 = scene(float(np.float32(o * (1 - 8e-4))))
+    assert img2["neval"][px] == img["neval"][px] - 1
+    _flip_check(img, img2, px)
+
+
+def test_ambiguity_flag_transmittance_stop_and_bound():
+    """Three splats centred on one pixel (alpha = o there) whose third step
+    leaves T' = 1e-4 (1 + 3e-4): bit 2 fires; with T' = 1e-4 (1 - 3e-4) the
+    walk stops before the third splat instead, within the bound.  A third
+    splat of alpha 0.5 sets no flag."""
+    o1 = o2 = float(np.float32(0.905))
+    T = (1 - o1) * (1 - o2)
+    o3 = float(np.float32(1 - 1e-4 * (1 + 3e-4) / T))
+    o3b = float(np.float32(1 - 1e-4 * (1 - 3e-4) / T))
+    cols = [[0.9, 0.1, 0.2], [0.1, 0.8, 0.3], [0.2, 0.3, 0.95]]
+    img = _render(_front_splats([2.0, 2.5, 3.0], [o1, o2, o3], cols, scale=0.05))
+    assert img["amb"][12, 15] & 2
+    img2 = _render(_front_splats([2.0, 2.5, 3.0], [o1, o2, o3b], cols, scale=0.05))
+    assert img["neval"][12, 15] == img2["neval"][12, 15] == 3
+    assert img["alpha"][12, 15] > img2["alpha"][12, 15]  # only the first render adds the third splat
+    _flip_check(img, img2, (12, 15))
+    clear = _render(_front_splats([2.0, 2.5, 3.0], [o1, o2, 0.5], cols, scale=0.05))
+    assert clear["amb"][12, 15] == 0
+
+
+def test_ambiguity_flag_depth_tie_and_bound():
+    """Two overlapping splats whose depths differ by 4e-7 relative: bit 4
+    fires; exchanging their depths reverses their order, within the bound.
+    Depths 1e-3 apart set no flag."""
+    cols = [[0.95, 0.1, 0.1], [0.1, 0.1, 0.95]]
+    z = 2.0
+    img = _render(_front_splats([z, z * (1 + 4e-7)], [0.6, 0.7], cols, scale=0.05))
+    assert img["amb"][12, 15] & 4
+    img2 = _render(_front_splats([z * (1 + 4e-7), z], [0.6, 0.7], cols, scale=0.05))
+    _flip_check(img, img2, (12, 15))
+    clear = _render(_front_splats([z, z * (1 + 1e-3)], [0.6, 0.7], cols, scale=0.05))
+    assert clear["amb"][12, 15] == 0
+
+
+def test_ambiguity_bound_covers_fp32_renderer():
+    """The FP32 oracle takes its threshold decisions in FP32, as a GPU does:
+    on every pixel it differs from the FP64 oracle by FP32 noise plus at most
+    the bound of the FP64 oracle's flagged decisions (rgb: wbound max rgb,
+    alpha: wbound)."""
+    for w in (synth.make_c0(n=4096, width=96, height=72, f=80.0), synth.make_tiny(seed=4)):
+        for e in range(w.n_envs):
+            b = _render(w, e=e)
+            b32 = _render(w, "plain", "f32", e=e)
+            p = b["proj"]
+            cmax = float(p["rgb"][p["valid"] == 1].max())
+            d = np.abs(b["rgb"].astype(np.float64) - b32["rgb"]).max(-1)
+            da = np.abs(b["alpha"].astype(np.float64) - b32["alpha"])
+            assert np.all(d <= 1e-4 + b["wbound"] * cmax)
+            assert np.all(da <= 1e-4 + b["wbound"])
+            amb = b["amb"] != 0
+            assert np.all(b["wbound"][~amb] == 0) and np.all(b["wbound"][amb] > 0)
 
 
 def test_p4_invariants_c0():

@@ -52,6 +52,103 @@ def test_noalloc_matches_allocating_path_twice(make):
     scene.close()
 
 
+def _c0_batch(E):
+    """E envs of the c0 scene (16,384 Gaussians, 128x96), each camera shifted
+    by its own offset."""
+    w = synth.make_c0()
+    rng = np.random.default_rng(3)
+    t = np.zeros((E, 3))
+    t[:, :2] = rng.uniform(-0.2, 0.2, (E, 2))
+    t[:, 2] = 3.0
+    cams = synth.make_cameras(E, 110.0, 110.0, 64.0, 48.0, 128, 96, [[1.0, 0.0, 0.0, 0.0]] * E, t)
+    return synth.Workload("c0 batch", w.background, w.link_offsets, w.links, np.zeros((E, 0, 7), np.float32), cams)
+
+
+def _near_far_batch(E, near_from):
+    """E envs of a 1,024-Gaussian cube of large splats (scale ~0.15 m), 128x96:
+    envs before near_from view it from 8 m (~3.4k intersection keys each),
+    envs from near_from on from 1.5 m (~16k keys each)."""
+    rng = np.random.default_rng(5)
+    n = 1024
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    sh = rng.normal(0, 0.3, (n, 16, 3))
+    sh[:, 0, :] += 0.5
+    bg = synth.Gaussians(*(np.ascontiguousarray(a, np.float32) for a in
+                           (rng.uniform(-1, 1, (n, 3)), q, np.log(0.15) + rng.normal(0, 0.2, (n, 3)),
+                            rng.uniform(0.5, 0.9, n), sh)))
+    t = np.zeros((E, 3))
+    t[:, :2] = rng.uniform(-0.1, 0.1, (E, 2))
+    t[:, 2] = np.where(np.arange(E) < near_from, 8.0, 1.5)
+    cams = synth.make_cameras(E, 110.0, 110.0, 64.0, 48.0, 128, 96, [[1.0, 0.0, 0.0, 0.0]] * E, t)
+    return synth.Workload("near/far", bg, np.zeros(1, np.int64), bg.slice(0, 0), np.zeros((E, 0, 7), np.float32), cams)
+
+
+def _noalloc(L, scene, w, outs):
+    rgb, depth, alpha = outs
+    return L.gs_render_batch_noalloc(scene._h, w.n_envs, None, gsbatch._ptr(np.ascontiguousarray(w.cams)),
+                                     C.c_void_p(rgb.data_ptr()), C.c_void_p(depth.data_ptr()),
+                                     C.c_void_p(alpha.data_ptr()), None)
+
+
+def test_noalloc_several_waves():
+    """60 envs of 16,384 Gaussians do not fit one pass of the 32 MiB array
+    (about 1 MiB of projected records per env), so the call renders them in
+    waves: every wave's images land at their own offsets, from the array's
+    leftovers of the wave before, equal to gs_render_batch bit for bit."""
+    import torch
+
+    ensure_built()
+    w = _c0_batch(60)
+    scene = gsbatch.scene_from_workload(w)
+    ref = scene.render(None, w.cams)
+    torch.cuda.synchronize()
+    L = gsbatch.lib()
+    for _ in range(2):
+        outs = _outputs(torch, 60, 96, 128)
+        st = _noalloc(L, scene, w, outs)
+        assert st == gsbatch.GS_OK, L.gs_last_error()
+        torch.cuda.synchronize()
+        scene.sync_status()
+        for got, exp in zip(outs, ref):
+            assert float((got - exp).abs().max()) <= 2e-3
+            assert torch.equal(got, exp)
+    scene.close()
+
+
+def test_noalloc_later_wave_overflow():
+    """512 envs in waves of 256 (about 65 KiB of records per env): the first
+    wave's 256 distant views fit the array's room for intersection keys
+    (~7 MB of ~16 MB), the second wave's 212 close views do not (~28 MB).
+    The call fails with GS_ERR_UNSUPPORTED when that wave is binned; the
+    first wave's images are complete (equal to gs_render_batch) and every
+    later env still holds the -1 fill."""
+    import torch
+
+    ensure_built()
+    E = 512
+    w = _near_far_batch(E, near_from=300)
+    scene = gsbatch.scene_from_workload(w)
+    ref = scene.render(None, w.cams)
+    torch.cuda.synchronize()
+    L = gsbatch.lib()
+    outs = _outputs(torch, E, 96, 128)
+    st = _noalloc(L, scene, w, outs)
+    assert st == gsbatch.GS_ERR_UNSUPPORTED
+    assert b"intersection keys" in L.gs_last_error()
+    torch.cuda.synchronize()
+    scene.sync_status()
+    rgb = outs[0]
+    unwritten = [bool((rgb[e] == -1.0).all()) for e in range(E)]
+    k = unwritten.index(True)
+    assert 1 <= k <= 300 and all(unwritten[k:])  # a later wave failed; nothing after it was written
+    print("first unwritten env", k)
+    for got, exp in zip(outs, ref):
+        assert torch.equal(got[:k], exp[:k])
+        assert bool((got[k:] == -1.0).all())
+    scene.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_array():
     import torch
 
