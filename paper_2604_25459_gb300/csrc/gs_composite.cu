@@ -301,6 +301,41 @@ __device__ __forceinline__ float splat_alpha(const float4& A, const float4& B, f
     return fminf(0.99f, __fmul_rn(A.z, ex2_approx(pw)));
 }
 
+// The same alpha at a lane's two pixel centres (fpx, fpy.x) and (fpx, fpy.y),
+// with the paired FP32 instructions of sm_100+ (two round-to-nearest
+// operations per instruction, element for element the arithmetic of
+// splat_alpha, so the values are bit-identical).
+__device__ __forceinline__ float2 splat_alpha2(const float4& A, const float4& B, float fpx, float2 fpy) {
+    const float dx = fpx - A.x;
+    const float2 dy = __fadd2_rn(fpy, make_float2(-A.y, -A.y));
+    const float bx = __fmul_rn(B.x, dx);
+    const float2 t = __ffma2_rn(make_float2(B.y, B.y), dy, make_float2(bx, bx));
+    const float2 s = __fmul2_rn(make_float2(B.z, B.z), dy);
+    const float2 q = __ffma2_rn(t, t, __fmul2_rn(s, s));
+    const float2 a = __fmul2_rn(make_float2(A.z, A.z), make_float2(ex2_approx(-q.x), ex2_approx(-q.y)));
+    return make_float2(fminf(0.99f, a.x), fminf(0.99f, a.y));
+}
+
+// blend() for a lane's two pixels at once: pixel k takes the splat where uk
+// is set.  A pixel that does not take it keeps its state exactly (its weight
+// is 0, and fma(0, c, x) = x for the finite, non-negative sums here).  Returns
+// the sum of the two weights added.
+__device__ __forceinline__ float blend2(float2 al, bool u0, bool u1, const float4& C, float z, float2& T, float2& r,
+                                        float2& g, float2& b, float2& d, bool& done0, bool& done1) {
+    const float2 am = make_float2(u0 ? al.x : 0.0f, u1 ? al.y : 0.0f);
+    const float2 Tn = __fmul2_rn(T, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am.x, -am.y)));
+    const bool s0 = u0 && Tn.x < 1e-4f, s1 = u1 && Tn.y < 1e-4f;
+    done0 = done0 || s0;
+    done1 = done1 || s1;
+    const float2 w = __fmul2_rn(make_float2(s0 ? 0.0f : am.x, s1 ? 0.0f : am.y), T);
+    r = __ffma2_rn(w, make_float2(C.x, C.x), r);
+    g = __ffma2_rn(w, make_float2(C.y, C.y), g);
+    b = __ffma2_rn(w, make_float2(C.z, C.z), b);
+    d = __ffma2_rn(w, make_float2(z, z), d);
+    T = make_float2(s0 ? T.x : Tn.x, s1 ? T.y : Tn.y);
+    return w.x + w.y;
+}
+
 // Whether a splat can reach alpha >= 1/255 at any pixel centre of the 8x8
 // subtile whose first centre is (x0, y0): the minimum of its quadratic form
 // q = (l00 dx + l01 dy)^2 + (l11 dy)^2 over the rectangle spanned by the
@@ -455,8 +490,9 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         al = ts > near_range ? fminf(0.99f, A.w * ex2_approx(-0.72134752044448170f * q)) : 0.0f;
     };
     bool done0 = !in0, done1 = !in1;
-    float T0 = 1.0f, r0 = 0.0f, g0 = 0.0f, b0 = 0.0f, d0 = 0.0f;
-    float T1 = 1.0f, r1 = 0.0f, g1 = 0.0f, b1 = 0.0f, d1 = 0.0f;
+    // the lane's two pixels: .x = (px, py0), .y = (px, py1)
+    float2 Tp = make_float2(1.0f, 1.0f), rp = make_float2(0.0f, 0.0f), gp = rp, bp = rp, dp = rp;
+    const float2 fpy = make_float2(fpy0, fpy1);
     uint32_t ncomp = 0;
 
     uint32_t n = P.counts[tile_base + t];
@@ -582,54 +618,37 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             const float4 none = make_float4(0.f, 0.f, 0.f, 0.f);
                             if (h10 && a10 >= (1.0f / 255.0f)) {
                                 if constexpr (CNT) ++ncomp;
-                                blend(a10, none, t10, T0, r0, g0, b0, d0, done0);
+                                blend(a10, none, t10, Tp.x, rp.x, gp.x, bp.x, dp.x, done0);
                             }
                             if (h11 && a11 >= (1.0f / 255.0f)) {
                                 if constexpr (CNT) ++ncomp;
-                                blend(a11, none, t11, T1, r1, g1, b1, d1, done1);
+                                blend(a11, none, t11, Tp.y, rp.y, gp.y, bp.y, dp.y, done1);
                             }
                             if (h20 && !done0 && a20 >= (1.0f / 255.0f)) {
                                 if constexpr (CNT) ++ncomp;
-                                blend(a20, none, t20, T0, r0, g0, b0, d0, done0);
+                                blend(a20, none, t20, Tp.x, rp.x, gp.x, bp.x, dp.x, done0);
                             }
                             if (h21 && !done1 && a21 >= (1.0f / 255.0f)) {
                                 if constexpr (CNT) ++ncomp;
-                                blend(a21, none, t21, T1, r1, g1, b1, d1, done1);
+                                blend(a21, none, t21, Tp.y, rp.y, gp.y, bp.y, dp.y, done1);
                             }
                         } else if (MODE != 1 && (h10 || h11 || h20 || h21)) {
                             const float4 A1 = sA[j1], B1 = sB[j1];
                             const float4 A2 = sA[j2], B2 = sB[j2];
-                            const float dx1 = fpx - A1.x, dx2 = fpx - A2.x;
-                            const float a10 = splat_alpha(A1, B1, dx1, fpy0 - A1.y);
-                            const float a11 = splat_alpha(A1, B1, dx1, fpy1 - A1.y);
-                            const float a20 = splat_alpha(A2, B2, dx2, fpy0 - A2.y);
-                            const float a21 = splat_alpha(A2, B2, dx2, fpy1 - A2.y);
-                            const bool u10 = h10 && a10 >= (1.0f / 255.0f);
-                            const bool u11 = h11 && a11 >= (1.0f / 255.0f);
+                            const float2 a1 = splat_alpha2(A1, B1, fpx, fpy);
+                            const float2 a2 = splat_alpha2(A2, B2, fpx, fpy);
+                            const bool u10 = h10 && a1.x >= (1.0f / 255.0f);
+                            const bool u11 = h11 && a1.y >= (1.0f / 255.0f);
                             float w1 = 0.0f, w2 = 0.0f;
                             if (u10 || u11) {
-                                const float4 C1 = sC[j1];
-                                if (u10) {
-                                    if constexpr (CNT) ++ncomp;
-                                    w1 += blend(a10, C1, A1.w, T0, r0, g0, b0, d0, done0);
-                                }
-                                if (u11) {
-                                    if constexpr (CNT) ++ncomp;
-                                    w1 += blend(a11, C1, A1.w, T1, r1, g1, b1, d1, done1);
-                                }
+                                if constexpr (CNT) ncomp += (uint32_t)u10 + (uint32_t)u11;
+                                w1 = blend2(a1, u10, u11, sC[j1], A1.w, Tp, rp, gp, bp, dp, done0, done1);
                             }
-                            const bool u20 = h20 && !done0 && a20 >= (1.0f / 255.0f);
-                            const bool u21 = h21 && !done1 && a21 >= (1.0f / 255.0f);
+                            const bool u20 = h20 && !done0 && a2.x >= (1.0f / 255.0f);
+                            const bool u21 = h21 && !done1 && a2.y >= (1.0f / 255.0f);
                             if (u20 || u21) {
-                                const float4 C2 = sC[j2];
-                                if (u20) {
-                                    if constexpr (CNT) ++ncomp;
-                                    w2 += blend(a20, C2, A2.w, T0, r0, g0, b0, d0, done0);
-                                }
-                                if (u21) {
-                                    if constexpr (CNT) ++ncomp;
-                                    w2 += blend(a21, C2, A2.w, T1, r1, g1, b1, d1, done1);
-                                }
+                                if constexpr (CNT) ncomp += (uint32_t)u20 + (uint32_t)u21;
+                                w2 = blend2(a2, u20, u21, sC[j2], A2.w, Tp, rp, gp, bp, dp, done0, done1);
                             }
                             if constexpr (SC) score_pair = make_float2(w1, w2);
                         }
@@ -930,19 +949,19 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     if (MODE == 1) {  // range and hit per ray
         if (in0) {
             const size_t pix = pix_base + (size_t)py0 * W + px;
-            const float a = 1.0f - T0;
-            P.depth[pix] = a > 0.0f ? d0 / a : 0.0f;
+            const float a = 1.0f - Tp.x;
+            P.depth[pix] = a > 0.0f ? dp.x / a : 0.0f;
             if (P.alpha) P.alpha[pix] = a;
         }
         if (in1) {
             const size_t pix = pix_base + (size_t)py1 * W + px;
-            const float a = 1.0f - T1;
-            P.depth[pix] = a > 0.0f ? d1 / a : 0.0f;
+            const float a = 1.0f - Tp.y;
+            P.depth[pix] = a > 0.0f ? dp.y / a : 0.0f;
             if (P.alpha) P.alpha[pix] = a;
         }
     } else if (!SC) {
-        if (in0) store(py0, T0, r0, g0, b0, d0);
-        if (in1) store(py1, T1, r1, g1, b1, d1);
+        if (in0) store(py0, Tp.x, rp.x, gp.x, bp.x, dp.x);
+        if (in1) store(py1, Tp.y, rp.y, gp.y, bp.y, dp.y);
     }
     __syncthreads();  // shared staging is reused by the next item
     }  // items of the claim
