@@ -55,6 +55,7 @@ struct gs_plan_s {
     std::vector<gs_camera> cams;
     int flags = 0;
     int tile_w = 16, tile_h = 16, chunk = 1;
+    int quad = 0;  // compositor's quadrant form (16x16 tiles), chosen by the autotuner
     Scratch sc;
     struct Wave {
         int e0, e1;
@@ -441,8 +442,19 @@ gs_status upload_tables(gs_scene s, const std::vector<EnvSpec>& specs, int e0, i
 // and flagged in the status word.
 gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& io, int tw, int th, int chunk,
                    unsigned long long cap, cudaStream_t st, bool timers, int64_t* launches,
-                   unsigned long long* total_out) {
+                   unsigned long long* total_out, int quad) {
     const int We = wt.We;
+    bool use_quad = false;
+    if (tw == 16 && th == 16 && !io.lidars && !io.score) {
+        if (quad < 0) {
+            long long most = 0;
+            for (int e = 0; e < We; ++e)
+                most = std::max(most, (long long)wt.host_envs[e].W * wt.host_envs[e].H);
+            use_quad = most <= kQuadMaxPixels;
+        } else {
+            use_quad = quad != 0;
+        }
+    }
     CK(sc.xf.ensure(sizeof(LinkXf) * (size_t)std::max(wt.xf_items, 1)), "alloc link table");
     CK(sc.r0.ensure(wt.recs * 16), "alloc records");
     CK(sc.r1.ensure(wt.recs * 16), "alloc records");
@@ -607,6 +619,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.neval = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() : nullptr;
         C.tile_w = tw;
         C.tile_h = th;
+        C.quad = use_quad ? 1 : 0;
         C.rgb = io.rgb;
         C.depth = io.depth;
         C.alpha = io.alpha;
@@ -940,7 +953,7 @@ gs_status plan_eager(gs_plan p, const std::vector<EnvSpec>& specs, const float* 
         WaveTables wt = plan_wave_tables(p, i, host);
         unsigned long long tot = 0;
         ST(run_wave(s, p->sc, wt, WaveIO{poses, rgb, depth, alpha, 0}, p->tile_w, p->tile_h, p->chunk, 0, st, false,
-                    &launches, &tot));
+                    &launches, &tot, p->quad));
         totals->push_back(tot);
     }
     return GS_OK;
@@ -960,7 +973,7 @@ gs_status plan_enqueue(gs_plan p, const std::vector<EnvSpec>& specs, const float
                           host.data(), dummy.data(), &nb, 0);
         WaveTables wt = plan_wave_tables(p, i, host);
         ST(run_wave(s, p->sc, wt, WaveIO{poses, rgb, depth, alpha, 0}, p->tile_w, p->tile_h, p->chunk, w.cap, st,
-                    false, &launches, nullptr));
+                    false, &launches, nullptr, p->quad));
     }
     return GS_OK;
 }
@@ -1334,15 +1347,18 @@ gs_status gs_plan_launch(gs_plan p, const float* link_poses, float* rgb, float* 
     if (!p->tuned) {
         // eager warm-up: autotune (tile shape x claim size) and size the key capacity
         struct Cand {
-            int tw, th, chunk;
+            int tw, th, chunk, quad;
         };
         std::vector<Cand> cands;
         if (p->flags & GS_PLAN_AUTOTUNE) {
             const int shapes[5][2] = {{16, 16}, {32, 8}, {16, 8}, {8, 8}, {32, 16}};
             for (auto& sh : shapes)
-                for (int ch : {1, 4}) cands.push_back({sh[0], sh[1], ch});
+                for (int ch : {1, 4}) {
+                    cands.push_back({sh[0], sh[1], ch, 0});
+                    if (sh[0] == 16 && sh[1] == 16) cands.push_back({16, 16, ch, 1});
+                }
         } else {
-            cands.push_back({p->tile_w, p->tile_h, 1});
+            cands.push_back({p->tile_w, p->tile_h, 1, 0});
         }
         cudaEvent_t a, b;
         CK(cudaEventCreate(&a), "event");
@@ -1355,6 +1371,7 @@ gs_status gs_plan_launch(gs_plan p, const float* link_poses, float* rgb, float* 
             p->tile_w = c.tw;
             p->tile_h = c.th;
             p->chunk = c.chunk;
+            p->quad = c.quad;
             ST(plan_tables(p, specs));
             std::vector<unsigned long long> tot;
             ST(plan_eager(p, specs, link_poses, rgb, depth, alpha, st, &tot));  // warm (sizes buffers)
@@ -1375,6 +1392,7 @@ gs_status gs_plan_launch(gs_plan p, const float* link_poses, float* rgb, float* 
         p->tile_w = bestc.tw;
         p->tile_h = bestc.th;
         p->chunk = bestc.chunk;
+        p->quad = bestc.quad;
         p->tuned_candidates = (int)cands.size();
         p->tuned_ms = best;
         ST(plan_tables(p, specs));
@@ -1425,6 +1443,7 @@ gs_status gs_plan_get_info(gs_plan p, gs_plan_info* out) {
     i.tile_w = p->tile_w;
     i.tile_h = p->tile_h;
     i.chunk = p->chunk;
+    i.quad = p->quad;
     i.waves = (int)p->waves.size();
     i.graph = p->exec != nullptr;
     i.tuned_candidates = p->tuned_candidates;

@@ -291,6 +291,12 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Sum of one float per lane over each group of eight lanes.
+__device__ __forceinline__ float group_sum(float v) {
+    for (int d = 4; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
 // alpha = min(0.99, o exp(-q/2)) = min(0.99, o 2^-((l00 dx + l01 dy)^2 + (l11 dy)^2))
 // where B = (l00, l01, l11) is the conic's upper Cholesky factor scaled by
 // sqrt(log2(e)/2): q is evaluated as a sum of two squares.
@@ -389,7 +395,15 @@ __device__ __forceinline__ bool reaches_rect(const float4& A, const float4& B, f
 // the (azimuth, beam) grid, the Gaussian evaluated at its closest approach).
 // MODE 2: the camera form that also counts composited (pixel, splat) pairs
 // into P.neval (MODE 0 leaves the count out of its blend loop).
-template <int TW, int TH, bool SC = false, int MODE = 0>
+// QUAD: each group of eight lanes owns a 4x4 quadrant of the warp's subtile
+// and walks only the splats whose box reaches that quadrant, dropping it once
+// the quadrant's pixels have terminated.  Small splats (low resolutions)
+// reach one quadrant, so the groups then advance through different splats at
+// once; large ones reach all four and the extra votes only cost (measured on
+// the 2048-env room workload: 64x64 -21 %, 128x128 -15 %, 320x240 -3 %,
+// 640x480 +1.4 % compositing time).  Every pixel still composites the same
+// splats in the same order, so the images are identical either way.
+template <int TW, int TH, bool SC = false, int MODE = 0, bool QUAD = false>
 __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 256 ? 8 : 12))) k_composite(CompParams P) {
     constexpr int NT = TW * TH / 2;
     constexpr int NB = NT;  // splats staged per batch (one per thread)
@@ -456,7 +470,13 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     constexpr int SWX = TW / 8;
     const int wx0 = tx * TW + (warp % SWX) * 8, wy0 = ty * TH + (warp / SWX) * 8;
     const int wx1 = wx0 + 7, wy1 = wy0 + 7;
-    const int px = wx0 + (lane & 7), py0 = wy0 + (lane >> 3), py1 = py0 + 4;
+    // QUAD: lanes in groups of eight, group q = lane / 8 owning the 4x4 quadrant
+    // (q & 1, q >> 1) of the warp's subtile, each lane a column and rows r, r + 2;
+    // otherwise lane = column (lane % 8) and rows lane / 8, lane / 8 + 4
+    const int grp = lane >> 3, l8 = lane & 7;
+    const int px = QUAD ? wx0 + 4 * (grp & 1) + (l8 & 3) : wx0 + (lane & 7);
+    const int py0 = QUAD ? wy0 + 4 * (grp >> 1) + (l8 >> 2) : wy0 + (lane >> 3);
+    const int py1 = QUAD ? py0 + 2 : py0 + 4;
     const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
     const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f, fpy1 = (float)py1 + 0.5f;
     float3 dir0 = make_float3(0.f, 0.f, 0.f), dir1 = dir0;  // LiDAR: the lane's two rays
@@ -580,12 +600,33 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         if (MODE != 1 && ov && R.y + R.w >= 24)
                             ov = reaches_rect(sA[j], sB[j], (float)wx0 + 0.5f, (float)wy0 + 0.5f);
                     }
-                    uint32_t m = __ballot_sync(0xffffffffu, ov);
+                    uint32_t m;
+                    if constexpr (QUAD) {
+                        // per quadrant: the splats whose box reaches it
+                        bool qa = false, qb = false, qc = false, qd = false;
+                        if (ov) {
+                            const int4 R = sR[j];
+                            const bool c0 = R.x <= wx0 + 3, c1 = R.x + R.y >= wx0 + 4;
+                            const bool r0 = R.z <= wy0 + 3, r1 = R.z + R.w >= wy0 + 4;
+                            qa = c0 && r0;
+                            qb = c1 && r0;
+                            qc = c0 && r1;
+                            qd = c1 && r1;
+                        }
+                        const uint32_t ma = __ballot_sync(0xffffffffu, qa), mb = __ballot_sync(0xffffffffu, qb);
+                        const uint32_t mc = __ballot_sync(0xffffffffu, qc), md = __ballot_sync(0xffffffffu, qd);
+                        const uint32_t dm = __ballot_sync(0xffffffffu, done0 && done1);
+                        m = grp == 0 ? ma : (grp == 1 ? mb : (grp == 2 ? mc : md));
+                        if (((dm >> (8 * grp)) & 0xffu) == 0xffu) m = 0u;
+                    } else {
+                        m = __ballot_sync(0xffffffffu, ov);
+                    }
                     float2 score_pair = make_float2(0.0f, 0.0f);  // contribution pass only
                     // two splats per iteration: their four alpha evaluations are
                     // independent; the blends then run in depth order
-                    while (m) {
-                        const int k1 = __ffs(m) - 1;
+                    while (QUAD ? __any_sync(0xffffffffu, m != 0u) : m != 0u) {
+                        const bool one = !QUAD || m != 0u;
+                        const int k1 = one ? __ffs(m) - 1 : 0;
                         m &= m - 1u;
                         const bool two = m != 0u;
                         const int k2 = two ? __ffs(m) - 1 : k1;
@@ -596,7 +637,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         // below 1/255 and the alpha test alone rejects it.  LiDAR rays
                         // keep the test (their grid box is a looser cone bound and a ray
                         // evaluation costs more).
-                        bool h10 = !done0, h11 = !done1, h20 = two && !done0, h21 = two && !done1;
+                        bool h10 = one && !done0, h11 = one && !done1, h20 = two && !done0, h21 = two && !done1;
                         if constexpr (MODE == 1) {
                             const int4 R1 = sR[j1];
                             const int4 R2 = sR[j2];
@@ -653,10 +694,12 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             if constexpr (SC) score_pair = make_float2(w1, w2);
                         }
                         if constexpr (SC) {  // warp-uniform: every lane reaches this point
-                            const float s1 = warp_sum(score_pair.x), s2 = warp_sum(score_pair.y);
+                            // the lanes that walk the same splats add their weights
+                            const float s1 = QUAD ? group_sum(score_pair.x) : warp_sum(score_pair.x);
+                            const float s2 = QUAD ? group_sum(score_pair.y) : warp_sum(score_pair.y);
                             score_pair = make_float2(0.0f, 0.0f);
-                            if (lane == 0) {
-                                if (s1 > 0.0f) atomicAdd(P.score + score_index(sG[j1]), s1);
+                            if (QUAD ? l8 == 0 : lane == 0) {
+                                if (one && s1 > 0.0f) atomicAdd(P.score + score_index(sG[j1]), s1);
                                 if (two && s2 > 0.0f) atomicAdd(P.score + score_index(sG[j2]), s2);
                             }
                         }
@@ -970,7 +1013,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     }  // claims
 }
 
-template <int TW, int TH, bool SC = false, int MODE = 0>
+template <int TW, int TH, bool SC = false, int MODE = 0, bool QUAD = false>
 static cudaError_t resident_ctas(int* out) {
     constexpr int NT = TW * TH / 2;
     static int per_sm[64] = {0};  // resident CTAs per SM, per device
@@ -981,7 +1024,7 @@ static cudaError_t resident_ctas(int* out) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (per_sm[dev] == 0) {
         int ps = 0, n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_composite<TW, TH, SC, MODE>, NT, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_composite<TW, TH, SC, MODE, QUAD>, NT, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -992,11 +1035,11 @@ static cudaError_t resident_ctas(int* out) {
     return cudaSuccess;
 }
 
-template <int TW, int TH, bool SC = false, int MODE = 0>
+template <int TW, int TH, bool SC = false, int MODE = 0, bool QUAD = false>
 static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas) {
     constexpr int NT = TW * TH / 2;
     int full = 0;
-    cudaError_t e = resident_ctas<TW, TH, SC, MODE>(&full);
+    cudaError_t e = resident_ctas<TW, TH, SC, MODE, QUAD>(&full);
     if (e != cudaSuccess) return e;
     const unsigned items = P.item_end - P.item_begin;
     unsigned grid = (unsigned)full;
@@ -1005,7 +1048,7 @@ static cudaError_t launch_tiles(const CompParams& P, cudaStream_t st, int* ctas)
     if (P.spill && grid > P.spill_ctas) grid = P.spill_ctas;
     if (grid == 0) grid = 1;
     *ctas = (int)grid;
-    k_composite<TW, TH, SC, MODE><<<grid, NT, 0, st>>>(P);
+    k_composite<TW, TH, SC, MODE, QUAD><<<grid, NT, 0, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -1022,6 +1065,10 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
         if (P.tile_w != 16 || P.tile_h != 16) return cudaErrorInvalidValue;
         return launch_tiles<16, 16, true>(P, st, ctas);
     }
+    if (P.quad && P.tile_w == 16 && P.tile_h == 16) {  // quadrant lists (16x16 camera tiles)
+        if (P.neval) return launch_tiles<16, 16, false, 2, true>(P, st, ctas);
+        return launch_tiles<16, 16, false, 0, true>(P, st, ctas);
+    }
     if (P.neval) {  // counting pass
         if (P.tile_w == 16 && P.tile_h == 16) return launch_tiles<16, 16, false, 2>(P, st, ctas);
         if (P.tile_w == 32 && P.tile_h == 16) return launch_tiles<32, 16, false, 2>(P, st, ctas);
@@ -1037,7 +1084,13 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
 }
 
 cudaError_t composite_max_ctas(int tile_w, int tile_h, int* ctas) {
-    if (tile_w == 16 && tile_h == 16) return resident_ctas<16, 16>(ctas);
+    if (tile_w == 16 && tile_h == 16) {
+        int a = 0, b = 0;
+        cudaError_t e = resident_ctas<16, 16>(&a);
+        if (e == cudaSuccess) e = resident_ctas<16, 16, false, 0, true>(&b);
+        *ctas = a > b ? a : b;
+        return e;
+    }
     if (tile_w == 32 && tile_h == 16) return resident_ctas<32, 16>(ctas);
     if (tile_w == 8 && tile_h == 8) return resident_ctas<8, 8>(ctas);
     if (tile_w == 16 && tile_h == 8) return resident_ctas<16, 8>(ctas);

@@ -52,7 +52,7 @@ class GsTimings(C.Structure):
 class GsPlanInfo(C.Structure):
     _fields_ = [("tile_w", C.c_int), ("tile_h", C.c_int), ("chunk", C.c_int), ("waves", C.c_int),
                 ("graph", C.c_int), ("tuned_candidates", C.c_int), ("tuned_ms", C.c_double), ("regrows", C.c_int),
-                ("key_capacity", C.c_int64), ("scratch_bytes", C.c_int64)]
+                ("key_capacity", C.c_int64), ("scratch_bytes", C.c_int64), ("quad", C.c_int)]
 
 
 # gs_env in include/gsbatch.h: camera, link range, pose offset, pixel offset (80 bytes)
