@@ -82,6 +82,25 @@ __device__ __forceinline__ int cidx(int e) { return e + ((e >> 4) << 1); }
 
 constexpr int kSortBins = 1024;  // depth ranges of the window counting sort
 
+// f(i, L[i]) for every i in [0, len) of this thread (i = tid + k NT), with up
+// to U loads of L in flight per thread.
+template <int NT, int U, typename F>
+__device__ __forceinline__ void for_keys(const unsigned long long* L, uint32_t len, F&& f) {
+    for (uint32_t i0 = threadIdx.x; i0 < len; i0 += NT * U) {
+        unsigned long long k[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t i = i0 + (uint32_t)(u * NT);
+            k[u] = i < len ? L[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t i = i0 + (uint32_t)(u * NT);
+            if (i < len) f(i, k[u]);
+        }
+    }
+}
+
 // Block-wide min and max of one u32 per thread; red holds 32 words.
 template <int NT>
 __device__ __forceinline__ void block_minmax_u32(uint32_t& mn, uint32_t& mx, uint32_t* red) {
@@ -106,24 +125,24 @@ __device__ __forceinline__ void block_minmax_u32(uint32_t& mn, uint32_t& mx, uin
 // sort by kSortBins equal ranges of the depth bits, then an insertion sort of
 // each range by whole keys (equal depths fall in index order).  Applies when
 // no range holds more than 32 keys; returns tmp then, else nullptr with keys
-// untouched.  c32: kSortBins u32; red: 32 u32.
+// untouched.  [zmin, zmax] bounds the window's depth bits (the window's
+// producer takes them while loading it).  c32 (kSortBins u32) holds zeros on
+// entry unless `dirty` is set (it is cleared here then); a successful sort
+// leaves it zeroed again (each thread clears its own ranges after the last
+// barrier; the next reader comes after the caller's next barriers).  red: 32 u32.
 template <int NT>
 __device__ unsigned long long* bin_sort(const unsigned long long* keys, unsigned long long* tmp, uint32_t* c32,
-                                        uint32_t* red, int n) {
+                                        uint32_t* red, int n, uint32_t zmin, uint32_t zmax, bool& dirty) {
     constexpr int PER = kSortBins / NT;
     static_assert(kSortBins % NT == 0, "ranges per thread");
-    const int tid = threadIdx.x;
-    uint32_t zmin = 0xffffffffu, zmax = 0u;
-    for (int i = tid; i < n; i += NT) {
-        const uint32_t z = (uint32_t)(keys[i] >> 32);
-        zmin = z < zmin ? z : zmin;
-        zmax = z > zmax ? z : zmax;
-    }
-    block_minmax_u32<NT>(zmin, zmax, red);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t span = zmax - zmin;
     const int shift = (span >> 10) ? 22 - __clz(span) : 0;  // span >> shift < kSortBins
-    for (int b = tid; b < kSortBins; b += NT) c32[b] = 0u;
-    __syncthreads();
+    if (dirty) {
+        for (int b = tid; b < kSortBins; b += NT) c32[b] = 0u;
+        __syncthreads();
+        dirty = false;
+    }
     for (int i = tid; i < n; i += NT) atomicAdd(&c32[((uint32_t)(keys[i] >> 32) - zmin) >> shift], 1u);
     __syncthreads();
     uint32_t loc[PER];
@@ -135,8 +154,31 @@ __device__ unsigned long long* bin_sort(const unsigned long long* keys, unsigned
         sum += loc[j];
         crowded |= loc[j] > 32u;
     }
-    if (__syncthreads_or(crowded)) return nullptr;
-    uint32_t run = block_excl_scan_u32<NT>(sum, red);
+    // exclusive scan of the per-thread sums; the warps' totals carry a crowded
+    // range in bit 31 (a window holds at most kCompCap keys)
+    uint32_t x = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    const bool wc = __any_sync(0xffffffffu, crowded);
+    if (lane == 31) red[warp] = x | (wc ? 0x80000000u : 0u);
+    __syncthreads();
+    uint32_t before = 0;
+    bool any = false;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        const uint32_t r = red[w];
+        if (w < warp) before += r & 0x7fffffffu;
+        any |= (r >> 31) != 0u;
+    }
+    __syncthreads();  // red is reused
+    if (any) {
+        dirty = true;  // c32 keeps the counts
+        return nullptr;
+    }
+    uint32_t run = before + x - sum;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         c32[tid * PER + j] = run;
@@ -166,6 +208,8 @@ __device__ unsigned long long* bin_sort(const unsigned long long* keys, unsigned
         }
     }
     __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PER; ++j) c32[tid * PER + j] = 0u;
     return tmp;
 }
 
@@ -174,11 +218,13 @@ __device__ unsigned long long* bin_sort(const unsigned long long* keys, unsigned
 // out; otherwise LSD radix passes of 4 bits over the depth bits that differ
 // inside the window give a stable order by depth, and runs of equal depth are
 // then ordered by index.  Returns the array that holds the result (keys or
-// tmp).  cnt: cidx(16*NT) u16 and at least kSortBins u32; red: 32 u32.
+// tmp).  cnt: cidx(16*NT) u16 and at least kSortBins u32 (see bin_sort for
+// zmin, zmax and dirty); red: 32 u32.
 template <int NT>
 __device__ unsigned long long* window_sort(unsigned long long* keys, unsigned long long* tmp, uint16_t* cnt,
-                                           uint32_t* red, int n) {
-    if (unsigned long long* r = bin_sort<NT>(keys, tmp, reinterpret_cast<uint32_t*>(cnt), red, n)) return r;
+                                           uint32_t* red, int n, uint32_t zmin, uint32_t zmax, bool& dirty) {
+    if (unsigned long long* r = bin_sort<NT>(keys, tmp, reinterpret_cast<uint32_t*>(cnt), red, n, zmin, zmax, dirty))
+        return r;
     const int tid = threadIdx.x;
     const int I = (n + NT - 1) / NT;  // keys per thread, blocked arrangement
     const int b0 = tid * I;
@@ -423,6 +469,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     __shared__ uint32_t sel_wn, sel_cnt;
     __shared__ int sel_state;
     __shared__ uint32_t s_ws[kSpillMax / (kCompCap / 2) + 2];  // window starts in the spill region
+    __shared__ uint32_t s_zr[2 * (NW > 0 ? NW : 1)];             // per warp: depth bounds of a loaded window
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(kbuf);
     unsigned char* ubuf = kbuf + CAP * 8;
     unsigned long long* tmp = reinterpret_cast<unsigned long long*>(ubuf);
@@ -441,6 +488,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     const bool dbg = P.dbg_sorted != nullptr;
     unsigned long long* spill =
         P.spill ? P.spill + (size_t)blockIdx.x * P.spill_cap : nullptr;  // this CTA's region
+    bool c32_dirty = true;  // the window sort's counters (cbuf) need clearing before use
     int el = P.e_begin;  // env of the current item, cached across items (uniform in the CTA)
     unsigned int e_lo = P.envs[el].tile_base, e_hi = e_lo + (unsigned)P.envs[el].T;
     if (tid == 0) s_item = atomicAdd(P.work, (unsigned)P.chunk);
@@ -530,12 +578,31 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         return g_link0 + (long long)(j - P.nbp);
     };
     bool finished = false;
+    uint32_t win_zmin = 0u, win_zmax = 0xffffffffu;  // depth-bit bounds of the loaded window
+    // A window producer's last pass: the block-wide depth bounds of the keys
+    // it loaded, folded into the barrier that ends the load.
+    auto end_load = [&](uint32_t zl, uint32_t zh) {
+        zl = __reduce_min_sync(0xffffffffu, zl);
+        zh = __reduce_max_sync(0xffffffffu, zh);
+        if (lane == 0) {
+            s_zr[warp] = zl;
+            s_zr[NW + warp] = zh;
+        }
+        __syncthreads();
+        win_zmin = s_zr[0];
+        win_zmax = s_zr[NW];
+        for (int w = 1; w < NW; ++w) {
+            win_zmin = min(win_zmin, s_zr[w]);
+            win_zmax = max(win_zmax, s_zr[NW + w]);
+        }
+    };
 
     // Sort keys[0, wn) (the next wn keys in depth order) and composite them;
     // `before` keys of the bucket precede them.  Sets `finished` once every
     // pixel of the tile has terminated.
     auto run_window = [&](uint32_t wn, uint32_t before) {
-        const unsigned long long* sorted = window_sort<NT>(keys, tmp, cnt, red, (int)wn);
+        const unsigned long long* sorted =
+            window_sort<NT>(keys, tmp, cnt, red, (int)wn, win_zmin, win_zmax, c32_dirty);
         if (dbg)
             for (uint32_t i = tid; i < wn; i += NT) P.dbg_sorted[start + before + i] = sorted[i];
         // Move the sorted window home (from the scratch half) and, where keys
@@ -750,6 +817,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     // isolated within eight levels).  False means a corrupted bucket.
     auto select = [&](const unsigned long long* L, uint32_t len, unsigned long long lo0, unsigned long long hi0,
                       uint32_t cap, unsigned long long& khi, uint32_t& wn) -> bool {
+        c32_dirty = true;  // hist shares the window sort's counters
         if (tid == 0) {
             sel_lo = lo0;
             sel_hi = hi0;
@@ -822,8 +890,14 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         if (n <= (uint32_t)CAP) {
             if (started || n == 0) return 0u;
             started = true;
-            for (uint32_t i = tid; i < n; i += NT) keys[i] = Lk[i];
-            __syncthreads();
+            uint32_t zl = 0xffffffffu, zh = 0u;
+            for_keys<NT, 6>(Lk, n, [&](uint32_t i, unsigned long long k) {
+                keys[i] = k;
+                const uint32_t z = (uint32_t)(k >> 32);
+                zl = min(zl, z);
+                zh = max(zh, z);
+            });
+            end_load(zl, zh);
             return n;
         }
         if (!started) {
@@ -850,14 +924,17 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                 }
                 if (tid == 0) sel_cnt = 0;
                 __syncthreads();
-                for (uint32_t i = tid; i < seg_len; i += NT) {
-                    const unsigned long long k = seg[i];
+                uint32_t zl = 0xffffffffu, zh = 0u;
+                for_keys<NT, 4>(seg, seg_len, [&](uint32_t, unsigned long long k) {
                     if (k >= seg_lo && k < kh) {
                         const uint32_t slot = atomicAdd(&sel_cnt, 1u);
                         if (slot < (uint32_t)CAP) keys[slot] = k;
+                        const uint32_t z = (uint32_t)(k >> 32);
+                        zl = min(zl, z);
+                        zh = max(zh, z);
                     }
-                }
-                __syncthreads();
+                });
+                end_load(zl, zh);
                 seg_used += wn;
                 seg_lo = kh;
                 return wn;
@@ -867,8 +944,14 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                 ++w;
                 if (b <= a) continue;
                 if (b - a <= (uint32_t)CAP) {
-                    for (uint32_t i = tid; i < b - a; i += NT) keys[i] = spill[a + i];
-                    __syncthreads();
+                    uint32_t zl = 0xffffffffu, zh = 0u;
+                    for_keys<NT, 6>(spill + a, b - a, [&](uint32_t i, unsigned long long k) {
+                        keys[i] = k;
+                        const uint32_t z = (uint32_t)(k >> 32);
+                        zl = min(zl, z);
+                        zh = max(zh, z);
+                    });
+                    end_load(zl, zh);
                     return b - a;
                 }
                 seg = spill + a;  // a bin of more than HALF keys
