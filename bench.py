@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="c1: skip the other forms measured in the same run (128x128, BF16/FP16, c3 plan, c4 rate)")
     ap.add_argument("--oracle-seconds", type=float, default=12.0,
                     help="CPU-baseline sample: oracle envs rendered one by one until this much time has passed")
     ap.add_argument("--workload", choices=["c1", "c3", "c4", "prune", "lidar"], default="c1",
@@ -211,9 +213,138 @@ def run_reference(a, rank, world):
 
 # ---------------------------------------------------------------- our arm
 
-def run_ours(a, rank, world, local_rank):
+def time_uniform(a, w, scene, step, E, W, H, dev, local_rank, world, steps, warmup, dtype="f32", obs=False,
+                 tile="16x16"):
+    """Warm-up, an untimed counting pass (composited pairs, visible records),
+    then `steps` timed steps bracketed by CUDA events on the launching stream
+    with the clocks sampled in between; returns the timings and the
+    compositor's roofline (plain-ALU bound) and the whole step's."""
     import torch
     import torch.distributed as dist
+
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    scene.sync_status()
+    # algorithmic work of one batch: composited (pixel, Gaussian) pairs (untimed pass)
+    scene.set_counters(True)
+    step()
+    torch.cuda.synchronize()
+    st = scene.stats()
+    n_eval = st["composited"]
+    n_vis = st["visible"]
+    n_pairs = st["n_gaussians"] * E  # (env, Gaussian) pairs tested
+    intersections = st["intersections"]
+    launches_per_step = st["kernel_launches"]
+    scene.set_counters(False)
+
+    scene.set_profile(True)
+    scene.timings(reset=True)
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for k in range(steps):
+        step()
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    scene.set_profile(False)
+    tim = scene.timings(reset=True)
+    lat = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(steps))
+    total_ms = evs[0].elapsed_time(evs[-1])
+    scene.sync_status()
+    t_max = max_over_ranks(total_ms, world, dev)
+    ms_step = t_max / steps
+    value = world * E * steps / (t_max / 1e3)
+
+    # roofline of the dominant kernel (compositing): plain-ALU bound.
+    comp_ms, comp_launches = tim["composite"]
+    per_launch_ms = comp_ms / max(comp_launches, 1)
+    launches_per_batch = comp_launches / steps
+    evals_per_launch = n_eval / max(launches_per_batch, 1)
+    ops_per_eval = 20.0  # quadratic form, ex2, alpha, T, 3 colour + 1 depth FMA (lane-ops)
+    sm_mhz = ck.get("sm_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    peak_lane_ops = props.multi_processor_count * 128 * sm_mhz * 1e6
+    achieved = evals_per_launch * ops_per_eval / (per_launch_ms / 1e3)
+    traffic = None
+    # the captured traffic holds for the captured form only: 640x480 camera images, 16x16 tiles
+    if (_sources_sha(COMPOSITE_TRAFFIC_SOURCES) == COMPOSITE_TRAFFIC_SHA and (W, H) == (640, 480)
+            and tile == "16x16" and not obs and dtype == "f32"):
+        traffic = COMPOSITE_TRAFFIC_PER_ENV * E / max(launches_per_batch, 1)  # bytes per launch
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_lane_ops / 1e9, "unit": "Glane-op/s",
+                "frac": achieved / peak_lane_ops, "traffic": traffic,
+                "kernel": "k_composite", "per_launch_ms": per_launch_ms,
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x median {sm_mhz:.0f} MHz "
+                              "(1 lane-op per lane per clock, FMA counted once)"}
+    phase_ms = {k: v[0] / steps for k, v in tim.items()}
+
+    # whole-step roofline: algorithmic HBM bytes vs FP32 work (paper's hot path, all steps)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    attr_bytes = (w.background.n + w.links.n) * (236 if dtype == "f32" else 132)
+    out_bytes = E * H * W * (6 if obs else 16)
+    io_bytes = attr_bytes + E * (w.n_links * 28 + 56) + out_bytes
+    # whole step: time floor = max(algorithmic bytes / HBM peak, algorithmic FP32 work / ALU peak), the
+    # work being N_eval x 20 (compositing) + E G x 20 (culling every pair) + E V x 300 (projecting the
+    # visible pairs: covariance, conic, SH degree 3)
+    fp32_ops = n_eval * 20.0 + n_pairs * 20.0 + n_vis * 300.0
+    hbm_floor_ms = io_bytes / (hbm * 1e9) * 1e3
+    alu_floor_ms = fp32_ops / peak_lane_ops * 1e3
+    step_roofline = {"io_bytes": io_bytes, "hbm_floor_ms": hbm_floor_ms, "hbm_gbs_peak": hbm,
+                     "fp32_lane_ops": fp32_ops, "alu_floor_ms": alu_floor_ms,
+                     "bound": "alu" if alu_floor_ms > hbm_floor_ms else "hbm",
+                     "frac": max(alu_floor_ms, hbm_floor_ms) / ms_step,
+                     "composited_pairs": n_eval, "visible_pairs": n_vis, "tested_pairs": n_pairs,
+                     "intersections": intersections}
+    return {"value": value, "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": _pct(lat, 0.99), "mean": sum(lat) / len(lat)},
+            "clocks": ck, "roofline": roofline, "step_roofline": step_roofline, "phase_ms_per_step": phase_ms,
+            "gpu_launches": int(launches_per_step * steps), "mpix_per_s": value * H * W / 1e6}
+
+
+def measure_uniform(a, w, dtype, dev, local_rank, world, steps, warmup, tile="16x16"):
+    """One uniform-resolution batch of workload w in storage dtype, timed as
+    the headline is; the scene and images are released afterwards."""
+    import torch
+
+    from paper_2604_25459_gb300 import gsbatch
+
+    tw, th = (int(x) for x in tile.split("x"))
+    E, H, W = w.n_envs, int(w.cams["height"][0]), int(w.cams["width"][0])
+    scene = gsbatch.scene_from_workload(w, dtype)
+    scene.set_tile(tw, th)
+    poses = torch.from_numpy(w.link_poses).to(dev)
+    rgb = torch.empty((E, H, W, 3), dtype=torch.float32, device=dev)
+    depth = torch.empty((E, H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        scene.render(poses, w.cams, rgb=rgb, depth=depth, want_alpha=False, stream=stream)
+
+    r = time_uniform(a, w, scene, step, E, W, H, dev, local_rank, world, steps, warmup, dtype=dtype, tile=tile)
+    scene.close()
+    del rgb, depth, poses
+    torch.cuda.empty_cache()
+    r["config"] = {"workload": f"{w.name}: {E} envs x {W}x{H} RGB-D, {dtype} storage, tile {tile}",
+                   "l2": f"outputs of {E * H * W * 16 / 1e9:.1f} GB written per step (> 129 MB L2)"}
+    return r
+
+
+def run_ours(a, rank, world, local_rank):
+    import torch
 
     import __graft_entry__
     from paper_2604_25459_gb300 import gsbatch, synth
@@ -248,99 +379,14 @@ def run_ours(a, rank, world, local_rank):
         def step():
             scene.render(poses, w.cams, rgb=rgb, depth=depth, want_alpha=False, stream=stream)
 
-    for _ in range(a.warmup):
-        step()
-    torch.cuda.synchronize()
-    scene.sync_status()
-    # algorithmic work of one batch: composited (pixel, Gaussian) pairs (untimed pass)
-    scene.set_counters(True)
-    step()
-    torch.cuda.synchronize()
-    st = scene.stats()
-    n_eval = st["composited"]
-    n_vis = st["visible"]
-    n_pairs = st["n_gaussians"] * E  # (env, Gaussian) pairs tested
-    intersections = st["intersections"]
-    launches_per_step = st["kernel_launches"]
-    scene.set_counters(False)
-
-    scene.set_profile(True)
-    scene.timings(reset=True)
-    clocks = ClockSampler(local_rank)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
-    evs[0].record(stream)
-    for k in range(a.steps):
-        step()
-        evs[k + 1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ck = clocks.stop()
-    scene.set_profile(False)
-    tim = scene.timings(reset=True)
-    lat = [evs[k].elapsed_time(evs[k + 1]) for k in range(a.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    scene.sync_status()
-    t_max = max_over_ranks(total_ms, world, dev)
-    ms_step = t_max / a.steps
-    value = world * E * a.steps / (t_max / 1e3)
-
-    # roofline of the dominant kernel (compositing): plain-ALU bound.
-    comp_ms, comp_launches = tim["composite"]
-    per_launch_ms = comp_ms / max(comp_launches, 1)
-    launches_per_batch = comp_launches / a.steps
-    evals_per_launch = n_eval / max(launches_per_batch, 1)
-    ops_per_eval = 20.0  # quadratic form, ex2, alpha, T, 3 colour + 1 depth FMA (lane-ops)
-    sm_mhz = ck.get("sm_mhz") or 2070.0
-    props = torch.cuda.get_device_properties(dev)
-    peak_lane_ops = props.multi_processor_count * 128 * sm_mhz * 1e6
-    achieved = evals_per_launch * ops_per_eval / (per_launch_ms / 1e3)
-    traffic = None
-    # the captured traffic holds for the captured form only: 640x480 camera images, 16x16 tiles
-    if (_sources_sha(COMPOSITE_TRAFFIC_SOURCES) == COMPOSITE_TRAFFIC_SHA and (W, H) == (640, 480)
-            and a.tile == "16x16" and not a.obs):
-        traffic = COMPOSITE_TRAFFIC_PER_ENV * E / max(launches_per_batch, 1)  # bytes per launch
+    r = time_uniform(a, w, scene, step, E, W, H, dev, local_rank, world, a.steps, a.warmup, dtype=a.dtype,
+                     obs=a.obs, tile=a.tile)
     try:  # measured plain-ALU rates, reported beside the derived peak
         alu = gsbatch.measure_alu_peak(stream)
     except Exception as ex:  # noqa: BLE001
         alu = {"error": str(ex)}
-    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_lane_ops / 1e9, "unit": "Glane-op/s",
-                "measured_fma_glane_ops": alu.get("fma_lane_ops_per_s", 0.0) / 1e9,
-                "measured_ex2_glane_ops": alu.get("ex2_lane_ops_per_s", 0.0) / 1e9,
-                "frac": achieved / peak_lane_ops, "traffic": traffic,
-                "kernel": "k_composite", "per_launch_ms": per_launch_ms,
-                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x median {sm_mhz:.0f} MHz "
-                              "(1 lane-op per lane per clock, FMA counted once)"}
-    phase_ms = {k: v[0] / a.steps for k, v in tim.items()}
-
-    # whole-step roofline: algorithmic HBM bytes vs FP32 work (paper's hot path, all steps)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    attr_bytes = (w.background.n + w.links.n) * (236 if a.dtype == "f32" else 132)
-    out_bytes = E * H * W * (6 if a.obs else 16)
-    io_bytes = attr_bytes + E * (w.n_links * 28 + 56) + out_bytes
-
-    # whole step: time floor = max(algorithmic bytes / HBM peak, algorithmic FP32 work / ALU peak), the
-    # work being N_eval x 20 (compositing) + E G x 20 (culling every pair) + E V x 300 (projecting the
-    # visible pairs: covariance, conic, SH degree 3)
-    fp32_ops = n_eval * 20.0 + n_pairs * 20.0 + n_vis * 300.0
-    hbm_floor_ms = io_bytes / (hbm * 1e9) * 1e3
-    alu_floor_ms = fp32_ops / peak_lane_ops * 1e3
-    step_roofline = {"io_bytes": io_bytes, "hbm_floor_ms": hbm_floor_ms, "hbm_gbs_peak": hbm,
-                     "fp32_lane_ops": fp32_ops, "alu_floor_ms": alu_floor_ms,
-                     "bound": "alu" if alu_floor_ms > hbm_floor_ms else "hbm",
-                     "frac": max(alu_floor_ms, hbm_floor_ms) / ms_step,
-                     "composited_pairs": n_eval, "visible_pairs": n_vis, "tested_pairs": n_pairs,
-                     "intersections": intersections}
+    r["roofline"]["measured_fma_glane_ops"] = alu.get("fma_lane_ops_per_s", 0.0) / 1e9
+    r["roofline"]["measured_ex2_glane_ops"] = alu.get("ex2_lane_ops_per_s", 0.0) / 1e9
 
     e2e = None
     if not a.no_e2e:
@@ -354,6 +400,8 @@ def run_ours(a, rank, world, local_rank):
             host_step = lambda: scene.render_host(poses_h, w.cams, rgb_h, depth_h)
         host_step()
         if world > 1:
+            import torch.distributed as dist
+
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(a.e2e_steps):
@@ -364,6 +412,14 @@ def run_ours(a, rank, world, local_rank):
                "d2h_bytes_per_step": int(rgb_h.nbytes + depth_h.nbytes),
                "ms_per_step": 1e3 * dt / a.e2e_steps,
                "api": "gs_render_batch_obs_host" if a.obs else "gs_render_batch_host"}
+        del rgb_h, depth_h, poses_h
+    scene.close()
+    if a.obs:
+        del rgb8, depth16
+    else:
+        del rgb, depth
+    del poses
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -372,50 +428,63 @@ def run_ours(a, rank, world, local_rank):
                "sample": f"envs 0..{done - 1} of the same c1 batch rendered one by one by the plain FP64 oracle "
                          f"({t:.1f} s of CPU time budgeted at {a.oracle_seconds:.0f} s)"}
 
+    # The other forms of the path, measured in the same run on the same GPU
+    # (one process, N=1 only): the RL-typical 128x128 image, the BF16/FP16
+    # storage forms of the headline batch, a short replay of the batched
+    # uneven plan and the request loop at one offered rate.
+    sub = None
+    headline = (E, W, H, a.dtype, a.obs, a.tile) == (2048, 640, 480, "f32", False, "16x16")
+    if world == 1 and headline and not a.no_sub:
+        sub = {}
+        sub_steps, sub_warm = 5, 3
+        w128 = synth.make_c2(n_envs=E, res="128x128")
+        sub["c2_128x128_f32"] = measure_uniform(a, w128, "f32", dev, local_rank, world, sub_steps, sub_warm)
+        del w128
+        for dt in ("bf16", "f16"):
+            sub[f"c1_{dt}"] = measure_uniform(a, w, dt, dev, local_rank, world, sub_steps, sub_warm)
+        sub["c3_plan"] = measure_c3(a, dev, local_rank, world, steps=3, warmup=1)
+        sub["c4_served"] = measure_c4(a, dev, local_rank, world, rates=[1e4], duration=2.0, plain=False)
+
     if rank == 0:
-        lat_sorted = sorted(lat)
         line = {
             "metric": METRIC if (E, W, H) == (2048, 640, 480) else f"env-frames/s at {E}x{W}x{H} RGB-D",
-            "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": a.dtype if a.dtype != "f32" else "f32", "data": "synthetic",
             "config": {"workload": f"c1: {E} envs x {W}x{H} RGB-D, 500k room-shell background + 20 links x 5k "
                                    f"Gaussians, SH degree 3, tile {a.tile}"
                                    + (", observation form: u8 RGB after per-env exposure/contrast/brightness + f16 depth"
                                       if a.obs else ""),
                        "envs_per_gpu": E, "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": f"outputs of {out_bytes / 1e9:.1f} GB written per step (> 129 MB L2)"},
-            "mpix_per_s": value * H * W / 1e6,
-            "latency_ms": {"p50": lat_sorted[len(lat) // 2], "p99": lat_sorted[min(len(lat) - 1,
-                                                                                   int(math.ceil(0.99 * len(lat))) - 1)],
-                           "mean": sum(lat) / len(lat)},
-            "clocks": ck,
-            "roofline": roofline,
-            "step_roofline": step_roofline,
-            "phase_ms_per_step": phase_ms,
-            "gpu_launches": int(launches_per_step * a.steps),
+                       "l2": f"outputs of {E * H * W * (6 if a.obs else 16) / 1e9:.1f} GB written per step "
+                             "(> 129 MB L2)"},
+            "mpix_per_s": r["mpix_per_s"],
+            "latency_ms": r["latency_ms"],
+            "clocks": r["clocks"],
+            "roofline": r["roofline"],
+            "step_roofline": r["step_roofline"],
+            "phase_ms_per_step": r["phase_ms_per_step"],
+            "gpu_launches": r["gpu_launches"],
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "sub_results": sub,
         }
         print(json.dumps(line), flush=True)
-    scene.close()
 
 
-def run_c3(a, rank, world, local_rank):
+def measure_c3(a, dev, local_rank, world, steps, warmup, envs_n=4096):
     """Batched uneven form: 4096 envs, per-env objects of 10k-200k Gaussians on a
     shared 300k background, resolutions {64^2, 128^2, 320x240, 640x480} with
-    probabilities {.3, .3, .2, .2}; one plan (autotuned tile shape and claim
-    size, replayed from a captured CUDA graph); a step is one plan launch."""
+    probabilities {.3, .3, .2, .2}; one plan (autotuned tile shape, claim
+    size and compositor form, replayed from a captured CUDA graph); a step is
+    one plan launch.  The compositor's roofline comes from an eager,
+    profiled render of the same batch (gs_render_batch_v) after the timing."""
     import torch
     import torch.distributed as dist
 
-    import __graft_entry__
     from paper_2604_25459_gb300 import gsbatch, synth
 
-    __graft_entry__.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    E = a.envs if a.envs != 2048 else 4096
+    E = envs_n
     t0 = time.perf_counter()
     w = synth.make_c3(n_envs=E, threads=os.cpu_count() or 8)
     gen_s = time.perf_counter() - t0
@@ -433,7 +502,7 @@ def run_c3(a, rank, world, local_rank):
     plan.launch(poses, rgb, depth, stream=stream)
     torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         plan.launch(poses, rgb, depth, stream=stream)
     torch.cuda.synchronize()
     scene.sync_status()
@@ -442,9 +511,9 @@ def run_c3(a, rank, world, local_rank):
         dist.barrier()
     clocks.start()
     time.sleep(0.3)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     evs[0].record(stream)
-    for k in range(a.steps):
+    for k in range(steps):
         plan.launch(poses, rgb, depth, stream=stream)
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
@@ -452,26 +521,63 @@ def run_c3(a, rank, world, local_rank):
         dist.barrier()
     ck = clocks.stop()
     scene.sync_status()
-    lat = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(a.steps))
+    lat = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(steps))
     total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), world, dev)
     info = plan.info()
-    if rank == 0:
-        value = world * E * a.steps / (total_ms / 1e3)
-        res, cnt = np.unique(w.cams["width"], return_counts=True)
-        line = {"metric": "env-frames/s, batched uneven RGB-D (4096 mixed-resolution envs)", "value": value,
-                "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-                "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"c3: {E} envs, 300k background + per-env objects log-uniform 10k-200k "
-                                       f"({w.links.n} object Gaussians), widths {dict(zip(res.tolist(), cnt.tolist()))}",
-                           "l2": f"{npx * 16 / 1e9:.2f} GB of outputs per step"},
-                "mpix_per_s": value * npx / E / 1e6,
-                "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
-                "clocks": ck, "plan": info, "generate_s": gen_s, "first_launch_s": tune_s,
-                "gpu_launches": None, "e2e": None, "cpu_baseline": None}
-        print(json.dumps(line), flush=True)
     plan.close()
+    # eager pass: composited pairs, then the compositor's time per launch
+    scene.set_tile(info["tile_w"], info["tile_h"])
+    scene.set_counters(True)
+    scene.render_v(envs, poses, rgb, depth, stream=stream)
+    torch.cuda.synchronize()
+    n_eval = scene.stats()["composited"]
+    scene.set_counters(False)
+    scene.set_profile(True)
+    scene.timings(reset=True)
+    scene.render_v(envs, poses, rgb, depth, stream=stream)
+    tim = scene.timings(reset=True)
+    scene.set_profile(False)
+    scene.sync_status()
+    comp_ms, comp_launches = tim["composite"]
+    sm_mhz = ck.get("sm_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * sm_mhz * 1e6
+    per_launch = comp_ms / max(comp_launches, 1)
+    achieved = n_eval / max(comp_launches, 1) * 20.0 / (per_launch / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Glane-op/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_composite", "per_launch_ms": per_launch,
+                "basis": "eager gs_render_batch_v of the same batch with the plan's tile shape (the plan's own "
+                         "launches are graph replays without per-kernel events); composited pairs x 20 lane-ops"}
     scene.close()
+    del rgb, depth, poses
+    torch.cuda.empty_cache()
+    value = world * E * steps / (total_ms / 1e3)
+    res, cnt = np.unique(w.cams["width"], return_counts=True)
+    return {"metric": "env-frames/s, batched uneven RGB-D (4096 mixed-resolution envs)", "value": value,
+            "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
+            "config": {"workload": f"c3: {E} envs, 300k background + per-env objects log-uniform 10k-200k "
+                                   f"({w.links.n} object Gaussians), widths {dict(zip(res.tolist(), cnt.tolist()))}",
+                       "l2": f"{npx * 16 / 1e9:.2f} GB of outputs per step"},
+            "mpix_per_s": value * npx / E / 1e6,
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": _pct(lat, 0.99)},
+            "clocks": ck, "plan": info, "roofline": roofline, "composited_pairs": n_eval,
+            "eager_phase_ms": {k: v[0] for k, v in tim.items()}, "generate_s": gen_s, "first_launch_s": tune_s}
+
+
+def run_c3(a, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    r = measure_c3(a, dev, local_rank, world, a.steps, a.warmup, envs_n=a.envs if a.envs != 2048 else 4096)
+    if rank == 0:
+        line = dict(r)
+        line.update({"n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                     "dtype": "f32", "data": "synthetic", "gpu_launches": None, "e2e": None, "cpu_baseline": None})
+        print(json.dumps(line), flush=True)
 
 
 def _pct(xs, q):
@@ -479,26 +585,21 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))] if xs else None
 
 
-def run_c4(a, rank, world, local_rank):
+def measure_c4(a, dev, local_rank, world, rates, duration, plain=True, envs_n=4096):
     """Served form: 8 resident scenes (room-shell backgrounds of 200k..1M
     Gaussians plus the 20-link robot) and 4096 env instances at the c3
     resolution mix.  Requests (one env's link poses, from the host) arrive as
     a Poisson stream at each offered rate and are served by the library's
     request loop (continuous batching under a 120 GB HBM budget on a pool of
     streams); reported per rate: served env-frames/s and p50/p99 latency
-    (arrival to completion on the device).  The plain per-batch path (every
-    env of every scene rendered by gs_render_batch_v, scene by scene) is timed
-    beside it.  Replicas only under torchrun: each rank serves its own copy."""
+    (arrival to completion on the device).  With `plain`, the plain per-batch
+    path (every env of every scene rendered by gs_render_batch_v, scene by
+    scene) is timed beside it."""
     import torch
-    import torch.distributed as dist
 
-    import __graft_entry__
     from paper_2604_25459_gb300 import gsbatch, synth
 
-    __graft_entry__.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    E = a.envs if a.envs != 2048 else 4096
+    E = envs_n
     t0 = time.perf_counter()
     w = synth.make_c4(n_envs=E)
     gen_s = time.perf_counter() - t0
@@ -514,30 +615,32 @@ def run_c4(a, rank, world, local_rank):
     npx = int((w.cams["width"].astype(np.int64) * w.cams["height"]).sum())
     stream = torch.cuda.current_stream()
 
-    # plain per-batch path: all envs, scene by scene, one step = every env once
-    poses_all = torch.from_numpy(w.request_poses(E, stream=99).reshape(E * L, 7)).to(dev)
-    rgb = torch.empty(npx * 3, device=dev)
-    depth = torch.empty(npx, device=dev)
-    envs_all = gsbatch.make_envs(w.cams, link_ranges=np.tile([0, L], (E, 1)), pose_offsets=np.arange(E) * L)
-    per_scene = [envs_all[w.env_scene == k] for k in range(S)]
+    plain_ms = None
+    if plain:  # plain per-batch path: all envs, scene by scene, one step = every env once
+        poses_all = torch.from_numpy(w.request_poses(E, stream=99).reshape(E * L, 7)).to(dev)
+        rgb = torch.empty(npx * 3, device=dev)
+        depth = torch.empty(npx, device=dev)
+        envs_all = gsbatch.make_envs(w.cams, link_ranges=np.tile([0, L], (E, 1)), pose_offsets=np.arange(E) * L)
+        per_scene = [envs_all[w.env_scene == k] for k in range(S)]
 
-    def plain_step():
-        for k in range(S):
-            scenes[k].render_v(per_scene[k], poses_all, rgb, depth, stream=stream)
+        def plain_step():
+            for k in range(S):
+                scenes[k].render_v(per_scene[k], poses_all, rgb, depth, stream=stream)
 
-    for _ in range(a.warmup):
-        plain_step()
-    torch.cuda.synchronize()
-    for sc in scenes:
-        sc.sync_status()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        plain_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1) / a.steps
-    del rgb, depth
+        for _ in range(a.warmup):
+            plain_step()
+        torch.cuda.synchronize()
+        for sc in scenes:
+            sc.sync_status()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            plain_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1) / a.steps
+        del rgb, depth, poses_all
+        torch.cuda.empty_cache()
 
     # the request loop
     sv = gsbatch.Server(budget_bytes=int(a.budget_gb * (1 << 30)), max_inflight=a.slots,
@@ -558,8 +661,8 @@ def run_c4(a, rank, world, local_rank):
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
-    for ri, rate in enumerate(float(r) for r in a.rates.split(",")):
-        n = max(1, int(rate * a.duration))
+    for ri, rate in enumerate(rates):
+        n = max(1, int(rate * duration))
         arr = np.cumsum(rng.exponential(1.0 / rate, n))
         env = rng.integers(0, E, n)
         poses = w.request_poses(n, stream=ri)
@@ -589,28 +692,46 @@ def run_c4(a, rank, world, local_rank):
     sv.close()
     for sc in scenes:
         sc.sync_status()
-    if rank == 0:
-        sustained = [s for s in sweep if s["served_env_frames_s"] >= 0.95 * s["offered_req_s"]]
-        top = max(sustained, key=lambda s: s["offered_req_s"]) if sustained else sweep[0]
-        res_w, cnt = np.unique(w.cams["width"], return_counts=True)
-        line = {"metric": "served env-frames/s and p99 latency (8 resident scenes, 4096 envs, Poisson arrivals)",
-                "value": top["served_env_frames_s"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
-                "warmup": a.warmup, "ms_per_step": plain_ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"c4: {S} scenes, backgrounds "
-                                       f"{[b.n for b in w.backgrounds]} + 20x5k robot, {E} envs, widths "
-                                       f"{dict(zip(res_w.tolist(), cnt.tolist()))}",
-                           "budget_gb": a.budget_gb, "slots": a.slots, "max_batch": a.max_batch,
-                           "tile": a.tile, "l2": f"{npx * 16 / 1e9:.2f} GB of outputs per plain step"},
-                "latency_ms": {"p50": top["p50_ms"], "p99": top["p99_ms"], "at_offered_req_s": top["offered_req_s"]},
-                "sweep": sweep,
-                "plain_per_batch": {"ms_per_step": plain_ms, "env_frames_s": E / (plain_ms / 1e3),
-                                    "latency_ms_one_step": plain_ms},
-                "clocks": ck, "generate_s": gen_s, "gpu_launches": None, "e2e": None, "cpu_baseline": None}
-        print(json.dumps(line), flush=True)
-    for sc in scenes:
         sc.close()
+    torch.cuda.empty_cache()
+    sustained = [x for x in sweep if x["served_env_frames_s"] >= 0.95 * x["offered_req_s"]]
+    top = max(sustained, key=lambda x: x["offered_req_s"]) if sustained else sweep[0]
+    res_w, cnt = np.unique(w.cams["width"], return_counts=True)
+    out = {"metric": "served env-frames/s and p99 latency (8 resident scenes, 4096 envs, Poisson arrivals)",
+           "value": top["served_env_frames_s"], "unit": UNIT,
+           "config": {"workload": f"c4: {S} scenes, backgrounds "
+                                  f"{[b.n for b in w.backgrounds]} + 20x5k robot, {E} envs, widths "
+                                  f"{dict(zip(res_w.tolist(), cnt.tolist()))}",
+                      "budget_gb": a.budget_gb, "slots": a.slots, "max_batch": a.max_batch, "tile": a.tile,
+                      "arrivals_s_per_rate": duration},
+           "latency_ms": {"p50": top["p50_ms"], "p99": top["p99_ms"], "at_offered_req_s": top["offered_req_s"]},
+           "sweep": sweep, "clocks": ck, "generate_s": gen_s}
+    if plain_ms is not None:
+        out["ms_per_step"] = plain_ms
+        out["plain_per_batch"] = {"ms_per_step": plain_ms, "env_frames_s": E / (plain_ms / 1e3),
+                                  "latency_ms_one_step": plain_ms,
+                                  "l2": f"{npx * 16 / 1e9:.2f} GB of outputs per plain step"}
+    return out
 
+
+def run_c4(a, rank, world, local_rank):
+    """The served form (see measure_c4) at every offered rate of --rates.
+    Replicas only under torchrun: each rank serves its own copy."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    r = measure_c4(a, dev, local_rank, world, [float(x) for x in a.rates.split(",")], a.duration, plain=True,
+                   envs_n=a.envs if a.envs != 2048 else 4096)
+    if rank == 0:
+        line = dict(r)
+        line.update({"n_gpus": world, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
+                     "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                     "gpu_launches": None, "e2e": None, "cpu_baseline": None})
+        print(json.dumps(line), flush=True)
 
 
 def run_prune(a, rank, world, local_rank):
