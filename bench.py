@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--rates", default="1000,3000,10000,30000", help="c4: offered request rates (req/s)")
     ap.add_argument("--prune-envs", type=int, default=64, help="prune: envs whose cameras rank the Gaussians")
     ap.add_argument("--beams", type=int, default=64, help="lidar: beams (rows)")
+    ap.add_argument("--rays", type=int, default=0,
+                    help="lidar: rays per env of a non-repetitive (rosette) pattern within +-0.6 rad of the sensor's "
+                         "x axis instead of a grid scan; --beams x --azimuth then only bins them over +-0.65 rad")
     ap.add_argument("--azimuth", type=int, default=1024, help="lidar: azimuth steps across the window (columns)")
     ap.add_argument("--az-window", default="0,6.283185307179586",
                     help="lidar: azimuth window az_min,az_max in radians (a full turn: rotating; narrower: solid-state)")
@@ -812,10 +815,16 @@ def run_prune(a, rank, world, local_rank):
 
 
 def run_lidar(a, rank, world, local_rank):
-    """Batch-LiDAR on the c1 scene: every env carries a rotating LiDAR of
-    --beams x --azimuth rays (elevation -0.4..0.3 rad) at its jittered head
-    position; a step scans all envs (range + hit per ray) with the links posed
-    per env.  Reported in rays/s."""
+    """Batch-LiDAR on the c1 scene: every env carries a LiDAR at its jittered
+    head position, a rotating one of --beams x --azimuth rays (elevation
+    -0.4..0.3 rad; --az-window narrower: solid-state), or with --rays R a
+    non-repetitive rosette pattern of R rays per env (a different phase per
+    env); a step scans all envs (range + hit per ray) with the links posed per
+    env.  Reported in rays/s, with the compositor's roofline: composited
+    (ray, Gaussian) pairs x 40 lane-ops (the ray-space evaluation: three dot
+    products with the rows of G, a cross product, a reciprocal, q and t*,
+    ex2, alpha, then transmittance and range) per launch time, against the
+    FP32 lane peak."""
     import torch
     import torch.distributed as dist
 
@@ -834,17 +843,42 @@ def run_lidar(a, rank, world, local_rank):
     sens["q_ws"] = [1.0, 0.0, 0.0, 0.0]
     sens["t_ws"] = -(np.array([-1.0, 0.0, 1.4]) + rng.uniform(-0.2, 0.2, (E, 3)))
     sens["rows"], sens["cols"] = a.beams, a.azimuth
-    sens["elev_min"], sens["elev_max"], sens["near_range"] = -0.4, 0.3, 0.05
-    az0, az1 = (float(x) for x in a.az_window.split(","))
-    sens["az_min"], sens["az_max"] = az0, az1  # a full turn: rotating; narrower: solid-state
+    sens["near_range"] = 0.05
     R, Cc = a.beams, a.azimuth
-    out_r = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)
-    out_h = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    if a.rays > 0:
+        sens["elev_min"], sens["elev_max"] = -0.65, 0.65
+        sens["az_min"], sens["az_max"] = -0.65, 0.65
+        dirs = torch.from_numpy(synth.rosette_rays(E, a.rays, seed=7)).to(dev)
+        out_r = torch.empty((E, a.rays), dtype=torch.float32, device=dev)
+        out_h = torch.empty((E, a.rays), dtype=torch.float32, device=dev)
+        rays = E * a.rays
+
+        def step():
+            scene.render_rays(poses, sens, dirs, out_r, out_h, stream=stream)
+        desc = (f"non-repetitive rosette LiDAR, {a.rays} rays per env within 0.6 rad of the sensor axis, binned on a "
+                f"{R}x{Cc} grid over +-0.65 rad")
+    else:
+        sens["elev_min"], sens["elev_max"] = -0.4, 0.3
+        az0, az1 = (float(x) for x in a.az_window.split(","))
+        sens["az_min"], sens["az_max"] = az0, az1  # a full turn: rotating; narrower: solid-state
+        out_r = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)
+        out_h = torch.empty((E, R, Cc), dtype=torch.float32, device=dev)
+        rays = E * R * Cc
+
+        def step():
+            scene.render_lidar(poses, sens, out_r, out_h, stream=stream)
+        desc = (f"{'rotating' if az1 - az0 >= 6.28318 else 'solid-state'} LiDAR {R} beams x {Cc} azimuth steps over "
+                f"azimuth {az0:.3f}..{az1:.3f} rad, elevation -0.4..0.3 rad")
     for _ in range(a.warmup):
-        scene.render_lidar(poses, sens, out_r, out_h, stream=stream)
+        step()
     torch.cuda.synchronize()
     scene.sync_status()
+    scene.set_counters(True)  # untimed: composited (ray, Gaussian) pairs
+    step()
+    torch.cuda.synchronize()
+    n_eval = scene.stats()["composited"]
+    scene.set_counters(False)
     scene.set_profile(True)
     scene.timings(reset=True)
     clocks = ClockSampler(local_rank)
@@ -855,28 +889,35 @@ def run_lidar(a, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(a.steps):
-        scene.render_lidar(poses, sens, out_r, out_h, stream=stream)
+        step()
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
     tim = scene.timings(reset=True)
     scene.set_profile(False)
     scene.sync_status()
-    ms = e0.elapsed_time(e1) / a.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, world, dev)
     hit_frac = float((out_h > 0.5).float().mean())
+    comp_ms, comp_launches = tim["composite"]
+    per_launch = comp_ms / max(comp_launches, 1)
+    launches_per_step = comp_launches / a.steps
+    sm_mhz = ck.get("sm_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * sm_mhz * 1e6
+    achieved = n_eval / max(launches_per_step, 1) * 40.0 / (per_launch / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Glane-op/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_composite (LiDAR form)",
+                "per_launch_ms": per_launch, "composited_pairs": n_eval, "lane_ops_per_pair": 40}
     if rank == 0:
-        rays = E * R * Cc
-        line = {"metric": f"LiDAR rays/s ({E} envs x {R}x{Cc} rays, c1 scene)", "value": world * rays / (ms / 1e3),
+        line = {"metric": f"LiDAR rays/s ({E} envs x {rays // E} rays, c1 scene)", "value": world * rays / (ms / 1e3),
                 "unit": "rays/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"c1 scene (500k room-shell background + 20x5k robot), {E} envs, "
-                                       f"{'rotating' if az1 - az0 >= 6.28318 else 'solid-state'} LiDAR {R} beams x "
-                                       f"{Cc} azimuth steps over azimuth {az0:.3f}..{az1:.3f} rad, elevation "
-                                       f"-0.4..0.3 rad",
+                "config": {"workload": f"c1 scene (500k room-shell background + 20x5k robot), {E} envs, {desc}",
                            "rays_hit_over_half": hit_frac},
                 "env_scans_per_s": world * E / (ms / 1e3),
                 "phase_ms_per_step": {k: v[0] / a.steps for k, v in tim.items()},
+                "roofline": roofline,
                 "clocks": ck, "gpu_launches": None, "e2e": None, "cpu_baseline": None}
         print(json.dumps(line), flush=True)
     scene.close()

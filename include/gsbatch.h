@@ -210,6 +210,28 @@ typedef struct {
 gs_status gs_render_lidar(gs_scene s, int n_envs, const float* link_poses, const gs_lidar* sensors, float* range,
                           float* hit, void* cuda_stream);
 
+/* Scan n_envs environments along arbitrary rays: the non-repetitive scan
+ * patterns of the paper's LiDAR list (Sec. III-E, Table II), whose rays are
+ * not a regular (azimuth, beam) grid.  Each ray is composited exactly as a
+ * ray of gs_render_lidar.
+ *   sensors   HOST gs_lidar [n_envs]: pose and near_range as for
+ *             gs_render_lidar; rows, cols, elevation range and azimuth window
+ *             only describe a binning grid (all sensors alike) that must
+ *             contain every ray direction: a zero direction, or one outside
+ *             the grid, reads 0 and sets the device status word
+ *             (gs_scene_sync_status reports it).  About one ray per cell bins
+ *             best; any density is correct.
+ *   n_rays    rays per environment, 1 .. 2^24
+ *   ray_dirs  DEVICE float32 [n_envs][n_rays][3]: directions in the sensor
+ *             frame (x forward, y left, z up; need not be unit length)
+ *   range     DEVICE float32 [n_envs][n_rays]: sum(alpha T t*) / (1 - T), 0 where nothing is hit
+ *   hit       DEVICE float32 [n_envs][n_rays] (1 - T), or NULL
+ * Blocks the host once per wave (intersection and ray totals).  Errors as
+ * gs_render_lidar (GS_ERR_INVALID also for n_rays out of range or a null
+ * ray_dirs). */
+gs_status gs_render_rays(gs_scene s, int n_envs, const float* link_poses, const gs_lidar* sensors, int n_rays,
+                         const float* ray_dirs, float* range, float* hit, void* cuda_stream);
+
 /* Contribution pass (support for pruning, a scene transform that follows the
  * paper's Gaussian pruning for speed and memory, Sec. III-C): renders n_envs
  * environments like gs_render_batch (one resolution, 16x16 tiles whatever

@@ -27,9 +27,14 @@ along the ray in ray space instead of through a 2D projection:
 * outputs: hit = 1 - T and range = sum(alpha T t*) / (1 - T) (0 where
   1 - T = 0).
 
+The non-repetitive patterns of the paper's list have no grid: ``render_rays``
+takes the rays as a list of directions and composites each one the same way
+(both entry points share ``_composite_rays``).
+
 Computed in FP64 by brute force over every (ray, Gaussian) pair: small inputs
 only.  Pinned in ``tests/test_oracle_pins.py`` (closed forms for one and two
-Gaussians, a joint rigid motion of sensor and scene).
+Gaussians on grid and off-grid rays, a joint rigid motion of sensor and
+scene, a ray list equal to a grid's rays).
 """
 from __future__ import annotations
 
@@ -63,14 +68,10 @@ def ray_directions(rows: int, cols: int, elev_min: float, elev_max: float, az_mi
     return np.stack([ct * np.cos(phi)[None, :], ct * np.sin(phi)[None, :], np.broadcast_to(st, (rows, cols))], -1)
 
 
-def render_lidar(mean, quat, log_scale, opacity, link_of, link_poses, sensor, rank=None) -> dict:
-    """One env.  mean/quat/log_scale/opacity: the scene's Gaussians (background
-    then link-major); link_of [n]: -1 for background, else the link index whose
-    pose (link_poses [L][7], link -> world) moves it; sensor: dict with q_ws,
-    t_ws (world -> sensor), rows, cols, elev_min, elev_max, near and
-    optionally az_min, az_max (default: a full revolution); rank [n]
-    (optional): the order among Gaussians at equal distance (default: global
-    index).  Returns range [rows, cols], hit [rows, cols]."""
+def _sensor_frame(mean, quat, log_scale, opacity, link_of, link_poses, sensor, rank):
+    """Per Gaussian, sensor frame (RLGK then the sensor pose): G = diag(e^-s)
+    R^T, b = G mu, opacity; and the compositing order (distance |mu|, ties by
+    global index or rank)."""
     mean = np.asarray(mean, np.float64)
     Rg = quat_to_mat(quat)
     s = np.asarray(log_scale, np.float64)
@@ -95,22 +96,26 @@ def render_lidar(mean, quat, log_scale, opacity, link_of, link_poses, sensor, ra
     dist = np.linalg.norm(mu, axis=1)
     tie = np.arange(len(dist)) if rank is None else np.asarray(rank)
     order = np.lexsort((tie, dist))
-    D = ray_directions(sensor["rows"], sensor["cols"], sensor["elev_min"], sensor["elev_max"],
-                       sensor.get("az_min", 0.0), sensor.get("az_max", 2.0 * np.pi))
-    rows, cols = D.shape[:2]
-    rng = np.zeros((rows, cols))
-    hit = np.zeros((rows, cols))
-    Go, bo, oo = G[order], b[order], o[order]
-    for j in range(rows):
-        a = np.einsum("nij,cj->cni", Go, D[j])           # [cols, n, 3]
+    return G[order], b[order], o[order]
+
+
+def _composite_rays(Go, bo, oo, near, D) -> tuple:
+    """Rays D [m, 3] (unit, sensor frame) over Gaussians in compositing order:
+    (range [m], hit [m])."""
+    m = D.shape[0]
+    rng = np.zeros(m)
+    hit = np.zeros(m)
+    for c0 in range(0, m, 64):
+        Dc = D[c0:c0 + 64]
+        a = np.einsum("nij,cj->cni", Go, Dc)           # [c, n, 3]
         aa = (a * a).sum(-1)
         ab = (a * bo[None]).sum(-1)
         cr = np.cross(a, np.broadcast_to(bo[None], a.shape))
         qmin = (cr * cr).sum(-1) / aa
         tstar = ab / aa
         alpha = np.minimum(0.99, oo[None] * np.exp(-0.5 * qmin))
-        use = (alpha >= 1.0 / 255.0) & (tstar > sensor["near"])
-        for i in range(cols):
+        use = (alpha >= 1.0 / 255.0) & (tstar > near)
+        for i in range(Dc.shape[0]):
             T, acc = 1.0, 0.0
             for k in np.nonzero(use[i])[0]:
                 al = alpha[i, k]
@@ -119,6 +124,32 @@ def render_lidar(mean, quat, log_scale, opacity, link_of, link_poses, sensor, ra
                     break
                 acc += al * T * tstar[i, k]
                 T = Tn
-            hit[j, i] = 1.0 - T
-            rng[j, i] = acc / (1.0 - T) if T < 1.0 else 0.0
+            hit[c0 + i] = 1.0 - T
+            rng[c0 + i] = acc / (1.0 - T) if T < 1.0 else 0.0
+    return rng, hit
+
+
+def render_lidar(mean, quat, log_scale, opacity, link_of, link_poses, sensor, rank=None) -> dict:
+    """One env.  mean/quat/log_scale/opacity: the scene's Gaussians (background
+    then link-major); link_of [n]: -1 for background, else the link index whose
+    pose (link_poses [L][7], link -> world) moves it; sensor: dict with q_ws,
+    t_ws (world -> sensor), rows, cols, elev_min, elev_max, near and
+    optionally az_min, az_max (default: a full revolution); rank [n]
+    (optional): the order among Gaussians at equal distance (default: global
+    index).  Returns range [rows, cols], hit [rows, cols]."""
+    Go, bo, oo = _sensor_frame(mean, quat, log_scale, opacity, link_of, link_poses, sensor, rank)
+    D = ray_directions(sensor["rows"], sensor["cols"], sensor["elev_min"], sensor["elev_max"],
+                       sensor.get("az_min", 0.0), sensor.get("az_max", 2.0 * np.pi))
+    rows, cols = D.shape[:2]
+    rng, hit = _composite_rays(Go, bo, oo, sensor["near"], D.reshape(-1, 3))
+    return {"range": rng.reshape(rows, cols), "hit": hit.reshape(rows, cols)}
+
+
+def render_rays(mean, quat, log_scale, opacity, link_of, link_poses, sensor, dirs, rank=None) -> dict:
+    """One env along the rays dirs [m, 3] (sensor frame, normalised here);
+    sensor: dict with q_ws, t_ws, near.  Returns range [m], hit [m]."""
+    Go, bo, oo = _sensor_frame(mean, quat, log_scale, opacity, link_of, link_poses, sensor, rank)
+    D = np.asarray(dirs, np.float64).reshape(-1, 3)
+    D = D / np.linalg.norm(D, axis=1, keepdims=True)
+    rng, hit = _composite_rays(Go, bo, oo, sensor["near"], D)
     return {"range": rng, "hit": hit}

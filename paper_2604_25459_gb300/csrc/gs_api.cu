@@ -501,6 +501,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     P.nvis = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() + 1 : nullptr;
     P.nfp64 = (s->counters && cap == 0) ? s->neval.as<unsigned long long>() + 2 : nullptr;
     P.lidars = io.lidars;
+    P.cell_pad = io.ray_dirs ? 0.51f : 0.0f;  // a ray anywhere in its cell (+ rounding)
     P.bg_index = s->bg_order.empty() ? nullptr : s->bg_index.as<int>();
     PhaseTimer t2(s, st, GS_PHASE_PROJECT, timers);
     if (io.lidars) CK(launch_project_lidar(P, wt.n_blocks, st), "LiDAR projection");
@@ -536,6 +537,40 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     t4.done(2);
     *launches += 2;
     CK(cudaMemsetAsync(sc.cursor.p, 0, wt.tiles * 4, st), "memset cursors");
+    // arbitrary rays: cells, rays grouped by tile, compositor items (eager only)
+    std::vector<unsigned long long> items;
+    if (io.ray_dirs) {
+        if (cap != 0) return fail(GS_ERR_UNSUPPORTED, "arbitrary-ray scans are not planned");
+        const size_t nr = (size_t)We * (size_t)io.n_rays;
+        CK(s->ray_cell.ensure(nr * 4), "alloc ray cells");
+        CK(s->ray_list.ensure(nr * 4), "alloc ray lists");
+        for (DevBuf* b : {&s->ray_cnt, &s->ray_off, &s->ray_cur, &s->item_cnt, &s->item_off})
+            CK(b->ensure(wt.tiles * 4), "alloc ray tables");
+        for (DevBuf* b : {&s->ray_tot, &s->item_tot}) CK(b->ensure((size_t)We * 8), "alloc ray totals");
+        for (DevBuf* b : {&s->ray_base, &s->item_base}) CK(b->ensure((size_t)(We + 1) * 8), "alloc ray bases");
+        CK(cudaMemsetAsync(s->ray_cnt.p, 0, wt.tiles * 4, st), "memset ray counts");
+        CK(cudaMemsetAsync(s->ray_cur.p, 0, wt.tiles * 4, st), "memset ray cursors");
+        PhaseTimer tr(s, st, GS_PHASE_SCAN, timers);
+        CK(launch_ray_count(io.ray_dirs, io.lidars, wt.envs, We, io.n_rays, s->ray_cell.as<uint32_t>(),
+                            s->ray_cnt.as<uint32_t>(), status, st),
+           "ray cells");
+        CK(launch_scan(wt.envs, s->ray_cnt.as<uint32_t>(), s->ray_off.as<uint32_t>(),
+                       s->ray_tot.as<unsigned long long>(), s->ray_base.as<unsigned long long>(), We, st),
+           "ray scan");
+        CK(launch_ray_scatter(wt.envs, We, io.n_rays, s->ray_cell.as<uint32_t>(), s->ray_off.as<uint32_t>(),
+                              s->ray_cur.as<uint32_t>(), s->ray_list.as<uint32_t>(), s->ray_cnt.as<uint32_t>(),
+                              s->item_cnt.as<uint32_t>(), (unsigned)wt.tiles, st),
+           "ray lists");
+        CK(launch_scan(wt.envs, s->item_cnt.as<uint32_t>(), s->item_off.as<uint32_t>(),
+                       s->item_tot.as<unsigned long long>(), s->item_base.as<unsigned long long>(), We, st),
+           "item scan");
+        tr.done(7);
+        *launches += 7;
+        items.resize((size_t)We + 1);
+        CK(cudaMemcpyAsync(items.data(), s->item_base.p, sizeof(unsigned long long) * (We + 1),
+                           cudaMemcpyDeviceToHost, st),
+           "read items");
+    }
 
     // sub-waves of envs whose keys fit (eager), or the whole wave (planned)
     std::vector<unsigned long long> ebv;
@@ -601,6 +636,18 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.e_end = ebd;
         C.item_begin = wt.host_envs[ea].tile_base;
         C.item_end = wt.host_envs[ebd].tile_base;
+        if (io.ray_dirs) {  // items are chunks of rays (see run_wave's ray binning)
+            C.item_begin = (unsigned)items[(size_t)ea];
+            C.item_end = (unsigned)items[(size_t)ebd];
+            C.ray_dirs = io.ray_dirs;
+            C.ray_cell = s->ray_cell.as<uint32_t>();
+            C.ray_list = s->ray_list.as<uint32_t>();
+            C.ray_cnt = s->ray_cnt.as<uint32_t>();
+            C.ray_off = s->ray_off.as<uint32_t>();
+            C.item_off = s->item_off.as<uint32_t>();
+            C.item_base = s->item_base.as<unsigned long long>();
+            C.n_rays = io.n_rays;
+        }
         C.chunk = chunk;
         C.work = sc.work.as<unsigned int>();
         C.r0 = P.r0;
@@ -1127,12 +1174,18 @@ gs_status gs_render_batch_host(gs_scene s, int n_envs, const float* link_poses, 
     return render_uniform(s, n_envs, link_poses, cams, rgb, depth, alpha, cuda_stream, true);
 }
 
-gs_status gs_render_lidar(gs_scene s, int n_envs, const float* link_poses, const gs_lidar* sensors, float* range,
-                          float* hit, void* cuda_stream) {
+namespace {
+
+// Batch-LiDAR scans on the sensors' (azimuth, beam) grids; with ray_dirs,
+// along the given rays instead (the grid then only bins them).
+gs_status lidar_scan(gs_scene s, int n_envs, const float* link_poses, const gs_lidar* sensors, const float* ray_dirs,
+                     int n_rays, float* range, float* hit, void* cuda_stream) {
     if (!s) return fail(GS_ERR_INVALID, "null scene");
     if (n_envs < 0) return fail(GS_ERR_INVALID, "negative n_envs");
     if (n_envs == 0) return GS_OK;
     if (!sensors || !range) return fail(GS_ERR_INVALID, "null sensors or range output");
+    if (ray_dirs && (n_rays < 1 || n_rays > (1 << 24)))
+        return fail(GS_ERR_INVALID, "n_rays %d outside [1, 2^24]", n_rays);
     const int L = s->D.n_links;
     if (L > 0 && !link_poses) return fail(GS_ERR_INVALID, "null link_poses with %d links", L);
     const int rows = sensors[0].rows, cols = sensors[0].cols;
@@ -1165,11 +1218,11 @@ gs_status gs_render_lidar(gs_scene s, int n_envs, const float* link_poses, const
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     CK(cudaSetDevice(s->device), "set device");
-    const size_t px = (size_t)rows * cols;
-    if (s->D.n == 0) {
+    const size_t px = ray_dirs ? (size_t)n_rays : (size_t)rows * cols;  // outputs per env
+    if (s->D.n == 0 || ray_dirs) {  // rays outside their grid (and an empty scene) read 0
         CK(cudaMemsetAsync(range, 0, (size_t)n_envs * px * 4, st), "clear range");
         if (hit) CK(cudaMemsetAsync(hit, 0, (size_t)n_envs * px * 4, st), "clear hit");
-        return GS_OK;
+        if (s->D.n == 0) return GS_OK;
     }
     const int tw = 16, th = 16;
     std::vector<EnvSpec> specs((size_t)n_envs);
@@ -1189,11 +1242,28 @@ gs_status gs_render_lidar(gs_scene s, int n_envs, const float* link_poses, const
                          &wt));
         WaveIO io{link_poses, nullptr, range, hit, 0};
         io.lidars = s->lidar_tab.as<gs_lidar>();
+        if (ray_dirs) {
+            io.ray_dirs = ray_dirs + (size_t)w.first * (size_t)n_rays * 3;
+            io.n_rays = n_rays;
+        }
         ST(run_wave(s, s->sc, wt, io, tw, th, 1, 0, st, true, &launches, nullptr));
         s->stats.waves++;
     }
     s->stats.kernel_launches = launches;
     return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_render_lidar(gs_scene s, int n_envs, const float* link_poses, const gs_lidar* sensors, float* range,
+                          float* hit, void* cuda_stream) {
+    return lidar_scan(s, n_envs, link_poses, sensors, nullptr, 0, range, hit, cuda_stream);
+}
+
+gs_status gs_render_rays(gs_scene s, int n_envs, const float* link_poses, const gs_lidar* sensors, int n_rays,
+                         const float* ray_dirs, float* range, float* hit, void* cuda_stream) {
+    if (!ray_dirs) return fail(GS_ERR_INVALID, "null ray_dirs");
+    return lidar_scan(s, n_envs, link_poses, sensors, ray_dirs, n_rays, range, hit, cuda_stream);
 }
 
 gs_status gs_scene_contribution(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
@@ -1691,7 +1761,9 @@ void gs_scene_destroy(gs_scene s) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&s->g0, &s->g1, &s->g2, &s->g3, &s->gsh, &s->stage_rgb[0], &s->stage_rgb[1],
                       &s->stage_depth[0], &s->stage_depth[1], &s->stage_alpha[0], &s->stage_alpha[1], &s->poses,
-                      &s->neval, &s->appear, &s->lidar_tab, &s->bg_index, &s->bg_slot};
+                      &s->neval, &s->appear, &s->lidar_tab, &s->bg_index, &s->bg_slot, &s->ray_cell,
+                      &s->ray_list, &s->ray_cnt, &s->ray_off, &s->ray_cur, &s->item_cnt, &s->item_off,
+                      &s->ray_tot, &s->ray_base, &s->item_tot, &s->item_base};
     for (DevBuf* b : bufs) b->release();
     s->sc.release();
     for (auto& m : s->marks) {

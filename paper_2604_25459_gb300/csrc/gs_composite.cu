@@ -441,6 +441,10 @@ __device__ __forceinline__ bool reaches_rect(const float4& A, const float4& B, f
 // the (azimuth, beam) grid, the Gaussian evaluated at its closest approach).
 // MODE 2: the camera form that also counts composited (pixel, splat) pairs
 // into P.neval (MODE 0 leaves the count out of its blend loop).
+// MODE 3: LiDAR along arbitrary rays: an item is a chunk of at most 256 rays
+// of one grid tile (16x16 tiles only); the chunk's rays are counting-sorted by
+// cell so that each warp takes 64 neighbouring rays, and the warp's culling
+// box is the bounding box of its rays' cells instead of a subtile.
 // QUAD: each group of eight lanes owns a 4x4 quadrant of the warp's subtile
 // and walks only the splats whose box reaches that quadrant, dropping it once
 // the quadrant's pixels have terminated.  Small splats (low resolutions)
@@ -459,6 +463,8 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     constexpr int CB = (18 * NT * 2 > kSortBins * 4) ? 18 * NT * 2 : kSortBins * 4;  // >= selection histogram
     constexpr int NW = NT / 32;
     constexpr bool CNT = MODE != 0 || SC;  // count composited pairs
+    constexpr bool LID = MODE == 1 || MODE == 3;  // LiDAR records and ray evaluation
+    static_assert(MODE != 3 || 2 * NT == kRayChunk, "ray chunks: two rays per thread");
     static_assert(CAP * 8 + UB >= kBins * 4, "bin counters alias the key and staging buffers");
     static_assert(kBins % NT == 0, "bins per thread");
     __shared__ __align__(16) unsigned char kbuf[CAP * 8 + UB];  // window keys | sort scratch, staged records
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     uint16_t* cnt = reinterpret_cast<uint16_t*>(cbuf);
     uint32_t* hist = reinterpret_cast<uint32_t*>(cbuf);
     __shared__ uint32_t sG[SC ? NB : 1];  // contribution pass: slot of each staged splat
-    __shared__ float4 sD[MODE == 1 ? NB : 1];  // LiDAR: third row of G of each staged splat
+    __shared__ float4 sD[LID ? NB : 1];  // LiDAR: third row of G of each staged splat
     uint32_t* bins = reinterpret_cast<uint32_t*>(kbuf);  // partition counters (between windows only)
 
     __shared__ unsigned int s_item;
@@ -498,26 +504,47 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     if (first >= P.item_end) break;
     const unsigned int last = min(first + (unsigned)P.chunk, P.item_end);
     for (unsigned int item = first; item < last; ++item) {
-    if (item < e_lo || item >= e_hi) {
-        int lo = P.e_begin, hi = P.e_end - 1;  // env: last e with tile_base <= item
+    int t;
+    uint32_t rchunk = 0;  // MODE 3: chunk of the tile's rays
+    if constexpr (MODE == 3) {
+        int lo = P.e_begin, hi = P.e_end - 1;  // env: last e with item_base[e] <= item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&P.envs[mid].tile_base) <= item) lo = mid; else hi = mid - 1;
+            if (__ldg(&P.item_base[mid]) <= (unsigned long long)item) lo = mid; else hi = mid - 1;
         }
         el = lo;
         e_lo = P.envs[el].tile_base;
         e_hi = e_lo + (unsigned)P.envs[el].T;
+        const uint32_t li = item - (uint32_t)__ldg(&P.item_base[el]);
+        int a = 0, b = P.envs[el].T - 1;  // tile: last t with item_off[t] <= li (empty tiles come before)
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (__ldg(&P.item_off[e_lo + mid]) <= li) a = mid; else b = mid - 1;
+        }
+        t = a;
+        rchunk = li - __ldg(&P.item_off[e_lo + t]);
+    } else {
+        if (item < e_lo || item >= e_hi) {
+            int lo = P.e_begin, hi = P.e_end - 1;  // env: last e with tile_base <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(&P.envs[mid].tile_base) <= item) lo = mid; else hi = mid - 1;
+            }
+            el = lo;
+            e_lo = P.envs[el].tile_base;
+            e_hi = e_lo + (unsigned)P.envs[el].T;
+        }
+        t = (int)(item - e_lo);
     }
     const EnvInfo* Ep = P.envs + el;
     const int W = __ldg(&Ep->W), H = __ldg(&Ep->H), ntx = __ldg(&Ep->ntx);
     const unsigned int tile_base = e_lo;
     const unsigned int n_local = __ldg(&Ep->n_local);
     const unsigned long long pix_base = __ldg(&Ep->pix_base);
-    const int t = (int)(item - tile_base);
     const int tx = t % ntx, ty = t / ntx;
     constexpr int SWX = TW / 8;
-    const int wx0 = tx * TW + (warp % SWX) * 8, wy0 = ty * TH + (warp / SWX) * 8;
-    const int wx1 = wx0 + 7, wy1 = wy0 + 7;
+    int wx0 = tx * TW + (warp % SWX) * 8, wy0 = ty * TH + (warp / SWX) * 8;
+    int wx1 = wx0 + 7, wy1 = wy0 + 7;
     // QUAD: lanes in groups of eight, group q = lane / 8 owning the 4x4 quadrant
     // (q & 1, q >> 1) of the warp's subtile, each lane a column and rows r, r + 2;
     // otherwise lane = column (lane % 8) and rows lane / 8, lane / 8 + 4
@@ -525,9 +552,11 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     const int px = QUAD ? wx0 + 4 * (grp & 1) + (l8 & 3) : wx0 + (lane & 7);
     const int py0 = QUAD ? wy0 + 4 * (grp >> 1) + (l8 >> 2) : wy0 + (lane >> 3);
     const int py1 = QUAD ? py0 + 2 : py0 + 4;
-    const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
+    bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
     const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f, fpy1 = (float)py1 + 0.5f;
     float3 dir0 = make_float3(0.f, 0.f, 0.f), dir1 = dir0;  // LiDAR: the lane's two rays
+    int cx0 = px, cy0 = py0, cx1 = px, cy1 = py1;           // LiDAR: their grid cells
+    int ray0 = -1, ray1 = -1;                               // MODE 3: their indices
     float near_range = 0.0f;
     if constexpr (MODE == 1) {
         const gs_lidar* Ld = P.lidars + el;
@@ -542,6 +571,59 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         dir0 = make_float3(c0 * cp, c0 * sp, s0);
         dir1 = make_float3(c1 * cp, c1 * sp, s1);
         near_range = __ldg(&Ld->near_range);
+    }
+    if constexpr (MODE == 3) {
+        // the chunk's rays, counting-sorted by cell (row-major in the tile)
+        uint32_t* cellh = reinterpret_cast<uint32_t*>(kbuf);  // 256 counters
+        uint32_t* srt = cellh + 256;                          // 256 ray indices
+        const size_t renv = (size_t)el * (size_t)P.n_rays;
+        const uint32_t rc = __ldg(&P.ray_cnt[e_lo + t]);
+        const uint32_t nr = min((uint32_t)kRayChunk, rc - rchunk * (uint32_t)kRayChunk);
+        const size_t lbase = renv + __ldg(&P.ray_off[e_lo + t]) + (size_t)rchunk * kRayChunk;
+        for (int c = tid; c < 256; c += NT) cellh[c] = 0u;
+        __syncthreads();
+        uint32_t rr[2], cc[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint32_t k = (uint32_t)(tid + u * NT);
+            rr[u] = k < nr ? __ldg(&P.ray_list[lbase + k]) : 0xffffffffu;
+            cc[u] = k < nr ? (__ldg(&P.ray_cell[renv + rr[u]]) & 255u) : 0u;
+            if (k < nr) atomicAdd(&cellh[cc[u]], 1u);
+        }
+        __syncthreads();
+        const uint32_t h0 = cellh[2 * tid], h1 = cellh[2 * tid + 1];
+        const uint32_t ex = block_excl_scan_u32<NT>(h0 + h1, red);
+        cellh[2 * tid] = ex;
+        cellh[2 * tid + 1] = ex + h0;
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (rr[u] != 0xffffffffu) srt[atomicAdd(&cellh[cc[u]], 1u)] = rr[u];
+        __syncthreads();
+        const uint32_t s0 = (uint32_t)(warp * 64 + lane), s1 = s0 + 32u;
+        ray0 = s0 < nr ? (int)srt[s0] : -1;
+        ray1 = s1 < nr ? (int)srt[s1] : -1;
+        __syncthreads();  // kbuf holds the windows from here on
+        in0 = ray0 >= 0;
+        in1 = ray1 >= 0;
+        near_range = __ldg(&P.lidars[el].near_range);
+        auto take = [&](int r, int& ci, int& cj, float3& d) {
+            const uint32_t c = __ldg(&P.ray_cell[renv + (uint32_t)r]) & 255u;
+            ci = tx * 16 + (int)(c & 15u);
+            cj = ty * 16 + (int)(c >> 4);
+            const float* v = P.ray_dirs + (renv + (uint32_t)r) * 3;
+            const float x = v[0], y = v[1], z = v[2];
+            const float inv = 1.0f / sqrtf(x * x + y * y + z * z);
+            d = make_float3(x * inv, y * inv, z * inv);
+        };
+        if (in0) take(ray0, cx0, cy0, dir0);
+        if (in1) take(ray1, cx1, cy1, dir1);
+        // the warp's culling box: the cells of its rays
+        const int big = 1 << 30;
+        wx0 = __reduce_min_sync(0xffffffffu, min(in0 ? cx0 : big, in1 ? cx1 : big));
+        wy0 = __reduce_min_sync(0xffffffffu, min(in0 ? cy0 : big, in1 ? cy1 : big));
+        wx1 = __reduce_max_sync(0xffffffffu, max(in0 ? cx0 : -big, in1 ? cx1 : -big));
+        wy1 = __reduce_max_sync(0xffffffffu, max(in0 ? cy0 : -big, in1 ? cy1 : -big));
     }
     // LiDAR: alpha and t* of a staged Gaussian (b, o | g0 | g1 | g2) on ray d
     auto ray_eval = [&](const float4& A, const float4& B, const float4& C, const float4& D, const float3& d,
@@ -628,7 +710,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                     const float4 q2 = P.r2[ri];
                     const uint32_t rx = __float_as_uint(q1.w), ry = __float_as_uint(q2.w);
                     sA[s] = q0;
-                    if constexpr (MODE == 1) {
+                    if constexpr (LID) {
                         // g2 = |g2| (g0 x g1) / (|g0| |g1|): the rows of G are orthogonal
                         const float glen2 = __uint_as_float(P.r3[ri].w);
                         const float cx = q1.y * q2.z - q1.z * q2.y, cy = q1.z * q2.x - q1.x * q2.z,
@@ -664,7 +746,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         ov = R.x <= wx1 && R.x + R.y >= wx0 && R.z <= wy1 && R.z + R.w >= wy0;
                         // large splats: their box overstates the ellipse most (a box
                         // under 24 px in width + height is kept as it is)
-                        if (MODE != 1 && ov && R.y + R.w >= 24)
+                        if (!LID && ov && R.y + R.w >= 24)
                             ov = reaches_rect(sA[j], sB[j], (float)wx0 + 0.5f, (float)wy0 + 0.5f);
                     }
                     uint32_t m;
@@ -714,10 +796,20 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             h11 = h11 && x1 && (unsigned)(py1 - R1.z) <= (unsigned)R1.w;
                             h20 = h20 && x2 && (unsigned)(py0 - R2.z) <= (unsigned)R2.w;
                             h21 = h21 && x2 && (unsigned)(py1 - R2.z) <= (unsigned)R2.w;
+                        } else if constexpr (MODE == 3) {
+                            const int4 R1 = sR[j1];
+                            const int4 R2 = sR[j2];
+                            auto inb = [](const int4& R, int x, int y) {
+                                return (unsigned)(x - R.x) <= (unsigned)R.y && (unsigned)(y - R.z) <= (unsigned)R.w;
+                            };
+                            h10 = h10 && inb(R1, cx0, cy0);
+                            h11 = h11 && inb(R1, cx1, cy1);
+                            h20 = h20 && inb(R2, cx0, cy0);
+                            h21 = h21 && inb(R2, cx1, cy1);
                         }
-                        if (MODE == 1 && (h10 || h11 || h20 || h21)) {
-                            const float4 A1 = sA[j1], B1 = sB[j1], C1 = sC[j1], D1 = sD[MODE == 1 ? j1 : 0];
-                            const float4 A2 = sA[j2], B2 = sB[j2], C2 = sC[j2], D2 = sD[MODE == 1 ? j2 : 0];
+                        if (LID && (h10 || h11 || h20 || h21)) {
+                            const float4 A1 = sA[j1], B1 = sB[j1], C1 = sC[j1], D1 = sD[LID ? j1 : 0];
+                            const float4 A2 = sA[j2], B2 = sB[j2], C2 = sC[j2], D2 = sD[LID ? j2 : 0];
                             float a10, a11, a20, a21, t10, t11, t20, t21;
                             ray_eval(A1, B1, C1, D1, dir0, a10, t10);
                             ray_eval(A1, B1, C1, D1, dir1, a11, t11);
@@ -740,7 +832,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                                 if constexpr (CNT) ++ncomp;
                                 blend(a21, none, t21, Tp.y, rp.y, gp.y, bp.y, dp.y, done1);
                             }
-                        } else if (MODE != 1 && (h10 || h11 || h20 || h21)) {
+                        } else if (!LID && (h10 || h11 || h20 || h21)) {
                             const float4 A1 = sA[j1], B1 = sB[j1];
                             const float4 A2 = sA[j2], B2 = sB[j2];
                             const float2 a1 = splat_alpha2(A1, B1, fpx, fpy);
@@ -1072,7 +1164,20 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         else if (P.depth) P.depth[pix] = dep;
         if (P.alpha) P.alpha[pix] = a;
     };
-    if (MODE == 1) {  // range and hit per ray
+    if (MODE == 3) {  // range and hit per ray, at the ray's index
+        if (in0) {
+            const size_t o = pix_base + (size_t)ray0;
+            const float a = 1.0f - Tp.x;
+            P.depth[o] = a > 0.0f ? dp.x / a : 0.0f;
+            if (P.alpha) P.alpha[o] = a;
+        }
+        if (in1) {
+            const size_t o = pix_base + (size_t)ray1;
+            const float a = 1.0f - Tp.y;
+            P.depth[o] = a > 0.0f ? dp.y / a : 0.0f;
+            if (P.alpha) P.alpha[o] = a;
+        }
+    } else if (MODE == 1) {  // range and hit per ray
         if (in0) {
             const size_t pix = pix_base + (size_t)py0 * W + px;
             const float a = 1.0f - Tp.x;
@@ -1142,6 +1247,7 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
         return cudaErrorInvalidValue;
     if (P.lidars) {  // LiDAR scans run on 16x16 tiles only
         if (P.tile_w != 16 || P.tile_h != 16 || P.score) return cudaErrorInvalidValue;
+        if (P.ray_list) return launch_tiles<16, 16, false, 3>(P, st, ctas);
         return launch_tiles<16, 16, false, 1>(P, st, ctas);
     }
     if (P.score) {  // the contribution pass runs on 16x16 tiles only

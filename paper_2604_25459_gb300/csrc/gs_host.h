@@ -111,6 +111,11 @@ struct gs_scene_s {
     gsb::DevBuf neval;
     gsb::DevBuf appear;  // appearance parameters copied from the host (observation form)
     gsb::DevBuf lidar_tab;  // the current wave's LiDAR sensors
+    // arbitrary-ray scans: per ray its cell, the rays grouped by tile, per
+    // (env, tile) ray counts, offsets, cursors, item counts and offsets, per
+    // env the scans' totals and bases
+    gsb::DevBuf ray_cell, ray_list, ray_cnt, ray_off, ray_cur, item_cnt, item_off, ray_tot, ray_base, item_tot,
+        item_base;
     // storage order of the background: bg_order[k] is the caller's index of
     // the background Gaussian stored at position k; device copies of it
     // (bg_index) and of its inverse (bg_slot), int32
@@ -136,6 +141,8 @@ struct WaveIO {
     const gs_appearance* appear = nullptr;  // device, indexed by the wave's env
     float* score = nullptr;      // contribution pass (no images)
     const gs_lidar* lidars = nullptr;  // LiDAR scan: device table of the wave's sensors
+    const float* ray_dirs = nullptr;   // with lidars: arbitrary rays [wave env][n_rays][3] (sensor frame)
+    int n_rays = 0;
 };
 
 struct WaveTables {       // device copies of one wave's tables

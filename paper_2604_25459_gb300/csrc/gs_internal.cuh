@@ -39,6 +39,7 @@ enum : uint32_t {
     kStBadPose = 1u,     // zero or non-finite link pose quaternion
     kStBadScene = 2u,    // zero or non-finite Gaussian quaternion at scene build
     kStOverflow = 4u,    // intersection keys beyond the capacity (planned launches) or a corrupted bucket
+    kStBadRay = 8u,      // a ray direction outside its sensor's binning grid (or zero)
 };
 
 // Row-major rigid transform camera <- frame, plus the camera centre in that frame.
@@ -118,6 +119,8 @@ struct ProjParams {
     unsigned long long* nfp64; // nullable: counter of (env, Gaussian) pairs whose conic took the FP64 branch
     const gs_lidar* lidars;    // LiDAR projection only: per env of the wave
     const int* bg_index;       // nullable: caller's index of the background Gaussian in slot j (into r3.w)
+    float cell_pad;            // LiDAR: grid boxes widened by this many cells (arbitrary rays: a ray
+                               // anywhere in a cell, not only at its centre)
 };
 
 struct BinParams {
@@ -180,6 +183,16 @@ struct CompParams {
     const gs_lidar* lidars;  // nullable: LiDAR scan (range in depth, hit in alpha), per env of the wave
     const uint4* r3;         // LiDAR scan: records' fourth word (|g2|)
     uint32_t* status;
+    // Arbitrary rays (set with lidars): items are (env, tile, chunk of <= 256
+    // rays); outputs are indexed by ray, at envs[e].pix_base + ray.
+    const float* ray_dirs;         // [wave env][n_rays][3], sensor frame
+    const uint32_t* ray_cell;      // [wave env][n_rays]: tile << 8 | cell in tile (row-major 16x16)
+    const uint32_t* ray_list;      // [wave env][n_rays]: ray indices grouped by tile
+    const uint32_t* ray_cnt;       // per (env, tile) at tile_base: rays in the tile
+    const uint32_t* ray_off;       // per (env, tile): first entry of the tile in the env's ray_list
+    const uint32_t* item_off;      // per (env, tile): first item of the tile within its env
+    const unsigned long long* item_base;  // per wave env (+1): first item of the env
+    int n_rays;
 };
 
 // Launchers (return cudaGetLastError()).
@@ -197,6 +210,17 @@ cudaError_t launch_project(const DevGaussians& D, const ProjParams& P, int n_blo
 // diag(e^-s) R^T in the sensor frame and b = G mu; ranges over the
 // (azimuth, beam) grid.
 cudaError_t launch_project_lidar(const ProjParams& P, int n_blocks, cudaStream_t st);
+// Arbitrary rays, per wave: the cell of every ray on its sensor's binning
+// grid (zero and out-of-grid directions flagged and left out) and the rays per
+// (env, tile); then the rays grouped by tile and the compositor's items
+// (chunks of at most kRayChunk rays per tile).  ray_cnt and ray_cur are zeroed
+// by the caller.
+constexpr int kRayChunk = 256;
+cudaError_t launch_ray_count(const float* dirs, const gs_lidar* lidars, const EnvInfo* envs, int We, int n_rays,
+                             uint32_t* cell, uint32_t* cnt, uint32_t* status, cudaStream_t st);
+cudaError_t launch_ray_scatter(const EnvInfo* envs, int We, int n_rays, const uint32_t* cell, const uint32_t* off,
+                               uint32_t* cur, uint32_t* list, const uint32_t* cnt, uint32_t* item_cnt,
+                               unsigned int tiles, cudaStream_t st);
 // grid.x covers the largest env's mask words; max_T sizes the shared histogram
 cudaError_t launch_count(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st);
 cudaError_t launch_scan(const EnvInfo* envs, const uint32_t* counts, uint32_t* off_local,

@@ -13,6 +13,13 @@
 // point with alpha >= 1/255 (q <= q*) lies within r = sqrt(q*) max_k |f_k| of
 // mu: the rays that can reach it lie within the cone of half-angle
 // asin(r / |mu|).
+//
+// Arbitrary rays (non-repetitive scan patterns) reuse the grid as a binning
+// structure: each ray falls in one cell of its sensor's (azimuth, beam) grid,
+// the Gaussians' grid boxes are widened by half a cell (so they hold every
+// cell that a direction inside the cone can fall in, not only the cells whose
+// centres lie inside it), and the compositor walks a tile's keys for the rays
+// of that tile.
 #include "gs_internal.cuh"
 
 namespace gsb {
@@ -84,14 +91,16 @@ __global__ void __launch_bounds__(256) k_project_lidar(ProjParams P) {
                 if (reach < dist) {
                     const float rho = asinf(fminf(1.0f, reach / dist)) * 1.001f + 1e-5f;
                     const float thc = asinf(fmaxf(-1.0f, fminf(1.0f, mz / dist)));
-                    any = grid_range(thc - rho, thc + rho, em, (eM - em) / (float)rows, rows, j0, j1);
+                    const float estep = (eM - em) / (float)rows;
+                    any = grid_range(thc - rho - P.cell_pad * estep, thc + rho + P.cell_pad * estep, em, estep, rows,
+                                     j0, j1);
                     if (any && fabsf(thc) + rho < kHalfPi) {
                         const float dphi = asinf(fminf(1.0f, sinf(rho) / cosf(thc))) * 1.001f + 1e-5f;
                         // azimuth relative to the window start, within one turn: [0, 2 pi)
                         const float az0 = __ldg(&L->az_min), step = (__ldg(&L->az_max) - az0) / (float)cols;
                         float rel = atan2f(my, mx) - az0;
                         rel -= kTwoPi * floorf(rel / kTwoPi);
-                        const float lo = rel - dphi, hi = rel + dphi;
+                        const float lo = rel - dphi - P.cell_pad * step, hi = rel + dphi + P.cell_pad * step;
                         // the cone's azimuths in this turn, and their copy one turn away
                         // when the cone crosses 0 (a full revolution then takes the
                         // columns between the two ranges as well)
@@ -154,6 +163,87 @@ __global__ void __launch_bounds__(256) k_project_lidar(ProjParams P) {
 cudaError_t launch_project_lidar(const ProjParams& P, int n_blocks, cudaStream_t st) {
     if (n_blocks == 0) return cudaSuccess;
     k_project_lidar<<<n_blocks, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- arbitrary rays
+
+// Cell of ray r of wave env el: azimuth phi = atan2(y, x) and elevation
+// asin(z / |d|); column floor(((phi - az_min) mod 2 pi) / step) within the
+// window, row floor((theta - elev_min) / estep).  grid: (rays / 256, envs).
+__global__ void __launch_bounds__(256) k_ray_count(const float* __restrict__ dirs, const gs_lidar* lidars,
+                                                   const EnvInfo* envs, int n_rays, uint32_t* cell, uint32_t* cnt,
+                                                   uint32_t* status) {
+    const int el = blockIdx.y;
+    const int r = blockIdx.x * 256 + threadIdx.x;
+    if (r >= n_rays) return;
+    const size_t k = (size_t)el * n_rays + r;
+    const float dx = dirs[3 * k], dy = dirs[3 * k + 1], dz = dirs[3 * k + 2];
+    const gs_lidar* L = lidars + el;
+    const EnvInfo& E = envs[el];
+    const float n = sqrtf(dx * dx + dy * dy + dz * dz);
+    bool ok = n > 0.0f && isfinite(n);
+    int i = 0, j = 0;
+    if (ok) {
+        const float em = __ldg(&L->elev_min), eM = __ldg(&L->elev_max);
+        const float az0 = __ldg(&L->az_min), span = __ldg(&L->az_max) - az0;
+        const float th = asinf(fmaxf(-1.0f, fminf(1.0f, dz / n)));
+        float rel = atan2f(dy, dx) - az0;
+        rel -= kTwoPi * floorf(rel / kTwoPi);
+        const float fi = floorf(rel / (span / (float)E.W));
+        const float fj = floorf((th - em) / ((eM - em) / (float)E.H));
+        ok = rel < span && fi >= 0.0f && fi < (float)E.W && fj >= 0.0f && fj < (float)E.H;
+        i = (int)fi;
+        j = (int)fj;
+    }
+    if (!ok) {
+        cell[k] = 0xffffffffu;
+        atomicOr(status, kStBadRay);
+        return;
+    }
+    const int t = (j >> 4) * E.ntx + (i >> 4);
+    cell[k] = ((uint32_t)t << 8) | ((uint32_t)(j & 15) << 4) | (uint32_t)(i & 15);
+    atomicAdd(cnt + E.tile_base + t, 1u);
+}
+
+// Rays grouped by tile: list[el][off[tile] + rank] = r.
+__global__ void __launch_bounds__(256) k_ray_scatter(const EnvInfo* envs, int n_rays, const uint32_t* cell,
+                                                     const uint32_t* off, uint32_t* cur, uint32_t* list) {
+    const int el = blockIdx.y;
+    const int r = blockIdx.x * 256 + threadIdx.x;
+    if (r >= n_rays) return;
+    const size_t k = (size_t)el * n_rays + r;
+    const uint32_t c = cell[k];
+    if (c == 0xffffffffu) return;
+    const unsigned int tb = envs[el].tile_base;
+    const uint32_t t = c >> 8;
+    const uint32_t pos = off[tb + t] + atomicAdd(cur + tb + t, 1u);
+    list[(size_t)el * n_rays + pos] = (uint32_t)r;
+}
+
+// Compositor items per (env, tile): chunks of at most kRayChunk rays.
+__global__ void __launch_bounds__(256) k_ray_items(const EnvInfo* envs, int We, const uint32_t* cnt,
+                                                   uint32_t* item_cnt) {
+    const unsigned int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= envs[We].tile_base) return;
+    item_cnt[i] = (cnt[i] + (uint32_t)kRayChunk - 1u) / (uint32_t)kRayChunk;
+}
+
+cudaError_t launch_ray_count(const float* dirs, const gs_lidar* lidars, const EnvInfo* envs, int We, int n_rays,
+                             uint32_t* cell, uint32_t* cnt, uint32_t* status, cudaStream_t st) {
+    if (We == 0 || n_rays == 0) return cudaSuccess;
+    k_ray_count<<<dim3((unsigned)((n_rays + 255) / 256), (unsigned)We), 256, 0, st>>>(dirs, lidars, envs, n_rays,
+                                                                                      cell, cnt, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ray_scatter(const EnvInfo* envs, int We, int n_rays, const uint32_t* cell, const uint32_t* off,
+                               uint32_t* cur, uint32_t* list, const uint32_t* cnt, uint32_t* item_cnt,
+                               unsigned int tiles, cudaStream_t st) {
+    if (We == 0 || n_rays == 0) return cudaSuccess;
+    k_ray_scatter<<<dim3((unsigned)((n_rays + 255) / 256), (unsigned)We), 256, 0, st>>>(envs, n_rays, cell, off,
+                                                                                        cur, list);
+    k_ray_items<<<(tiles + 255) / 256, 256, 0, st>>>(envs, We, cnt, item_cnt);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,7 @@ _SIGS = {
     "gs_render_batch_obs": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_scene_contribution": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 4),
     "gs_render_lidar": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 5),
+    "gs_render_rays": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int] + [C.c_void_p] * 4),
     "gs_render_batch_obs_host": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_plan_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "gs_plan_launch": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
@@ -360,6 +361,28 @@ class Scene:
             stream = torch.cuda.current_stream()
         _check(lib().gs_render_lidar(self._h, E, _ptr(link_poses), _ptr(sensors), _ptr(rng), _ptr(hit),
                                      _stream_handle(stream)))
+        return rng, hit
+
+    def render_rays(self, link_poses, sensors: np.ndarray, ray_dirs, rng=None, hit=None, want_hit: bool = True,
+                    stream=None):
+        """Batch-LiDAR along arbitrary rays (gs_render_rays): sensors numpy
+        LIDAR_DTYPE [E] (pose, near range, binning grid); ray_dirs CUDA float32
+        [E, R, 3] in the sensor frame; returns (range [E, R], hit [E, R] or
+        None) CUDA tensors."""
+        import torch
+
+        sensors = np.ascontiguousarray(sensors, dtype=LIDAR_DTYPE)
+        E, R = int(ray_dirs.shape[0]), int(ray_dirs.shape[1])
+        if E != int(sensors.shape[0]) or tuple(ray_dirs.shape[2:]) != (3,):
+            raise ValueError("ray_dirs must be [n_envs, n_rays, 3] with one sensor per env")
+        if rng is None:
+            rng = torch.empty((E, R), dtype=torch.float32, device="cuda")
+        if hit is None and want_hit:
+            hit = torch.empty((E, R), dtype=torch.float32, device="cuda")
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        _check(lib().gs_render_rays(self._h, E, _ptr(link_poses), _ptr(sensors), R, _ptr(ray_dirs), _ptr(rng),
+                                    _ptr(hit), _stream_handle(stream)))
         return rng, hit
 
     def contribution(self, link_poses, cams: np.ndarray, scores=None, stream=None):

@@ -110,7 +110,7 @@ def _rng(*key: int) -> np.random.Generator:
     return np.random.default_rng([int(k) for k in key])
 
 
-_STREAM = {"bg": 1, "robot": 2, "joints": 3, "cams": 4, "tiny": 5, "c0": 6}
+_STREAM = {"bg": 1, "robot": 2, "joints": 3, "cams": 4, "tiny": 5, "c0": 6, "rays": 11}
 
 
 def _attributes(rng: np.random.Generator, n: int) -> tuple:
@@ -323,6 +323,24 @@ def make_tiny(seed: int = 0, n: int = 48, width: int = 32, height: int = 24, f: 
     t_cw = -pos
     cams = make_cameras(n_envs, f, f, width / 2.0, height / 2.0, width, height, q_cw, t_cw)
     return Workload("tiny", bg, offsets, links, poses, cams)
+
+
+def rosette_rays(n_envs: int, n_rays: int, seed: int = 0, half_fov: float = 0.6, turns: float = 37.0,
+                 petals: float = 7.3) -> np.ndarray:
+    """Ray directions of a non-repetitive scan pattern, float32 [E][R][3] in
+    the sensor frame (x forward, y left, z up): a rosette inside a cone of
+    half-angle half_fov about +x, ray k at polar angle
+    half_fov |sin(petals u)| and azimuth about the axis 2 pi u, u = turns
+    (k + phase_e) / R, with a seeded phase per env so that frames differ (the
+    pattern does not repeat; densest near the axis, as such sensors are)."""
+    rng = _rng(seed, _STREAM["rays"])
+    phase = rng.uniform(0.0, float(n_rays), size=(n_envs, 1))
+    u = turns * (np.arange(n_rays)[None, :] + phase) / n_rays
+    rho = half_fov * np.abs(np.sin(petals * u))
+    psi = 2.0 * np.pi * u
+    # direction at polar angle rho from +x, rotated by psi about +x
+    d = np.stack([np.cos(rho), np.sin(rho) * np.cos(psi), np.sin(rho) * np.sin(psi)], -1)
+    return np.ascontiguousarray(d, dtype=np.float32)
 
 
 def to_half(a: np.ndarray, dtype: str) -> np.ndarray:

@@ -93,3 +93,110 @@ def test_lidar_argument_checks_and_empty_scene():
             scene.render_lidar(None, bad)
         assert ei.value.status == gsbatch.GS_ERR_INVALID
     scene.close()
+
+
+# ---------------------------------------------------------------- arbitrary rays
+
+def _ray_sensors(E, rows=48, cols=64, seed=4):
+    """Sensors whose (azimuth, beam) grid only bins the rays: +-0.65 rad both ways."""
+    s = _sensors(E, rows=rows, cols=cols, seed=seed, az=(-0.65, 0.65))
+    s["elev_min"], s["elev_max"] = -0.65, 0.65
+    return s
+
+
+def _oracle_rays(w, e, sen, dirs):
+    bg, lk = w.background, w.links
+    cat = lambda f: np.concatenate([getattr(bg, f), getattr(lk, f)])
+    link_of = np.concatenate([np.full(bg.n, -1), np.repeat(np.arange(w.n_links), np.diff(w.link_offsets))])
+    return lidar.render_rays(cat("mean"), cat("quat"), cat("log_scale"), cat("opacity"), link_of, w.link_poses[e],
+                             dict(q_ws=sen["q_ws"].astype(float), t_ws=sen["t_ws"].astype(float),
+                                  near=float(sen["near_range"])), dirs)
+
+
+def _check_scan(g_r, g_h, ref, label):
+    dh = np.abs(g_h - ref["hit"])
+    both = (ref["hit"] >= 0.5) & (g_h >= 0.5)
+    rel = np.abs(g_r - ref["range"])[both] / ref["range"][both]
+    print(label, "rays hit >= 0.5:", int(both.sum()), "of", g_h.size, "hit max", dh.max(), "p99",
+          np.quantile(dh, 0.99), "range rel max", rel.max() if rel.size else None)
+    assert ref["hit"].max() > 0.5 and both.sum() > 20
+    assert np.quantile(dh, 0.99) <= 2e-3 and dh.max() <= 0.05
+    assert np.quantile(rel, 0.99) <= 1e-4 and rel.max() <= 1e-2
+
+
+def test_rays_match_oracle():
+    """A non-repetitive (rosette) scan pattern, a different phase per env,
+    with the robot's links moving, against the FP64 ray-list oracle."""
+    import torch
+
+    ensure_built()
+    w = synth.make_c1(n_envs=2, width=64, height=48, f=50.0, n_bg=8_000, per_link=200)
+    dirs = synth.rosette_rays(w.n_envs, 3000, seed=3)
+    sens = _ray_sensors(w.n_envs)
+    scene = gsbatch.scene_from_workload(w)
+    rng, hit = scene.render_rays(torch.from_numpy(w.link_poses).cuda(), sens, torch.from_numpy(dirs).cuda())
+    torch.cuda.synchronize()
+    scene.sync_status()
+    g_r, g_h = rng.cpu().numpy(), hit.cpu().numpy()
+    scene.close()
+    for e in range(w.n_envs):
+        _check_scan(g_r[e], g_h[e], _oracle_rays(w, e, sens[e], dirs[e]), f"rays env {e}")
+
+
+def test_rays_of_a_grid_scan_like_the_grid():
+    """The rays of a rotating scan's grid, given as a list (shuffled), scan
+    like the grid form within the FP32 rounding of their directions."""
+    import torch
+
+    ensure_built()
+    w = synth.make_c1(n_envs=2, width=64, height=48, f=50.0, n_bg=8_000, per_link=200)
+    sens = _sensors(w.n_envs, rows=16, cols=128)
+    scene = gsbatch.scene_from_workload(w)
+    poses = torch.from_numpy(w.link_poses).cuda()
+    g_rng, g_hit = scene.render_lidar(poses, sens)
+    D = lidar.ray_directions(16, 128, -0.5, 0.35).reshape(-1, 3)
+    perm = np.random.default_rng(8).permutation(len(D))
+    dirs = np.ascontiguousarray(np.broadcast_to(D[perm], (w.n_envs,) + D.shape), np.float32)
+    r_rng, r_hit = scene.render_rays(poses, sens, torch.from_numpy(dirs).cuda())
+    torch.cuda.synchronize()
+    scene.sync_status()
+    scene.close()
+    g_r = g_rng.cpu().numpy().reshape(w.n_envs, -1)[:, perm]
+    g_h = g_hit.cpu().numpy().reshape(w.n_envs, -1)[:, perm]
+    for e in range(w.n_envs):
+        _check_scan(r_rng.cpu().numpy()[e], r_hit.cpu().numpy()[e], {"range": g_r[e], "hit": g_h[e]},
+                    f"grid rays env {e}")
+
+
+def test_rays_outside_the_grid_and_argument_checks():
+    """A zero direction and one outside the binning grid read 0 and set the
+    status word; every other ray is bit-identical to the scan without them."""
+    import torch
+
+    ensure_built()
+    w = synth.make_c1(n_envs=2, width=64, height=48, f=50.0, n_bg=8_000, per_link=200)
+    dirs = synth.rosette_rays(w.n_envs, 1000, seed=5)
+    sens = _ray_sensors(w.n_envs)
+    scene = gsbatch.scene_from_workload(w)
+    poses = torch.from_numpy(w.link_poses).cuda()
+    r0, h0 = scene.render_rays(poses, sens, torch.from_numpy(dirs).cuda())
+    torch.cuda.synchronize()
+    scene.sync_status()
+    bad = dirs.copy()
+    bad[0, 10] = 0.0                  # zero direction
+    bad[1, 20] = [-1.0, 0.0, 0.0]     # behind the sensor: outside the +-0.65 rad window
+    r1, h1 = scene.render_rays(poses, sens, torch.from_numpy(bad).cuda())
+    torch.cuda.synchronize()
+    with pytest.raises(gsbatch.GsError) as ei:
+        scene.sync_status()
+    assert ei.value.status == gsbatch.GS_ERR_DEVICE
+    r0, h0, r1, h1 = (t.cpu().numpy() for t in (r0, h0, r1, h1))
+    assert r1[0, 10] == 0 and h1[0, 10] == 0 and r1[1, 20] == 0 and h1[1, 20] == 0
+    keep = np.ones(r0.shape, bool)
+    keep[0, 10] = keep[1, 20] = False
+    np.testing.assert_array_equal(r1[keep], r0[keep])
+    np.testing.assert_array_equal(h1[keep], h0[keep])
+    with pytest.raises(gsbatch.GsError) as ei:  # no rays
+        scene.render_rays(poses, sens, torch.zeros((w.n_envs, 0, 3), device="cuda"))
+    assert ei.value.status == gsbatch.GS_ERR_INVALID
+    scene.close()

@@ -655,6 +655,56 @@ def test_lidar_single_gaussian_closed_forms():
     assert abs(out["range"][j, i] - D) < 1e-12
 
 
+def test_lidar_ray_list_closed_forms_off_grid():
+    """Arbitrary rays (non-repetitive scan patterns): an isotropic Gaussian
+    (sigma) at distance D along a direction d that is on no grid: the ray d
+    gives hit = o and range = D; a ray at angle delta from d gives q_min =
+    (D sin delta)^2 / sigma^2 at t* = D cos delta.  Directions need not be
+    unit length."""
+    from oracle import lidar
+
+    sen = dict(q_ws=np.array([1.0, 0, 0, 0]), t_ws=np.zeros(3), near=0.05)
+    d = np.array([0.8, -0.35, 0.21])
+    d /= np.linalg.norm(d)
+    D, sig, o = 4.0, 0.06, 0.8
+    ax = np.cross(d, [0.0, 0.0, 1.0])
+    ax /= np.linalg.norm(ax)
+    deltas = np.array([0.0, 0.004, 0.011, 0.02])
+    rays = [np.cos(t) * d + np.sin(t) * ax for t in deltas]
+    rays = np.array(rays) * np.array([[1.0], [2.5], [0.3], [7.0]])  # arbitrary lengths
+    out = lidar.render_rays([D * d], [[1, 0, 0, 0]], [[np.log(sig)] * 3], [o], [-1], None, sen, rays)
+    a = o * np.exp(-0.5 * (D * np.sin(deltas)) ** 2 / sig ** 2)
+    keep = a >= 1 / 255
+    np.testing.assert_allclose(out["hit"][keep], a[keep], rtol=1e-12)
+    np.testing.assert_allclose(out["range"][keep], (D * np.cos(deltas))[keep], rtol=1e-12)
+    assert np.all(out["hit"][~keep] == 0) and np.all(out["range"][~keep] == 0)
+
+
+def test_lidar_ray_list_of_grid_rays_equals_grid_scan():
+    """A ray list holding a grid's rays (in a shuffled order) scans like the
+    grid, ray for ray (to the rounding of re-normalising the directions), with
+    links moving their Gaussians."""
+    from oracle import lidar
+
+    rng = np.random.default_rng(21)
+    n = 60
+    mean = np.concatenate([rng.uniform(-3, 3, (40, 3)) + [4.0, 0, 0], rng.normal(0, 0.1, (20, 3))])
+    quat = rng.normal(size=(n, 4))
+    ls = np.log(rng.uniform(0.05, 0.4, (n, 3)))
+    op = rng.uniform(0.3, 0.95, n)
+    link_of = np.array([-1] * 40 + [0] * 10 + [1] * 10)
+    poses = np.array([[1, 0, 0, 0, 2.0, 0.5, 0.1], [0.9, 0.1, 0.3, 0.0, 1.5, -0.4, 0.2]])
+    sen = _sensor(rows=6, cols=40, q=(0.98, 0.0, 0.05, 0.1), t=(0.1, 0.0, -0.2))
+    sen["az_min"], sen["az_max"] = -1.2, 1.4
+    grid = lidar.render_lidar(mean, quat, ls, op, link_of, poses, sen)
+    D = lidar.ray_directions(6, 40, sen["elev_min"], sen["elev_max"], -1.2, 1.4).reshape(-1, 3)
+    perm = rng.permutation(len(D))
+    out = lidar.render_rays(mean, quat, ls, op, link_of, poses, sen, D[perm])
+    np.testing.assert_allclose(out["hit"], grid["hit"].reshape(-1)[perm], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(out["range"], grid["range"].reshape(-1)[perm], rtol=1e-12, atol=1e-14)
+    assert (grid["hit"] > 0.5).sum() > 10  # the scan hits things
+
+
 def test_lidar_occlusion_and_order():
     """Two Gaussians on one ray: the nearer one (o = 0.99) leaves T = 0.01;
     range = (0.99 D1 + 0.01 o2 D2) / (1 - T_final)."""
