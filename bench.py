@@ -763,8 +763,10 @@ def run_prune(a, rank, world, local_rank):
     scores = scene.contribution(poses[:ns], w.cams[:ns], stream=stream)
     torch.cuda.synchronize()
     score_s = time.perf_counter() - t0
-    p = gsbatch.prune_workload(w, scores.cpu().numpy(), keep_bg=0.3, keep_links=0.1)
-    pscene = gsbatch.scene_from_workload(p)
+    t0 = time.perf_counter()
+    pscene, _ = scene.prune(scores, keep_bg=0.3, keep_links=0.1)  # selection + new scene on the device
+    torch.cuda.synchronize()
+    prune_s = time.perf_counter() - t0
     rgb = torch.empty((E, H, W, 3), dtype=torch.float32, device=dev)
     depth = torch.empty((E, H, W), dtype=torch.float32, device=dev)
 
@@ -802,11 +804,12 @@ def run_prune(a, rank, world, local_rank):
                 "ms_per_step": pruned_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"c1 pruned by contribution over the cameras of {ns} envs: "
-                                       f"{p.background.n} of {w.background.n} background and {p.links.n} of "
+                                       f"{pscene.n_background} of {w.background.n} background and "
+                                       f"{pscene.stats()['n_gaussians'] - pscene.n_background} of "
                                        f"{w.links.n} link Gaussians kept"},
                 "unpruned": {"ms_per_step": full_ms, "env_frames_s": E / (full_ms / 1e3)},
                 "speedup": full_ms / pruned_ms, "error_vs_unpruned_fp64_oracle": errs,
-                "contribution_pass_s": score_s, "clocks": ck,
+                "contribution_pass_s": score_s, "prune_s": prune_s, "clocks": ck,
                 "gpu_launches": None, "e2e": None, "cpu_baseline": None}
         print(json.dumps(line), flush=True)
     pscene.close()

@@ -244,6 +244,28 @@ gs_status gs_render_rays(gs_scene s, int n_envs, const float* link_poses, const 
 gs_status gs_scene_contribution(gs_scene s, int n_envs, const float* link_poses, const gs_camera* cams,
                                 float* scores, void* cuda_stream);
 
+/* Pruning as a scene transform (the paper prunes Gaussians for speed and
+ * memory, Sec. III-C, keeping about 30 % of a static scene and up to 90 %
+ * fewer on dynamic objects; it does not give its criterion).  Ranks the
+ * Gaussians by score, descending (equal scores: lower index first), and
+ * creates a new scene (*out, destroyed by the caller) holding the top
+ * ceil(keep_bg n_bg) background Gaussians and the top ceil(keep_links n_l) of
+ * every link's cluster, kept in their original order: the new scene's
+ * background index and link offsets number the kept Gaussians in the caller's
+ * order, and they render exactly as in the source scene.  The source scene is
+ * unchanged.
+ *   scores     DEVICE float32 [background + link Gaussians], the caller's order
+ *              (for instance gs_scene_contribution's weights); no NaN
+ *   keep_bg, keep_links  fractions in [0, 1]
+ *   kept       HOST int64 [kept_cap] or NULL: receives, for every Gaussian of
+ *              the new scene (background, then link-major), its index in the source
+ * Selection and the new scene's attributes are computed on the device; the
+ * call synchronises it.  Errors: GS_ERR_INVALID (null handle or scores,
+ * fraction out of range, NaN score, kept_cap below the kept count),
+ * GS_ERR_OOM, GS_ERR_CUDA. */
+gs_status gs_scene_prune(gs_scene s, const float* scores, double keep_bg, double keep_links, gs_scene* out,
+                         int64_t* kept, int64_t kept_cap);
+
 /* One environment of an uneven batch (gs_render_batch_v, plans).  80 bytes. */
 typedef struct {
     gs_camera cam;        /* its own camera, width and height */

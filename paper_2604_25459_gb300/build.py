@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libgsbatch.so")
 SOURCES = ["gs_api.cu", "gs_tables.cu", "gs_project.cu", "gs_bin.cu", "gs_composite.cu", "gs_noalloc.cu", "gs_peak.cu", "gs_lidar.cu",
-           "gs_server.cu"]
+           "gs_server.cu", "gs_prune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

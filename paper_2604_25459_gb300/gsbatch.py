@@ -98,6 +98,8 @@ _SIGS = {
     "gs_scene_contribution": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 4),
     "gs_render_lidar": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 5),
     "gs_render_rays": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int] + [C.c_void_p] * 4),
+    "gs_scene_prune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_void_p), C.c_void_p,
+                                 C.c_int64]),
     "gs_render_batch_obs_host": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "gs_plan_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "gs_plan_launch": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
@@ -210,6 +212,38 @@ class Scene:
         self.n_background = int(v.n)
         self.n_links = 0
         self._alive = True
+
+    @classmethod
+    def _adopt(cls, handle, dtype: str, sh_degree: int, n_background: int, n_links: int) -> "Scene":
+        """Wrap a scene handle the library created (gs_scene_prune)."""
+        self = cls.__new__(cls)
+        self._h = handle
+        self.dtype = dtype
+        self.sh_degree = sh_degree
+        self.n_background = n_background
+        self.n_links = n_links
+        self._alive = True
+        return self
+
+    def prune(self, scores, keep_bg: float = 0.3, keep_links: float = 0.1):
+        """Pruning as a scene transform (gs_scene_prune, selection and the new
+        scene on the device): scores CUDA float32 [n Gaussians], the caller's
+        order.  Returns (the pruned Scene, kept int64 numpy: each kept
+        Gaussian's index in this scene, new order)."""
+        import torch
+
+        if not (torch.is_tensor(scores) and scores.is_cuda and scores.dtype == torch.float32):
+            scores = torch.as_tensor(np.ascontiguousarray(scores, dtype=np.float32)).cuda()
+        n = int(scores.numel())
+        kept = np.zeros(max(n, 1), np.int64)
+        h = C.c_void_p()
+        _check(lib().gs_scene_prune(self._h, _ptr(scores), float(keep_bg), float(keep_links), C.byref(h),
+                                    _ptr(kept), n))
+        sub = Scene._adopt(h, self.dtype, self.sh_degree, 0, self.n_links)
+        n_kept = sub.stats()["n_gaussians"]
+        kept = kept[:n_kept]
+        sub.n_background = int((kept < self.n_background).sum())
+        return sub, kept
 
     @staticmethod
     def _make_view(g, dtype, sh_degree, stored):
@@ -600,37 +634,31 @@ def measure_alu_peak(stream=None) -> dict:
     return {"fma_lane_ops_per_s": f.value, "ex2_lane_ops_per_s": e.value}
 
 
-def prune_workload(w, scores, keep_bg: float = 0.3, keep_links: float = 0.1):
-    """Scene transform: keep the highest-ranked Gaussians by contribution
-    score (``scores``: numpy [n_background + n_link_gaussians], global order),
-    the top ``keep_bg`` fraction of the background and the top ``keep_links``
-    fraction of every link's cluster; kept Gaussians stay in their original
-    order.  Returns a synth.Workload with the same poses and cameras."""
+def prune_workload(w, scores, keep_bg: float = 0.3, keep_links: float = 0.1, scene=None):
+    """The pruned workload of gs_scene_prune (the selection runs in the
+    library): the Gaussians it keeps from w, in their original order, with the
+    same poses and cameras.  scores: per Gaussian, the caller's order (numpy or
+    CUDA); scene: w's scene (built here when None).  Returns (workload, pruned
+    Scene); the caller closes the scene."""
     from . import synth
-    scores = np.asarray(scores, dtype=np.float64)
+
+    own = scene is None
+    if own:
+        scene = scene_from_workload(w)
+    sub, kept = scene.prune(scores, keep_bg, keep_links)
+    if own:
+        scene.close()
     nb = w.background.n
-
-    def top(s, frac):
-        k = int(np.ceil(frac * len(s)))
-        if k >= len(s):
-            return np.arange(len(s))
-        return np.sort(np.argpartition(-s, k - 1)[:k]) if k > 0 else np.zeros(0, np.int64)
-
-    bg_idx = top(scores[:nb], keep_bg)
-    offs = np.asarray(w.link_offsets, dtype=np.int64)
-    parts, new_offs = [], [0]
-    for l in range(len(offs) - 1):
-        a, b = int(offs[l]), int(offs[l + 1])
-        idx = a + top(scores[nb + a:nb + b], keep_links)
-        parts.append(idx)
-        new_offs.append(new_offs[-1] + len(idx))
-    link_idx = np.concatenate(parts) if parts else np.zeros(0, np.int64)
+    bg_idx, link_idx = kept[kept < nb], kept[kept >= nb] - nb
+    old = np.asarray(w.link_offsets, dtype=np.int64)
+    counts = [int(((link_idx >= old[l]) & (link_idx < old[l + 1])).sum()) for l in range(len(old) - 1)]
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
 
     def take(g, idx):
         return synth.Gaussians(g.mean[idx], g.quat[idx], g.log_scale[idx], g.opacity[idx], g.sh[idx])
 
-    return synth.Workload(w.name + "_pruned", take(w.background, bg_idx), np.asarray(new_offs, np.int64),
-                          take(w.links, link_idx), w.link_poses, w.cams)
+    return synth.Workload(w.name + "_pruned", take(w.background, bg_idx), offs, take(w.links, link_idx),
+                          w.link_poses, w.cams), sub
 
 
 def make_envs(cams: np.ndarray, link_ranges=None, pose_offsets=None) -> np.ndarray:
