@@ -289,8 +289,8 @@ gs_status gs_render_batch_v(gs_scene s, int n_envs, const gs_env* envs, const fl
 /* A plan is a fixed batch (environments, resolutions, link subsets) rendered
  * repeatedly with changing poses.  Its first launch runs eagerly: with
  * GS_PLAN_AUTOTUNE it times every tile shape (8x8, 16x8, 16x16, 32x8, 32x16) and
- * compositor claim size (1 or 4 tiles per atomic), on 16x16 tiles also the
- * compositor's quadrant form (lanes in groups of eight, each group walking
+ * compositor claim size (1 or 4 tiles per atomic), on 16x16 and 8x8 tiles also
+ * the compositor's quadrant form (lanes in groups of eight, each group walking
  * the splats of its own 4x4 pixel quadrant), and keeps the fastest (the
  * images do not depend on the choice); it sizes the intersection-key buffer at
  * 1.25x what that launch needed.  With GS_PLAN_GRAPH the whole render (all
@@ -313,7 +313,7 @@ typedef struct {
     int regrows;            /* capacity re-measurements after overflows */
     int64_t key_capacity;   /* intersection keys, all waves */
     int64_t scratch_bytes;  /* device scratch held by the plan */
-    int quad;               /* 1 if the compositor runs its quadrant form (16x16 tiles only) */
+    int quad;               /* 1 if the compositor runs its quadrant form (16x16 or 8x8 tiles) */
 } gs_plan_info;
 gs_status gs_plan_create(gs_scene s, int n_envs, const gs_env* envs, int flags, gs_plan* out);
 gs_status gs_plan_launch(gs_plan p, const float* link_poses, float* rgb, float* depth, float* alpha,

@@ -445,7 +445,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
                    unsigned long long* total_out, int quad) {
     const int We = wt.We;
     bool use_quad = false;
-    if (tw == 16 && th == 16 && !io.lidars && !io.score) {
+    if (((tw == 16 && th == 16) || (tw == 8 && th == 8)) && !io.lidars && !io.score) {
         if (quad < 0) {
             long long most = 0;
             for (int e = 0; e < We; ++e)
@@ -1425,7 +1425,7 @@ gs_status gs_plan_launch(gs_plan p, const float* link_poses, float* rgb, float* 
             for (auto& sh : shapes)
                 for (int ch : {1, 4}) {
                     cands.push_back({sh[0], sh[1], ch, 0});
-                    if (sh[0] == 16 && sh[1] == 16) cands.push_back({16, 16, ch, 1});
+                    if (sh[0] == sh[1]) cands.push_back({sh[0], sh[1], ch, 1});  // quadrant form: 16x16, 8x8
                 }
         } else {
             cands.push_back({p->tile_w, p->tile_h, 1, 0});

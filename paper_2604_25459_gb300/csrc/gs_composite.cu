@@ -452,7 +452,11 @@ __device__ __forceinline__ bool reaches_rect(const float4& A, const float4& B, f
 // once; large ones reach all four and the extra votes only cost (measured on
 // the 2048-env room workload: 64x64 -21 %, 128x128 -15 %, 320x240 -3 %,
 // 640x480 +1.4 % compositing time).  Every pixel still composites the same
-// splats in the same order, so the images are identical either way.
+// splats in the same order, so the images are identical either way.  Every
+// bucket is long at those resolutions, so the quadrant form also fills each
+// window of a partitioned bucket up to the cap and keeps several keys in
+// flight per thread in the partition passes (64x64 and 128x128 -6 to -7 %;
+// neither paid at 640x480).
 template <int TW, int TH, bool SC = false, int MODE = 0, bool QUAD = false>
 __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 256 ? 8 : 12))) k_composite(CompParams P) {
     constexpr int NT = TW * TH / 2;
@@ -878,11 +882,12 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
     auto key_range = [&](const unsigned long long* L, uint32_t len, unsigned long long& mn,
                          unsigned long long& mx) {
         unsigned long long a = ~0ull, b = 0;
-        for (uint32_t i = tid; i < len; i += NT) {
-            const unsigned long long k = L[i];
+        auto take = [&](uint32_t, unsigned long long k) {
             a = k < a ? k : a;
             b = k > b ? k : b;
-        }
+        };
+        if constexpr (QUAD) for_keys<NT, 4>(L, len, take);  // long buckets are the rule there
+        else for (uint32_t i = tid; i < len; i += NT) take(i, L[i]);
         for (int d = 16; d > 0; d >>= 1) {
             const unsigned long long oa = __shfl_xor_sync(0xffffffffu, a, d);
             const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, d);
@@ -1068,15 +1073,29 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
             const int shift = (span >> 11) ? 53 - __clzll((long long)span) : 0;  // span >> shift < kBins
             for (int i = tid; i < kBins; i += NT) bins[i] = 0;
             __syncthreads();
-            for (uint32_t i = tid; i < n; i += NT) {
-                const unsigned long long k = Lk[i];
+            auto count_key = [&](uint32_t, unsigned long long k) {
                 if (k >= klo && k < kh) atomicAdd(&bins[(uint32_t)((k - klo) >> shift)], 1u);
-            }
+            };
+            if constexpr (QUAD) for_keys<NT, 4>(Lk, n, count_key);
+            else for (uint32_t i = tid; i < n; i += NT) count_key(i, Lk[i]);
             __syncthreads();
             constexpr int PER = kBins / NT;
-            uint32_t loc = 0;
+            uint32_t loc = 0, big = 0;
 #pragma unroll 4
-            for (int j = 0; j < PER; ++j) loc += bins[tid * PER + j];
+            for (int j = 0; j < PER; ++j) {
+                const uint32_t c = bins[tid * PER + j];
+                loc += c;
+                if constexpr (QUAD) big = c > big ? c : big;
+            }
+            // window stride: a window holds the bins that start in one stride of
+            // keys, so it is at most stride + the largest bin; the quadrant form
+            // (low resolutions: every bucket long) fills windows up to the cap
+            uint32_t stride = HALF;
+            if constexpr (QUAD) {
+                uint32_t none = 0;
+                block_minmax_u32<NT>(none, big, red);
+                if (big <= (uint32_t)HALF) stride = (uint32_t)CAP - big;
+            }
             uint32_t run = block_excl_scan_u32<NT>(loc, red);
 #pragma unroll 4
             for (int j = 0; j < PER; ++j) {
@@ -1085,14 +1104,14 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                 run += c;
             }
             __syncthreads();
-            // window v: the bins that start in [v HALF, (v+1) HALF)
-            nw = (int)((m + HALF - 1) / HALF);
+            // window v: the bins that start in [v stride, (v+1) stride)
+            nw = (int)((m + stride - 1) / stride);
             for (int v = tid; v <= nw; v += NT) {
                 uint32_t x = m;
                 if (v == 0) {
                     x = 0;
                 } else if (v < nw) {
-                    const uint32_t target = (uint32_t)v * HALF;
+                    const uint32_t target = (uint32_t)v * stride;
                     int lo = 0, hi = kBins;  // first bin whose start >= target
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
@@ -1103,13 +1122,14 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                 s_ws[v] = x;
             }
             __syncthreads();
-            for (uint32_t i = tid; i < n; i += NT) {
-                const unsigned long long k = Lk[i];
+            auto place = [&](uint32_t, unsigned long long k) {
                 if (k >= klo && k < kh) {
                     const uint32_t pos = atomicAdd(&bins[(uint32_t)((k - klo) >> shift)], 1u);
                     spill[pos] = k;
                 }
-            }
+            };
+            if constexpr (QUAD) for_keys<NT, 4>(Lk, n, place);
+            else for (uint32_t i = tid; i < n; i += NT) place(i, Lk[i]);
             __syncthreads();
             w = 0;
             processed += m;
@@ -1254,9 +1274,13 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
         if (P.tile_w != 16 || P.tile_h != 16) return cudaErrorInvalidValue;
         return launch_tiles<16, 16, true>(P, st, ctas);
     }
-    if (P.quad && P.tile_w == 16 && P.tile_h == 16) {  // quadrant lists (16x16 camera tiles)
+    if (P.quad && P.tile_w == 16 && P.tile_h == 16) {  // quadrant lists (16x16 and 8x8 camera tiles)
         if (P.neval) return launch_tiles<16, 16, false, 2, true>(P, st, ctas);
         return launch_tiles<16, 16, false, 0, true>(P, st, ctas);
+    }
+    if (P.quad && P.tile_w == 8 && P.tile_h == 8) {
+        if (P.neval) return launch_tiles<8, 8, false, 2, true>(P, st, ctas);
+        return launch_tiles<8, 8, false, 0, true>(P, st, ctas);
     }
     if (P.neval) {  // counting pass
         if (P.tile_w == 16 && P.tile_h == 16) return launch_tiles<16, 16, false, 2>(P, st, ctas);
@@ -1277,6 +1301,13 @@ cudaError_t composite_max_ctas(int tile_w, int tile_h, int* ctas) {
         int a = 0, b = 0;
         cudaError_t e = resident_ctas<16, 16>(&a);
         if (e == cudaSuccess) e = resident_ctas<16, 16, false, 0, true>(&b);
+        *ctas = a > b ? a : b;
+        return e;
+    }
+    if (tile_w == 8 && tile_h == 8) {
+        int a = 0, b = 0;
+        cudaError_t e = resident_ctas<8, 8>(&a);
+        if (e == cudaSuccess) e = resident_ctas<8, 8, false, 0, true>(&b);
         *ctas = a > b ? a : b;
         return e;
     }

@@ -169,8 +169,8 @@ gs_status upload_tables(gs_scene s, const std::vector<EnvSpec>& specs, int e0, i
 // Launches one wave on st: link table, projection, binning, compositing.
 // cap == 0: eager (reads the intersection totals back, grows the key buffer);
 // cap > 0: planned (no host sync; keys beyond cap dropped and flagged).
-// quad: the compositor's quadrant form on 16x16 camera tiles: 1 on, 0 off,
-// -1 when no image of the wave exceeds kQuadMaxPixels.
+// quad: the compositor's quadrant form on 16x16 or 8x8 camera tiles: 1 on,
+// 0 off, -1 when no image of the wave exceeds kQuadMaxPixels.
 gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& io, int tw, int th, int chunk,
                    unsigned long long cap, cudaStream_t st, bool timers, int64_t* launches,
                    unsigned long long* total_out, int quad = -1);

@@ -168,7 +168,7 @@ struct CompParams {
     unsigned long long* dbg_sorted;  // nullable: receives the full depth-ordered lists
     unsigned long long* neval;       // nullable: composited (pixel, Gaussian) pair counter
     int tile_w, tile_h;
-    int quad;       // 16x16 camera tiles: per-quadrant splat lists (k_composite's QUAD form)
+    int quad;       // 16x16 or 8x8 camera tiles: per-quadrant splat lists (k_composite's QUAD form)
     float* rgb;     // images at envs[e].pix_base (x3 for rgb); unused when rgb8 is set
     float* depth;   // unused when depth16 is set
     float* alpha;   // nullable
@@ -241,7 +241,7 @@ constexpr int kWordsPerBlock = 256;  // binning block: 8 warps x 32 visibility w
 constexpr int kCompCap = 768;
 constexpr int kBins = 2048;         // key ranges of the long-bucket partition
 constexpr int kSpillMax = 32768;    // keys per CTA in the spill region, at most
-// Plain renders use the compositor's quadrant form (QUAD) on 16x16 tiles when
+// Plain renders use the compositor's quadrant form (QUAD) on 16x16 or 8x8 tiles when
 // no image of the wave has more pixels than this (measured crossover on the
 // room workload: faster at 320x240 and below, slower at 640x480).
 constexpr int kQuadMaxPixels = 320 * 240;

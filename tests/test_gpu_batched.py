@@ -125,10 +125,10 @@ def test_plan_autotune_graph_replay_and_regrow():
             assert torch.equal(a, b), f"step {step}"
     info = plan.info()
     print("plan", info)
-    # 5 tile shapes x 2 claim sizes, plus the quadrant form on 16x16 tiles
-    assert info["graph"] == 1 and info["tuned_candidates"] == 12
+    # 5 tile shapes x 2 claim sizes, plus the quadrant form on 16x16 and 8x8 tiles
+    assert info["graph"] == 1 and info["tuned_candidates"] == 14
     assert (info["tile_w"], info["tile_h"]) in ((16, 16), (32, 8), (16, 8), (8, 8), (32, 16))
-    assert info["quad"] in (0, 1) and (info["quad"] == 0 or (info["tile_w"], info["tile_h"]) == (16, 16))
+    assert info["quad"] in (0, 1) and (info["quad"] == 0 or info["tile_w"] == info["tile_h"])
     # objects pulled up to the cameras need far more keys than planned: the
     # replay drops keys and says so, the next launch regrows and is exact again
     p3 = w.link_poses.copy()
