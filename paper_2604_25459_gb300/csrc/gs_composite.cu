@@ -629,19 +629,32 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         wx1 = __reduce_max_sync(0xffffffffu, max(in0 ? cx0 : -big, in1 ? cx1 : -big));
         wy1 = __reduce_max_sync(0xffffffffu, max(in0 ? cy0 : -big, in1 ? cy1 : -big));
     }
-    // LiDAR: alpha and t* of a staged Gaussian (b, o | g0 | g1 | g2) on ray d
-    auto ray_eval = [&](const float4& A, const float4& B, const float4& C, const float4& D, const float3& d,
-                        float& al, float& ts) {
-        const float u0 = B.x * d.x + B.y * d.y + B.z * d.z;
-        const float u1 = C.x * d.x + C.y * d.y + C.z * d.z;
-        const float u2 = D.x * d.x + D.y * d.y + D.z * d.z;
-        const float aa = u0 * u0 + u1 * u1 + u2 * u2;
-        const float ab = u0 * A.x + u1 * A.y + u2 * A.z;
-        const float c0 = u1 * A.z - u2 * A.y, c1 = u2 * A.x - u0 * A.z, c2 = u0 * A.y - u1 * A.x;
-        const float inv = 1.0f / aa;
-        const float q = (c0 * c0 + c1 * c1 + c2 * c2) * inv;
-        ts = ab * inv;
-        al = ts > near_range ? fminf(0.99f, A.w * ex2_approx(-0.72134752044448170f * q)) : 0.0f;
+    // LiDAR: alpha and t* of a staged Gaussian (b, o | g0 | g1 | g2) on each
+    // of the lane's two rays d: u = G d, q = |u x b|^2 / |u|^2, t* = u.b / |u|^2,
+    // with paired FP32 instructions (the reciprocal of |u|^2 by the fast
+    // division, ~2 ulp, far inside the scan's tolerance).
+    auto ray_eval2 = [&](const float4& A, const float4& B, const float4& C, const float4& D, float2& al,
+                         float2& ts) {
+        const float2 dx = make_float2(dir0.x, dir1.x), dy = make_float2(dir0.y, dir1.y),
+                     dz = make_float2(dir0.z, dir1.z);
+        auto dot = [&](const float4& G) {
+            return __ffma2_rn(make_float2(G.z, G.z), dz,
+                              __ffma2_rn(make_float2(G.y, G.y), dy, __fmul2_rn(make_float2(G.x, G.x), dx)));
+        };
+        const float2 u0 = dot(B), u1 = dot(C), u2 = dot(D);
+        const float2 aa = __ffma2_rn(u2, u2, __ffma2_rn(u1, u1, __fmul2_rn(u0, u0)));
+        const float2 ab = __ffma2_rn(u2, make_float2(A.z, A.z),
+                                     __ffma2_rn(u1, make_float2(A.y, A.y), __fmul2_rn(u0, make_float2(A.x, A.x))));
+        const float2 c0 = __ffma2_rn(u1, make_float2(A.z, A.z), __fmul2_rn(u2, make_float2(-A.y, -A.y)));
+        const float2 c1 = __ffma2_rn(u2, make_float2(A.x, A.x), __fmul2_rn(u0, make_float2(-A.z, -A.z)));
+        const float2 c2 = __ffma2_rn(u0, make_float2(A.y, A.y), __fmul2_rn(u1, make_float2(-A.x, -A.x)));
+        const float2 cc = __ffma2_rn(c2, c2, __ffma2_rn(c1, c1, __fmul2_rn(c0, c0)));
+        const float2 inv = make_float2(__fdividef(1.0f, aa.x), __fdividef(1.0f, aa.y));
+        const float2 q = __fmul2_rn(cc, inv);
+        ts = __fmul2_rn(ab, inv);
+        const float k = -0.72134752044448170f;  // -log2(e) / 2
+        al.x = ts.x > near_range ? fminf(0.99f, A.w * ex2_approx(k * q.x)) : 0.0f;
+        al.y = ts.y > near_range ? fminf(0.99f, A.w * ex2_approx(k * q.y)) : 0.0f;
     };
     bool done0 = !in0, done1 = !in1;
     // the lane's two pixels: .x = (px, py0), .y = (px, py1)
@@ -814,11 +827,11 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         if (LID && (h10 || h11 || h20 || h21)) {
                             const float4 A1 = sA[j1], B1 = sB[j1], C1 = sC[j1], D1 = sD[LID ? j1 : 0];
                             const float4 A2 = sA[j2], B2 = sB[j2], C2 = sC[j2], D2 = sD[LID ? j2 : 0];
-                            float a10, a11, a20, a21, t10, t11, t20, t21;
-                            ray_eval(A1, B1, C1, D1, dir0, a10, t10);
-                            ray_eval(A1, B1, C1, D1, dir1, a11, t11);
-                            ray_eval(A2, B2, C2, D2, dir0, a20, t20);
-                            ray_eval(A2, B2, C2, D2, dir1, a21, t21);
+                            float2 al1, ts1, al2, ts2;
+                            ray_eval2(A1, B1, C1, D1, al1, ts1);
+                            ray_eval2(A2, B2, C2, D2, al2, ts2);
+                            const float a10 = al1.x, a11 = al1.y, a20 = al2.x, a21 = al2.y;
+                            const float t10 = ts1.x, t11 = ts1.y, t20 = ts2.x, t21 = ts2.y;
                             const float4 none = make_float4(0.f, 0.f, 0.f, 0.f);
                             if (h10 && a10 >= (1.0f / 255.0f)) {
                                 if constexpr (CNT) ++ncomp;
