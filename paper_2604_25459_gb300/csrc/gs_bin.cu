@@ -13,12 +13,15 @@
 
 namespace gsb {
 
-__device__ __forceinline__ void tile_span(uint32_t rx, uint32_t ry, int tw, int th, int& tx0, int& tx1, int& ty0,
+// Tile widths and heights are powers of two (8, 16 or 32; the API rejects
+// other shapes), and box coordinates are non-negative, so the tile of a pixel
+// coordinate is a shift of it: sx = log2(tile width), sy = log2(tile height).
+__device__ __forceinline__ void tile_span(uint32_t rx, uint32_t ry, int sx, int sy, int& tx0, int& tx1, int& ty0,
                                           int& ty1) {
-    tx0 = (int)(rx & 0xffffu) / tw;
-    tx1 = (int)(rx >> 16) / tw;
-    ty0 = (int)(ry & 0xffffu) / th;
-    ty1 = (int)(ry >> 16) / th;
+    tx0 = (int)((rx & 0xffffu) >> sx);
+    tx1 = (int)((rx >> 16) >> sx);
+    ty0 = (int)((ry & 0xffffu) >> sy);
+    ty1 = (int)((ry >> 16) >> sy);
 }
 
 // Visit the visible Gaussians of mask words [w0, w1) of one env.  Each warp
@@ -58,10 +61,11 @@ __device__ __forceinline__ void block_histogram(const BinParams& P, const EnvInf
                                                 uint16_t* wbuf, uint32_t* hist) {
     const uint32_t* mask = P.mask + E.mask_base;
     const uint4* r3 = P.r3 + E.rec_base;
+    const int sx = __ffs(P.tile_w) - 1, sy = __ffs(P.tile_h) - 1;
     for_each_visible(mask, w0, w1, wbuf, [&](int64_t j) {
         const uint4 q = r3[j];
         int tx0, tx1, ty0, ty1;
-        tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
+        tile_span(q.x, q.y, sx, sy, tx0, tx1, ty0, ty1);
         // one flat loop over the span (lanes with spans of different shapes
         // then diverge only by their tile counts)
         const int n = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
@@ -222,6 +226,7 @@ __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
     __syncthreads();
     const uint32_t* mask = P.mask + E.mask_base;
     const uint4* r3 = P.r3 + E.rec_base;
+    const int sx = __ffs(P.tile_w) - 1, sy = __ffs(P.tile_h) - 1;
     bool dropped = false;
     for_each_visible(mask, w0, w1, wbuf, [&](int64_t j) {
         const uint4 q = r3[j];
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
                            : ((P.bg_index && j < (int64_t)P.n_bg) ? (uint32_t)__ldg(P.bg_index + j) : (uint32_t)j);
         const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)i;
         int tx0, tx1, ty0, ty1;
-        tile_span(q.x, q.y, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1);
+        tile_span(q.x, q.y, sx, sy, tx0, tx1, ty0, ty1);
         const int n = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
         int tx = tx0, t = ty0 * E.ntx + tx0;
         for (int i = 0; i < n; ++i) {
@@ -251,7 +256,14 @@ __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
 
 cudaError_t launch_scatter(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st) {
     if (n_envs == 0 || max_words == 0) return cudaSuccess;
-    const size_t smem = (size_t)max_T * 8;
+    size_t smem = (size_t)max_T * 8;
+    // Large images (at least half a 640x480 frame per env): at most 4 CTAs per
+    // SM, by padding the shared memory (29 KB dynamic + 16 KB static + the
+    // per-CTA reserve: 5 no longer fit).  Measured on the 2048-env room
+    // workload at 640x480: 6 CTAs/SM (what 40 registers allow) 20.7 ms, 5: 19.9,
+    // 4: 18.7, 3: 18.6 ms per step; at 320x240 and 128x128 six are fastest
+    // (6.8 vs 8.0 ms and 5.1 vs 6.2 ms with 4).
+    if ((long long)max_T * P.tile_w * P.tile_h >= 640ll * 480 / 2 && smem < (size_t)29 * 1024) smem = 29 * 1024;
     cudaError_t e = opt_in_smem((const void*)k_scatter, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((max_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);

@@ -191,10 +191,12 @@ __device__ unsigned long long* bin_sort(const unsigned long long* keys, unsigned
         tmp[pos] = k;
     }
     __syncthreads();
-    // range b is now [c32[b-1], c32[b]) (c32 holds each range's end)
+    // range b is now [c32[b-1], c32[b]) (c32 holds each range's end); the
+    // ranges are interleaved over the threads, so a cluster of crowded
+    // neighbouring ranges (a window's depths bunch up) spreads over many
+    // threads instead of the few that hold them in the blocked layout
 #pragma unroll 1
-    for (int j = 0; j < PER; ++j) {
-        const int b = tid * PER + j;
+    for (int b = tid; b < kSortBins; b += NT) {
         const int e = (int)c32[b];
         const int a = b ? (int)c32[b - 1] : 0;
         for (int x = a + 1; x < e; ++x) {
