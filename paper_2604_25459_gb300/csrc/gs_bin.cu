@@ -24,46 +24,51 @@ __device__ __forceinline__ void tile_span(uint32_t rx, uint32_t ry, int sx, int 
     ty1 = (int)((ry >> 16) >> sy);
 }
 
-// Visit the visible Gaussians of mask words [w0, w1) of one env.  Each warp
-// takes 32 words at a time, expands their set bits into a dense list in its
-// slice of shared memory (1024 entries) and its lanes walk that list, so
-// sparse visibility (most of the background is off-screen in any one view)
-// does not leave lanes idle.
-template <typename F>
-__device__ __forceinline__ void for_each_visible(const uint32_t* mask, int64_t w0, int64_t w1, uint16_t* wbuf, F&& f) {
+// The visible record slots of mask words [w0, w1) of one env, one word per
+// thread (w1 - w0 <= blockDim.x), listed block-wide in slot order in lst (at
+// most 32 (w1 - w0) entries, slots relative to 32 w0); returns their number.
+// One list per block spreads the visible records evenly over its warps,
+// however unevenly visibility clusters in the storage order, and the scatter
+// walks the same list in both of its passes.  wtot: one u32 per warp.
+__device__ __forceinline__ int block_visible(const uint32_t* mask, int64_t w0, int64_t w1, uint16_t* lst,
+                                             uint32_t* wtot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint16_t* buf = wbuf + warp * 1024;
-    for (int64_t base = w0 + (int64_t)warp * 32; base < w1; base += (int64_t)nw * 32) {
-        const int64_t w = base + lane;
-        uint32_t m = w < w1 ? __ldg(mask + w) : 0u;
-        const uint32_t c = __popc(m);
-        uint32_t incl = c;
+    const int64_t w = w0 + threadIdx.x;
+    uint32_t m = w < w1 ? __ldg(mask + w) : 0u;
+    const uint32_t c = __popc(m);
+    uint32_t incl = c;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        uint32_t pos = incl - c;
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1u;
-            buf[pos++] = (uint16_t)(lane * 32 + b);
-        }
-        __syncwarp();
-        for (uint32_t j = lane; j < total; j += 32) f(base * 32 + buf[j]);
-        __syncwarp();
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
     }
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int i = 0; i < nw; ++i) {
+        const uint32_t t = wtot[i];
+        if (i < warp) before += t;
+        total += t;
+    }
+    uint32_t pos = before + incl - c;
+    while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1u;
+        lst[pos++] = (uint16_t)(threadIdx.x * 32 + bit);
+    }
+    __syncthreads();
+    return (int)total;
 }
 
-// Rebuilds a block's tile histogram of env el's visible records in hist[0, T).
-__device__ __forceinline__ void block_histogram(const BinParams& P, const EnvInfo& E, int64_t w0, int64_t w1,
-                                                uint16_t* wbuf, uint32_t* hist) {
-    const uint32_t* mask = P.mask + E.mask_base;
+// Rebuilds a block's tile histogram of env el's visible records (the block's
+// list from block_visible, records 32 w0 + lst[i]) in hist[0, T).  Neighbouring
+// threads take neighbouring records of the list.
+__device__ __forceinline__ void block_histogram(const BinParams& P, const EnvInfo& E, int64_t w0, const uint16_t* lst,
+                                                int nvis, uint32_t* hist) {
     const uint4* r3 = P.r3 + E.rec_base;
     const int sx = __ffs(P.tile_w) - 1, sy = __ffs(P.tile_h) - 1;
-    for_each_visible(mask, w0, w1, wbuf, [&](int64_t j) {
-        const uint4 q = r3[j];
+    for (int i = threadIdx.x; i < nvis; i += blockDim.x) {
+        const uint4 q = r3[w0 * 32 + lst[i]];
         int tx0, tx1, ty0, ty1;
         tile_span(q.x, q.y, sx, sy, tx0, tx1, ty0, ty1);
         // one flat loop over the span (lanes with spans of different shapes
@@ -80,14 +85,15 @@ __device__ __forceinline__ void block_histogram(const BinParams& P, const EnvInf
                 ++t;
             }
         }
-    });
+    }
 }
 
 // grid: (blocks over the largest env's visibility words, envs); block 256;
 // dynamic smem: max T u32.  Blocks past their env's words exit at once.
 __global__ void __launch_bounds__(256) k_count(BinParams P) {
     extern __shared__ uint32_t hist[];
-    __shared__ uint16_t wbuf[8 * 1024];
+    __shared__ uint16_t wbuf[32 * kWordsPerBlock];
+    __shared__ uint32_t wtot[32];
     const int el = P.e_begin + blockIdx.y;
     const EnvInfo E = P.envs[el];
     const int64_t words = (E.n_local + 31) / 32;
@@ -95,8 +101,8 @@ __global__ void __launch_bounds__(256) k_count(BinParams P) {
     if (w0 >= words) return;
     const int64_t w1 = min(w0 + (int64_t)P.words_per_block, words);
     for (int t = threadIdx.x; t < E.T; t += blockDim.x) hist[t] = 0;
-    __syncthreads();
-    block_histogram(P, E, w0, w1, wbuf, hist);
+    const int nvis = block_visible(P.mask + E.mask_base, w0, w1, wbuf, wtot);
+    block_histogram(P, E, w0, wbuf, nvis, hist);
     __syncthreads();
     uint32_t* cnt = P.counts + E.tile_base;
     for (int t = threadIdx.x; t < E.T; t += blockDim.x) {
@@ -109,6 +115,8 @@ static cudaError_t opt_in_smem(const void* fn, size_t smem) {
     if (smem <= 16 * 1024) return cudaSuccess;  // plus 16 KB of static shared memory
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
+
+static_assert(kWordsPerBlock <= 256, "binning blocks: one visibility word per thread of 256");
 
 cudaError_t launch_count(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st) {
     if (n_envs == 0 || max_words == 0) return cudaSuccess;
@@ -200,9 +208,10 @@ cudaError_t launch_scan(const EnvInfo* envs, const uint32_t* counts, uint32_t* o
 // shared cursor).  A key past the pair buffer's capacity (possible only for a
 // launch planned with a fixed capacity) is dropped and flagged.
 
-__global__ void __launch_bounds__(256) k_scatter(BinParams P) {
+__global__ void __launch_bounds__(256, 6) k_scatter(BinParams P) {  // <= 42 registers: 6 CTAs/SM
     extern __shared__ uint32_t sm[];
-    __shared__ uint16_t wbuf[8 * 1024];
+    __shared__ uint16_t wbuf[32 * kWordsPerBlock];
+    __shared__ uint32_t wtot[32];
     const int el = P.e_begin + blockIdx.y;
     const EnvInfo E = P.envs[el];
     const int64_t words = (E.n_local + 31) / 32;
@@ -212,8 +221,8 @@ __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
     uint32_t* hist = sm;
     uint32_t* base = sm + E.T;
     for (int t = threadIdx.x; t < E.T; t += blockDim.x) hist[t] = 0;
-    __syncthreads();
-    block_histogram(P, E, w0, w1, wbuf, hist);
+    const int nvis = block_visible(P.mask + E.mask_base, w0, w1, wbuf, wtot);
+    block_histogram(P, E, w0, wbuf, nvis, hist);
     __syncthreads();
     uint32_t* cur = P.cursor + E.tile_base;
     const uint32_t* off = P.off_local + E.tile_base;
@@ -224,11 +233,11 @@ __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
         hist[t] = 0;
     }
     __syncthreads();
-    const uint32_t* mask = P.mask + E.mask_base;
     const uint4* r3 = P.r3 + E.rec_base;
     const int sx = __ffs(P.tile_w) - 1, sy = __ffs(P.tile_h) - 1;
     bool dropped = false;
-    for_each_visible(mask, w0, w1, wbuf, [&](int64_t j) {
+    for (int iv = threadIdx.x; iv < nvis; iv += blockDim.x) {
+        const int64_t j = w0 * 32 + wbuf[iv];
         const uint4 q = r3[j];
         const uint32_t i = P.index_in_r3 ? q.w
                            : ((P.bg_index && j < (int64_t)P.n_bg) ? (uint32_t)__ldg(P.bg_index + j) : (uint32_t)j);
@@ -250,7 +259,7 @@ __global__ void __launch_bounds__(256) k_scatter(BinParams P) {
                 ++t;
             }
         }
-    });
+    }
     if (__syncthreads_or(dropped) && threadIdx.x == 0) atomicOr(P.status, kStOverflow);
 }
 
