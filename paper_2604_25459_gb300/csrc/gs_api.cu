@@ -524,6 +524,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     B.cursor = sc.cursor.as<uint32_t>();
     B.status = status;
     B.index_in_r3 = io.lidars ? 0 : 1;  // LiDAR records keep |g2| in r3.w
+    B.wrap = io.lidars ? 1 : 0;         // LiDAR boxes may wrap across azimuth 0
     B.bg_index = s->bg_order.empty() ? nullptr : s->bg_index.as<int>();
     B.n_bg = (unsigned)s->D.n_bg;
     PhaseTimer t3(s, st, GS_PHASE_COUNT, timers);

@@ -24,6 +24,45 @@ __device__ __forceinline__ void tile_span(uint32_t rx, uint32_t ry, int sx, int 
     ty1 = (int)((ry >> 16) >> sy);
 }
 
+// f(t) for every tile t of a record's span: rows ty0..ty1 of the columns
+// tx0..tx1 in one flat loop (lanes with spans of different shapes then diverge
+// only by their tile counts).  WRAP (LiDAR waves): a box with x0 > x1 covers
+// the columns [x0, cols) and [0, x1] (a cone across azimuth 0), so its tile
+// columns run tx0..ntx-1 and then 0..tx1.
+template <bool WRAP, typename F>
+__device__ __forceinline__ void for_span(uint32_t rx, uint32_t ry, int sx, int sy, int ntx, F&& f) {
+    int tx0, tx1, ty0, ty1;
+    tile_span(rx, ry, sx, sy, tx0, tx1, ty0, ty1);
+    if (WRAP && (rx & 0xffffu) > (rx >> 16)) {
+        const int nx = min(ntx, ntx - tx0 + tx1 + 1);
+        const int n = nx * (ty1 - ty0 + 1);
+        int tx = tx0, row = ty0 * ntx, c = 0;
+        for (int k = 0; k < n; ++k) {
+            f(row + tx);
+            if (++c == nx) {
+                c = 0;
+                tx = tx0;
+                row += ntx;
+            } else if (++tx == ntx) {
+                tx = 0;
+            }
+        }
+        return;
+    }
+    const int n = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+    int tx = tx0, t = ty0 * ntx + tx0;
+    for (int k = 0; k < n; ++k) {
+        f(t);
+        if (tx == tx1) {
+            tx = tx0;
+            t += ntx - (tx1 - tx0);
+        } else {
+            ++tx;
+            ++t;
+        }
+    }
+}
+
 // The visible record slots of mask words [w0, w1) of one env, one word per
 // thread (w1 - w0 <= blockDim.x), listed block-wide in slot order in lst (at
 // most 32 (w1 - w0) entries, slots relative to 32 w0); returns their number.
@@ -63,33 +102,20 @@ __device__ __forceinline__ int block_visible(const uint32_t* mask, int64_t w0, i
 // Rebuilds a block's tile histogram of env el's visible records (the block's
 // list from block_visible, records 32 w0 + lst[i]) in hist[0, T).  Neighbouring
 // threads take neighbouring records of the list.
+template <bool WRAP>
 __device__ __forceinline__ void block_histogram(const BinParams& P, const EnvInfo& E, int64_t w0, const uint16_t* lst,
                                                 int nvis, uint32_t* hist) {
     const uint4* r3 = P.r3 + E.rec_base;
     const int sx = __ffs(P.tile_w) - 1, sy = __ffs(P.tile_h) - 1;
     for (int i = threadIdx.x; i < nvis; i += blockDim.x) {
         const uint4 q = r3[w0 * 32 + lst[i]];
-        int tx0, tx1, ty0, ty1;
-        tile_span(q.x, q.y, sx, sy, tx0, tx1, ty0, ty1);
-        // one flat loop over the span (lanes with spans of different shapes
-        // then diverge only by their tile counts)
-        const int n = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-        int tx = tx0, t = ty0 * E.ntx + tx0;
-        for (int k = 0; k < n; ++k) {
-            atomicAdd(&hist[t], 1u);
-            if (tx == tx1) {
-                tx = tx0;
-                t += E.ntx - (tx1 - tx0);
-            } else {
-                ++tx;
-                ++t;
-            }
-        }
+        for_span<WRAP>(q.x, q.y, sx, sy, E.ntx, [&](int t) { atomicAdd(&hist[t], 1u); });
     }
 }
 
 // grid: (blocks over the largest env's visibility words, envs); block 256;
 // dynamic smem: max T u32.  Blocks past their env's words exit at once.
+template <bool WRAP>
 __global__ void __launch_bounds__(256) k_count(BinParams P) {
     extern __shared__ uint32_t hist[];
     __shared__ uint16_t wbuf[32 * kWordsPerBlock];
@@ -102,7 +128,7 @@ __global__ void __launch_bounds__(256) k_count(BinParams P) {
     const int64_t w1 = min(w0 + (int64_t)P.words_per_block, words);
     for (int t = threadIdx.x; t < E.T; t += blockDim.x) hist[t] = 0;
     const int nvis = block_visible(P.mask + E.mask_base, w0, w1, wbuf, wtot);
-    block_histogram(P, E, w0, wbuf, nvis, hist);
+    block_histogram<WRAP>(P, E, w0, wbuf, nvis, hist);
     __syncthreads();
     uint32_t* cnt = P.counts + E.tile_base;
     for (int t = threadIdx.x; t < E.T; t += blockDim.x) {
@@ -121,10 +147,12 @@ static_assert(kWordsPerBlock <= 256, "binning blocks: one visibility word per th
 cudaError_t launch_count(const BinParams& P, int n_envs, int max_words, int max_T, cudaStream_t st) {
     if (n_envs == 0 || max_words == 0) return cudaSuccess;
     const size_t smem = (size_t)max_T * 4;
-    cudaError_t e = opt_in_smem((const void*)k_count, smem);
+    const void* fn = P.wrap ? (const void*)k_count<true> : (const void*)k_count<false>;
+    cudaError_t e = opt_in_smem(fn, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((max_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
-    k_count<<<grid, 256, smem, st>>>(P);
+    if (P.wrap) k_count<true><<<grid, 256, smem, st>>>(P);
+    else k_count<false><<<grid, 256, smem, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -208,6 +236,7 @@ cudaError_t launch_scan(const EnvInfo* envs, const uint32_t* counts, uint32_t* o
 // shared cursor).  A key past the pair buffer's capacity (possible only for a
 // launch planned with a fixed capacity) is dropped and flagged.
 
+template <bool WRAP>
 __global__ void __launch_bounds__(256, 6) k_scatter(BinParams P) {  // <= 42 registers: 6 CTAs/SM
     extern __shared__ uint32_t sm[];
     __shared__ uint16_t wbuf[32 * kWordsPerBlock];
@@ -222,7 +251,7 @@ __global__ void __launch_bounds__(256, 6) k_scatter(BinParams P) {  // <= 42 reg
     uint32_t* base = sm + E.T;
     for (int t = threadIdx.x; t < E.T; t += blockDim.x) hist[t] = 0;
     const int nvis = block_visible(P.mask + E.mask_base, w0, w1, wbuf, wtot);
-    block_histogram(P, E, w0, wbuf, nvis, hist);
+    block_histogram<WRAP>(P, E, w0, wbuf, nvis, hist);
     __syncthreads();
     uint32_t* cur = P.cursor + E.tile_base;
     const uint32_t* off = P.off_local + E.tile_base;
@@ -242,23 +271,12 @@ __global__ void __launch_bounds__(256, 6) k_scatter(BinParams P) {  // <= 42 reg
         const uint32_t i = P.index_in_r3 ? q.w
                            : ((P.bg_index && j < (int64_t)P.n_bg) ? (uint32_t)__ldg(P.bg_index + j) : (uint32_t)j);
         const unsigned long long key = ((unsigned long long)q.z << 32) | (unsigned long long)i;
-        int tx0, tx1, ty0, ty1;
-        tile_span(q.x, q.y, sx, sy, tx0, tx1, ty0, ty1);
-        const int n = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-        int tx = tx0, t = ty0 * E.ntx + tx0;
-        for (int i = 0; i < n; ++i) {
+        for_span<WRAP>(q.x, q.y, sx, sy, E.ntx, [&](int t) {
             const uint32_t k = atomicAdd(&hist[t], 1u);
             const unsigned long long pos = eb + base[t] + k;
             if (pos < P.pair_cap) P.pairs[pos] = key;
             else dropped = true;
-            if (tx == tx1) {
-                tx = tx0;
-                t += E.ntx - (tx1 - tx0);
-            } else {
-                ++tx;
-                ++t;
-            }
-        }
+        });
     }
     if (__syncthreads_or(dropped) && threadIdx.x == 0) atomicOr(P.status, kStOverflow);
 }
@@ -273,10 +291,12 @@ cudaError_t launch_scatter(const BinParams& P, int n_envs, int max_words, int ma
     // 4: 18.7, 3: 18.6 ms per step; at 320x240 and 128x128 six are fastest
     // (6.8 vs 8.0 ms and 5.1 vs 6.2 ms with 4).
     if ((long long)max_T * P.tile_w * P.tile_h >= 640ll * 480 / 2 && smem < (size_t)29 * 1024) smem = 29 * 1024;
-    cudaError_t e = opt_in_smem((const void*)k_scatter, smem);
+    const void* fn = P.wrap ? (const void*)k_scatter<true> : (const void*)k_scatter<false>;
+    cudaError_t e = opt_in_smem(fn, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((max_words + P.words_per_block - 1) / P.words_per_block), (unsigned)n_envs);
-    k_scatter<<<grid, 256, smem, st>>>(P);
+    if (P.wrap) k_scatter<true><<<grid, 256, smem, st>>>(P);
+    else k_scatter<false><<<grid, 256, smem, st>>>(P);
     return cudaGetLastError();
 }
 

@@ -744,8 +744,18 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         sB[s] = make_float4(q1.x, q1.y, q1.z, __log2f(255.0f * q0.z));
                     }
                     sC[s] = q2;
-                    sR[s] = make_int4((int)(rx & 0xffffu), (int)((rx >> 16) - (rx & 0xffffu)), (int)(ry & 0xffffu),
-                                      (int)((ry >> 16) - (ry & 0xffffu)));
+                    int bx0 = (int)(rx & 0xffffu), bx1 = (int)(rx >> 16);
+                    if (LID && bx0 > bx1) {
+                        // a LiDAR box across azimuth 0 (columns [x0, cols) and
+                        // [0, x1]): the hull of its parts in this tile's columns
+                        // [ta, tb], the high part [max(x0, ta), tb] when x0 <= tb
+                        // and the low part [ta, min(x1, tb)] when x1 >= ta
+                        const int ta = tx * TW, tb = ta + TW - 1;
+                        const int h0 = max(bx0, ta), l1 = min(bx1, tb);
+                        bx0 = bx1 >= ta ? ta : h0;
+                        bx1 = h0 <= tb ? tb : l1;
+                    }
+                    sR[s] = make_int4(bx0, bx1 - bx0, (int)(ry & 0xffffu), (int)((ry >> 16) - (ry & 0xffffu)));
                     if constexpr (SC) sG[s] = g;
                 } else {  // never happens for a well-formed bucket; stage an empty range
                     sA[s] = make_float4(0.f, 0.f, 0.f, 0.f);

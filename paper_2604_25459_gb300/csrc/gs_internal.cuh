@@ -145,6 +145,7 @@ struct BinParams {
     int index_in_r3;
     const int* bg_index;
     unsigned int n_bg;
+    int wrap;  // LiDAR: a box with x0 > x1 covers columns [x0, cols) and [0, x1]
 };
 
 struct CompParams {

@@ -20,6 +20,12 @@
 // cell that a direction inside the cone can fall in, not only the cells whose
 // centres lie inside it), and the compositor walks a tile's keys for the rays
 // of that tile.
+//
+// A cone across the window's first column (azimuth 0 of a full turn) reaches
+// the first and the last columns: its box is stored wrapped, x0 > x1 meaning
+// columns [x0, cols) and [0, x1], which the binning kernels and the
+// compositor's LiDAR forms read as two ranges (a box over every column
+// between them would put the Gaussian in every tile of its rows).
 #include "gs_internal.cuh"
 
 namespace gsb {
@@ -102,16 +108,24 @@ __global__ void __launch_bounds__(256) k_project_lidar(ProjParams P) {
                         rel -= kTwoPi * floorf(rel / kTwoPi);
                         const float lo = rel - dphi - P.cell_pad * step, hi = rel + dphi + P.cell_pad * step;
                         // the cone's azimuths in this turn, and their copy one turn away
-                        // when the cone crosses 0 (a full revolution then takes the
-                        // columns between the two ranges as well)
+                        // when the cone crosses 0
                         int a0, a1, b0 = 0, b1 = -1;
                         const bool ina = grid_range(lo, hi, 0.0f, step, cols, a0, a1);
                         bool inb = false;
                         if (lo < 0.0f) inb = grid_range(lo + kTwoPi, hi + kTwoPi, 0.0f, step, cols, b0, b1);
                         else if (hi >= kTwoPi) inb = grid_range(lo - kTwoPi, hi - kTwoPi, 0.0f, step, cols, b0, b1);
                         if (ina && inb) {
-                            i0 = min(a0, b0);
-                            i1 = max(a1, b1);
+                            // two ranges, one from column 0 and one to the last
+                            // column: stored as a wrapped box i0 > i1 (columns
+                            // [i0, cols) and [0, i1]) unless they meet
+                            const int l1 = a0 <= b0 ? a1 : b1, h0 = a0 <= b0 ? b0 : a0;
+                            if (h0 <= l1 + 1) {
+                                i0 = 0;
+                                i1 = cols - 1;
+                            } else {
+                                i0 = h0;
+                                i1 = l1;
+                            }
                         } else if (ina) {
                             i0 = a0;
                             i1 = a1;

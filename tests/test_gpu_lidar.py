@@ -67,6 +67,55 @@ def test_lidar_scan_matches_oracle(window):
     scene.close()
 
 
+def test_lidar_cones_across_azimuth_zero():
+    """Gaussians straight ahead of a rotating LiDAR, where its columns wrap
+    (azimuth 0 is both the first and the last column): their cones reach both
+    ends of the grid, so their boxes are stored as two column ranges and each
+    Gaussian lands in the tiles of those columns only, not in every tile of
+    its rows; the scan there still matches the FP64 oracle."""
+    import torch
+
+    ensure_built()
+    rng = np.random.default_rng(23)
+    n = 300
+    # a patch of wall 3 m ahead: y across azimuth 0, z across the beams
+    mean = np.stack([3.0 + rng.normal(0.0, 0.01, n), rng.uniform(-0.25, 0.25, n), rng.uniform(-0.3, 0.3, n)], 1)
+    quat = rng.normal(size=(n, 4))
+    quat /= np.linalg.norm(quat, axis=1, keepdims=True)  # uniform random orientations (w, x, y, z)
+    ls = np.log(rng.uniform(0.02, 0.05, (n, 3)))
+    sh = rng.normal(0, 0.3, size=(n, 16, 3))
+    bg = synth.Gaussians(*(np.ascontiguousarray(a, np.float32) for a in
+                           (mean, quat, ls, rng.uniform(0.3, 0.95, n), sh)))
+    cams = synth.make_cameras(1, 50.0, 50.0, 32.0, 24.0, 64, 48, [[1, 0, 0, 0]], [[0, 0, 0]])
+    w = synth.Workload("wall", bg, np.zeros(1, np.int64), bg.slice(0, 0), np.zeros((1, 0, 7), np.float32), cams)
+    sens = np.zeros(1, dtype=gsbatch.LIDAR_DTYPE)
+    sens["q_ws"] = [1.0, 0.0, 0.0, 0.0]
+    sens["rows"], sens["cols"] = 16, 128  # 8 column tiles, one row of tiles
+    sens["elev_min"], sens["elev_max"], sens["near_range"] = -0.15, 0.15, 0.05
+    sens["az_min"], sens["az_max"] = 0.0, 2.0 * np.pi
+    # most of the patch's cones cross azimuth 0 (column width 2 pi / 128)
+    az = np.arctan2(mean[:, 1], mean[:, 0])
+    assert (np.abs(az) < np.pi / 128).sum() > n // 10
+    scene = gsbatch.scene_from_workload(w)
+    rg, hit = scene.render_lidar(None, sens)
+    torch.cuda.synchronize()
+    scene.sync_status()
+    keys = scene.stats()["intersections"]
+    print("Gaussians", n, "keys", keys)
+    assert 0 < keys <= 2 * n  # each in the first and/or last column tile of the one tile row
+    g_r, g_h = rg.cpu().numpy()[0], hit.cpu().numpy()[0]
+    ref = _oracle_scan(w, 0, sens[0])
+    dh = np.abs(g_h - ref["hit"])
+    both = (ref["hit"] >= 0.5) & (g_h >= 0.5)
+    rel = np.abs(g_r - ref["range"])[both] / ref["range"][both]
+    print("rays hit >= 0.5:", int(both.sum()), "in columns 0 and 127:", int(both[:, [0, 127]].sum()),
+          "hit max", dh.max(), "range rel max", rel.max() if rel.size else None)
+    assert both[:, 0].sum() > 3 and both[:, 127].sum() > 3
+    assert np.quantile(dh, 0.99) <= 2e-3 and dh.max() <= 0.05
+    assert np.quantile(rel, 0.99) <= 1e-4 and rel.max() <= 1e-2
+    scene.close()
+
+
 def test_lidar_argument_checks_and_empty_scene():
     import torch
 
