@@ -12,7 +12,9 @@
 // Since q(x) >= |x - mu|^2 / max_k e^{2 s_k} = |x - mu|^2 / max_k |f_k|^2, every
 // point with alpha >= 1/255 (q <= q*) lies within r = sqrt(q*) max_k |f_k| of
 // mu: the rays that can reach it lie within the cone of half-angle
-// asin(r / |mu|).
+// asin(r / |mu|).  The cone bounds the elevations; the azimuths are the exact
+// range of the ellipsoid's shadow on the sensor's xy-plane where that is
+// tighter (see below).
 //
 // Arbitrary rays (non-repetitive scan patterns) reuse the grid as a binning
 // structure: each ray falls in one cell of its sensor's (azimuth, beam) grid,
@@ -101,12 +103,41 @@ __global__ void __launch_bounds__(256) k_project_lidar(ProjParams P) {
                     any = grid_range(thc - rho - P.cell_pad * estep, thc + rho + P.cell_pad * estep, em, estep, rows,
                                      j0, j1);
                     if (any && fabsf(thc) + rho < kHalfPi) {
-                        const float dphi = asinf(fminf(1.0f, sinf(rho) / cosf(thc))) * 1.001f + 1e-5f;
+                        // azimuth half-widths below / above the centre: the cone's, and
+                        // where tighter the exact range of the Gaussian's shadow on the
+                        // xy-plane (azimuth depends on x and y only, so every ray that
+                        // meets {q <= q*} lies between the shadow's tangents from the
+                        // sensor).  In the frame of the centre direction e (normal n), with
+                        // S the shadow's covariance there and d the centre's distance, a
+                        // tangent y = k x solves k^2 (d^2 - q* s11) + 2 q* s12 k - q* s22 = 0.
+                        float dlo = asinf(fminf(1.0f, sinf(rho) / cosf(thc))) * 1.001f + 1e-5f, dhi = dlo;
+                        {
+                            const float d2 = mx * mx + my * my;
+                            const float id = rsqrtf(fmaxf(d2, 1e-30f));
+                            const float ex = mx * id, ey = my * id;
+                            const float Fm[9] = {a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3.x};
+                            float s11 = 0.0f, s12 = 0.0f, s22 = 0.0f;
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                const float fx = r0.x * Fm[k] + r0.y * Fm[3 + k] + r0.z * Fm[6 + k];
+                                const float fy = r1.x * Fm[k] + r1.y * Fm[3 + k] + r1.z * Fm[6 + k];
+                                const float pe = fx * ex + fy * ey, pn = fy * ex - fx * ey;
+                                s11 += pe * pe;
+                                s12 += pe * pn;
+                                s22 += pn * pn;
+                            }
+                            const float al = d2 - qstar * s11;
+                            if (al > 0.01f * d2) {  // the sensor well outside the shadow along e
+                                const float disc = sqrtf(qstar * qstar * s12 * s12 + al * qstar * s22);
+                                dhi = fminf(dhi, atanf((disc - qstar * s12) / al) * 1.001f + 1e-5f);
+                                dlo = fminf(dlo, atanf((disc + qstar * s12) / al) * 1.001f + 1e-5f);
+                            }
+                        }
                         // azimuth relative to the window start, within one turn: [0, 2 pi)
                         const float az0 = __ldg(&L->az_min), step = (__ldg(&L->az_max) - az0) / (float)cols;
                         float rel = atan2f(my, mx) - az0;
                         rel -= kTwoPi * floorf(rel / kTwoPi);
-                        const float lo = rel - dphi - P.cell_pad * step, hi = rel + dphi + P.cell_pad * step;
+                        const float lo = rel - dlo - P.cell_pad * step, hi = rel + dhi + P.cell_pad * step;
                         // the cone's azimuths in this turn, and their copy one turn away
                         // when the cone crosses 0
                         int a0, a1, b0 = 0, b1 = -1;
