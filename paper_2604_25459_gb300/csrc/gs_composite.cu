@@ -21,6 +21,7 @@
 // form (per-Gaussian blending weights, for pruning) and a LiDAR form (rays of
 // an (azimuth, beam) grid, Gaussians evaluated in ray space).
 #include "gs_internal.cuh"
+#include <type_traits>
 
 namespace gsb {
 
@@ -359,6 +360,7 @@ __device__ __forceinline__ float splat_alpha(const float4& A, const float4& B, f
 // with the paired FP32 instructions of sm_100+ (two round-to-nearest
 // operations per instruction, element for element the arithmetic of
 // splat_alpha, so the values are bit-identical).
+template <bool CLAMP = true>
 __device__ __forceinline__ float2 splat_alpha2(const float4& A, const float4& B, float fpx, float2 fpy) {
     const float dx = fpx - A.x;
     const float2 dy = __fadd2_rn(fpy, make_float2(-A.y, -A.y));
@@ -367,6 +369,7 @@ __device__ __forceinline__ float2 splat_alpha2(const float4& A, const float4& B,
     const float2 s = __fmul2_rn(make_float2(B.z, B.z), dy);
     const float2 q = __ffma2_rn(t, t, __fmul2_rn(s, s));
     const float2 a = __fmul2_rn(make_float2(A.z, A.z), make_float2(ex2_approx(-q.x), ex2_approx(-q.y)));
+    if constexpr (!CLAMP) return a;
     return make_float2(fminf(0.99f, a.x), fminf(0.99f, a.y));
 }
 
@@ -770,13 +773,18 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                 for (int c = 0; c < cnt_b; c += 32) {
                     const int j = c + lane;
                     bool ov = false;
-                    if (j < cnt_b) {
+                    if constexpr (!LID) {
+                        // camera splats: box, then the exact ellipse for large ones
+                        // (a box under 24 px in width + height is kept as it is: it
+                        // overstates the ellipse least), evaluated by every lane
+                        const int jj = j < cnt_b ? j : c;
+                        const int4 R = sR[jj];
+                        ov = j < cnt_b && R.x <= wx1 && R.x + R.y >= wx0 && R.z <= wy1 && R.z + R.w >= wy0;
+                        const bool rr = reaches_rect(sA[jj], sB[jj], (float)wx0 + 0.5f, (float)wy0 + 0.5f);
+                        ov = ov && (R.y + R.w < 24 || rr);
+                    } else if (j < cnt_b) {
                         const int4 R = sR[j];
                         ov = R.x <= wx1 && R.x + R.y >= wx0 && R.z <= wy1 && R.z + R.w >= wy0;
-                        // large splats: their box overstates the ellipse most (a box
-                        // under 24 px in width + height is kept as it is)
-                        if (!LID && ov && R.y + R.w >= 24)
-                            ov = reaches_rect(sA[j], sB[j], (float)wx0 + 0.5f, (float)wy0 + 0.5f);
                     }
                     uint32_t m;
                     if constexpr (QUAD) {
@@ -800,6 +808,14 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                         m = __ballot_sync(0xffffffffu, ov);
                     }
                     float2 score_pair = make_float2(0.0f, 0.0f);  // contribution pass only
+                    // Camera splats of opacity <= 0.98 never reach the 0.99 cap of
+                    // alpha (o 2^-q with q >= 0), so a chunk without brighter splats
+                    // walks a copy of the loop without the cap (non-quadrant form;
+                    // the quadrant form measured slower with the extra vote).
+                    bool clamp_chunk = true;
+                    if constexpr (!LID && !QUAD) clamp_chunk = __any_sync(0xffffffffu, j < cnt_b && sA[j].z > 0.98f);
+                    auto walk = [&](auto clamp_tag) {
+                    constexpr bool CL = decltype(clamp_tag)::value;
                     // two splats per iteration: their four alpha evaluations are
                     // independent; the blends then run in depth order
                     while (QUAD ? __any_sync(0xffffffffu, m != 0u) : m != 0u) {
@@ -836,7 +852,10 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             h20 = h20 && inb(R2, cx0, cy0);
                             h21 = h21 && inb(R2, cx1, cy1);
                         }
-                        if (LID && (h10 || h11 || h20 || h21)) {
+                        // Grid scans evaluate every lane's rays (no divergent branch, so
+                        // the vote below sees every lane); along arbitrary rays the
+                        // per-ray boxes cull so much that the branch pays.
+                        if (MODE == 1 || (MODE == 3 && (h10 || h11 || h20 || h21))) {
                             const float4 A1 = sA[j1], B1 = sB[j1], C1 = sC[j1], D1 = sD[LID ? j1 : 0];
                             const float4 A2 = sA[j2], B2 = sB[j2], C2 = sC[j2], D2 = sD[LID ? j2 : 0];
                             float2 al1, ts1, al2, ts2;
@@ -845,37 +864,88 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             const float a10 = al1.x, a11 = al1.y, a20 = al2.x, a21 = al2.y;
                             const float t10 = ts1.x, t11 = ts1.y, t20 = ts2.x, t21 = ts2.y;
                             const float4 none = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (h10 && a10 >= (1.0f / 255.0f)) {
-                                if constexpr (CNT) ++ncomp;
-                                blend(a10, none, t10, Tp.x, rp.x, gp.x, bp.x, dp.x, done0);
+                            bool voted = false;  // both splats blended by the vote path below
+                            if constexpr (MODE == 1) {
+                                // as in the camera form: both splats with selects unless a ray stops
+                                const bool u10 = h10 && a10 >= (1.0f / 255.0f), u11 = h11 && a11 >= (1.0f / 255.0f);
+                                const float2 am1 = make_float2(u10 ? a10 : 0.0f, u11 ? a11 : 0.0f);
+                                const float2 Tn1 =
+                                    __fmul2_rn(Tp, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am1.x, -am1.y)));
+                                const bool v20 = h20 && a20 >= (1.0f / 255.0f), v21 = h21 && a21 >= (1.0f / 255.0f);
+                                const float2 am2 = make_float2(v20 ? a20 : 0.0f, v21 ? a21 : 0.0f);
+                                const float2 Tn2 =
+                                    __fmul2_rn(Tn1, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am2.x, -am2.y)));
+                                const bool stop = Tn1.x < 1e-4f || Tn1.y < 1e-4f || Tn2.x < 1e-4f || Tn2.y < 1e-4f;
+                                if (!__any_sync(0xffffffffu, stop)) {
+                                    if constexpr (CNT) ncomp += (uint32_t)u10 + (uint32_t)u11 + (uint32_t)v20 + (uint32_t)v21;
+                                    dp = __ffma2_rn(__fmul2_rn(am1, Tp), ts1, dp);
+                                    dp = __ffma2_rn(__fmul2_rn(am2, Tn1), ts2, dp);
+                                    Tp = Tn2;
+                                    voted = true;
+                                }
                             }
-                            if (h11 && a11 >= (1.0f / 255.0f)) {
-                                if constexpr (CNT) ++ncomp;
-                                blend(a11, none, t11, Tp.y, rp.y, gp.y, bp.y, dp.y, done1);
+                            if (!voted) {
+                                if (h10 && a10 >= (1.0f / 255.0f)) {
+                                    if constexpr (CNT) ++ncomp;
+                                    blend(a10, none, t10, Tp.x, rp.x, gp.x, bp.x, dp.x, done0);
+                                }
+                                if (h11 && a11 >= (1.0f / 255.0f)) {
+                                    if constexpr (CNT) ++ncomp;
+                                    blend(a11, none, t11, Tp.y, rp.y, gp.y, bp.y, dp.y, done1);
+                                }
+                                if (h20 && !done0 && a20 >= (1.0f / 255.0f)) {
+                                    if constexpr (CNT) ++ncomp;
+                                    blend(a20, none, t20, Tp.x, rp.x, gp.x, bp.x, dp.x, done0);
+                                }
+                                if (h21 && !done1 && a21 >= (1.0f / 255.0f)) {
+                                    if constexpr (CNT) ++ncomp;
+                                    blend(a21, none, t21, Tp.y, rp.y, gp.y, bp.y, dp.y, done1);
+                                }
                             }
-                            if (h20 && !done0 && a20 >= (1.0f / 255.0f)) {
-                                if constexpr (CNT) ++ncomp;
-                                blend(a20, none, t20, Tp.x, rp.x, gp.x, bp.x, dp.x, done0);
-                            }
-                            if (h21 && !done1 && a21 >= (1.0f / 255.0f)) {
-                                if constexpr (CNT) ++ncomp;
-                                blend(a21, none, t21, Tp.y, rp.y, gp.y, bp.y, dp.y, done1);
-                            }
-                        } else if (!LID && (h10 || h11 || h20 || h21)) {
+                        } else if constexpr (!LID) {
                             const float4 A1 = sA[j1], B1 = sB[j1];
                             const float4 A2 = sA[j2], B2 = sB[j2];
-                            const float2 a1 = splat_alpha2(A1, B1, fpx, fpy);
-                            const float2 a2 = splat_alpha2(A2, B2, fpx, fpy);
+                            const float2 a1 = splat_alpha2<CL>(A1, B1, fpx, fpy);
+                            const float2 a2 = splat_alpha2<CL>(A2, B2, fpx, fpy);
                             const bool u10 = h10 && a1.x >= (1.0f / 255.0f);
                             const bool u11 = h11 && a1.y >= (1.0f / 255.0f);
                             float w1 = 0.0f, w2 = 0.0f;
-                            if (u10 || u11) {
+                            // Both splats' blends with plain selects while no pixel of the
+                            // warp stops at either (the common case); else one splat at a
+                            // time with the stop rule.  Either way the arithmetic is that
+                            // of blend2, so the images do not depend on the path taken.
+                            // Every lane of the warp reaches the vote: the camera path has
+                            // no divergent branch around it (branches here measured slower
+                            // than evaluating every lane's pixels).
+                            const float2 am1 = make_float2(u10 ? a1.x : 0.0f, u11 ? a1.y : 0.0f);
+                            const float2 Tn1 =
+                                __fmul2_rn(Tp, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am1.x, -am1.y)));
+                            const bool v20 = h20 && a2.x >= (1.0f / 255.0f);
+                            const bool v21 = h21 && a2.y >= (1.0f / 255.0f);
+                            const float2 am2 = make_float2(v20 ? a2.x : 0.0f, v21 ? a2.y : 0.0f);
+                            const float2 Tn2 =
+                                __fmul2_rn(Tn1, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am2.x, -am2.y)));
+                            const bool stop = Tn1.x < 1e-4f || Tn1.y < 1e-4f || Tn2.x < 1e-4f || Tn2.y < 1e-4f;
+                            if (!__any_sync(0xffffffffu, stop)) {
+                                if constexpr (CNT) ncomp += (uint32_t)u10 + (uint32_t)u11 + (uint32_t)v20 + (uint32_t)v21;
+                                const float4 C1 = sC[j1], C2 = sC[j2];
+                                const float2 x1 = __fmul2_rn(am1, Tp), x2 = __fmul2_rn(am2, Tn1);
+                                rp = __ffma2_rn(x1, make_float2(C1.x, C1.x), rp);
+                                gp = __ffma2_rn(x1, make_float2(C1.y, C1.y), gp);
+                                bp = __ffma2_rn(x1, make_float2(C1.z, C1.z), bp);
+                                dp = __ffma2_rn(x1, make_float2(A1.w, A1.w), dp);
+                                rp = __ffma2_rn(x2, make_float2(C2.x, C2.x), rp);
+                                gp = __ffma2_rn(x2, make_float2(C2.y, C2.y), gp);
+                                bp = __ffma2_rn(x2, make_float2(C2.z, C2.z), bp);
+                                dp = __ffma2_rn(x2, make_float2(A2.w, A2.w), dp);
+                                Tp = Tn2;
+                                w1 = x1.x + x1.y;
+                                w2 = x2.x + x2.y;
+                            } else {
                                 if constexpr (CNT) ncomp += (uint32_t)u10 + (uint32_t)u11;
                                 w1 = blend2(a1, u10, u11, sC[j1], A1.w, Tp, rp, gp, bp, dp, done0, done1);
-                            }
-                            const bool u20 = h20 && !done0 && a2.x >= (1.0f / 255.0f);
-                            const bool u21 = h21 && !done1 && a2.y >= (1.0f / 255.0f);
-                            if (u20 || u21) {
+                                const bool u20 = h20 && !done0 && a2.x >= (1.0f / 255.0f);
+                                const bool u21 = h21 && !done1 && a2.y >= (1.0f / 255.0f);
                                 if constexpr (CNT) ncomp += (uint32_t)u20 + (uint32_t)u21;
                                 w2 = blend2(a2, u20, u21, sC[j2], A2.w, Tp, rp, gp, bp, dp, done0, done1);
                             }
@@ -892,6 +962,10 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             }
                         }
                     }
+                    };
+                    if constexpr (LID || QUAD) walk(std::true_type{});
+                    else if (clamp_chunk) walk(std::true_type{});
+                    else walk(std::false_type{});
                     if (__all_sync(0xffffffffu, done0 && done1)) break;
                 }
             }
