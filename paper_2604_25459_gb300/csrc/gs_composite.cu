@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                                 const float2 am2 = make_float2(v20 ? a20 : 0.0f, v21 ? a21 : 0.0f);
                                 const float2 Tn2 =
                                     __fmul2_rn(Tn1, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am2.x, -am2.y)));
-                                const bool stop = Tn1.x < 1e-4f || Tn1.y < 1e-4f || Tn2.x < 1e-4f || Tn2.y < 1e-4f;
+                                const bool stop = Tn2.x < 1e-4f || Tn2.y < 1e-4f;  // Tn2 <= Tn1
                                 if (!__any_sync(0xffffffffu, stop)) {
                                     if constexpr (CNT) ncomp += (uint32_t)u10 + (uint32_t)u11 + (uint32_t)v20 + (uint32_t)v21;
                                     dp = __ffma2_rn(__fmul2_rn(am1, Tp), ts1, dp);
@@ -925,7 +925,9 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             const float2 am2 = make_float2(v20 ? a2.x : 0.0f, v21 ? a2.y : 0.0f);
                             const float2 Tn2 =
                                 __fmul2_rn(Tn1, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am2.x, -am2.y)));
-                            const bool stop = Tn1.x < 1e-4f || Tn1.y < 1e-4f || Tn2.x < 1e-4f || Tn2.y < 1e-4f;
+                            // Tn2 = Tn1 (1 - am2) <= Tn1 (1 - am2 <= 1, rounding is monotone),
+                            // so a pixel that stops at either splat has Tn2 < 1e-4
+                            const bool stop = Tn2.x < 1e-4f || Tn2.y < 1e-4f;
                             if (!__any_sync(0xffffffffu, stop)) {
                                 if constexpr (CNT) ncomp += (uint32_t)u10 + (uint32_t)u11 + (uint32_t)v20 + (uint32_t)v21;
                                 const float4 C1 = sC[j1], C2 = sC[j2];
