@@ -456,9 +456,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         }
     }
     CK(sc.xf.ensure(sizeof(LinkXf) * (size_t)std::max(wt.xf_items, 1)), "alloc link table");
-    CK(sc.r0.ensure(wt.recs * 16), "alloc records");
-    CK(sc.r1.ensure(wt.recs * 16), "alloc records");
-    CK(sc.r2.ensure(wt.recs * 16), "alloc records");
+    CK(sc.r012.ensure(wt.recs * 16 * kRecStride), "alloc records");
     CK(sc.r3.ensure(wt.recs * 16), "alloc records");
     CK(sc.mask.ensure(wt.words * 4), "alloc masks");
     CK(sc.counts.ensure(wt.tiles * 4), "alloc counts");
@@ -492,9 +490,9 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     P.envs = wt.envs;
     P.cams = wt.cams;
     P.xf = sc.xf.as<LinkXf>();
-    P.r0 = sc.r0.as<float4>();
-    P.r1 = sc.r1.as<float4>();
-    P.r2 = sc.r2.as<float4>();
+    P.r0 = sc.r012.as<float4>();
+    P.r1 = P.r0 + 1;
+    P.r2 = P.r0 + 2;
     P.r3 = sc.r3.as<uint4>();
     P.mask = sc.mask.as<uint32_t>();
     P.dbg_hxy = debug ? sc.dbg_hxy.as<float2>() : nullptr;
@@ -1668,9 +1666,11 @@ gs_status gs_debug_copy_records(gs_scene s, int env, uint8_t* visible, float* u,
     std::vector<float2> h(n_local);
     CK(cudaMemcpy(mask.data(), s->sc.mask.as<uint32_t>() + E.mask_base, mask.size() * 4, cudaMemcpyDeviceToHost),
        "copy");
-    CK(cudaMemcpy(a.data(), s->sc.r0.as<float4>() + E.rec_base, n_local * 16, cudaMemcpyDeviceToHost), "copy");
-    CK(cudaMemcpy(b.data(), s->sc.r1.as<float4>() + E.rec_base, n_local * 16, cudaMemcpyDeviceToHost), "copy");
-    CK(cudaMemcpy(c.data(), s->sc.r2.as<float4>() + E.rec_base, n_local * 16, cudaMemcpyDeviceToHost), "copy");
+    const float4* rec = s->sc.r012.as<float4>() + (size_t)kRecStride * E.rec_base;
+    const size_t pitch = 16 * kRecStride;
+    CK(cudaMemcpy2D(a.data(), 16, rec, pitch, 16, n_local, cudaMemcpyDeviceToHost), "copy");
+    CK(cudaMemcpy2D(b.data(), 16, rec + 1, pitch, 16, n_local, cudaMemcpyDeviceToHost), "copy");
+    CK(cudaMemcpy2D(c.data(), 16, rec + 2, pitch, 16, n_local, cudaMemcpyDeviceToHost), "copy");
     CK(cudaMemcpy(h.data(), s->sc.dbg_hxy.as<float2>() + E.rec_base, n_local * 8, cudaMemcpyDeviceToHost), "copy");
     if (visible) memset(visible, 0, (size_t)s->D.n);
     for (int64_t j = 0; j < n_local; ++j) {

@@ -727,9 +727,9 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                 const uint32_t g = (uint32_t)(keys[b + s] & 0xffffffffull);
                 if (g < n_local) {
                     const size_t ri = recbase + g;
-                    const float4 q0 = P.r0[ri];
-                    const float4 q1 = P.r1[ri];
-                    const float4 q2 = P.r2[ri];
+                    const float4 q0 = P.r0[kRecStride * ri];
+                    const float4 q1 = P.r1[kRecStride * ri];
+                    const float4 q2 = P.r2[kRecStride * ri];
                     const uint32_t rx = __float_as_uint(q1.w), ry = __float_as_uint(q2.w);
                     sA[s] = q0;
                     if constexpr (LID) {

@@ -15,8 +15,12 @@
 //   Per wave of envs (scratch), env el described by EnvInfo envs[el]:
 //     record slots: local index j = g for background Gaussians (padded to a
 //       multiple of 32), then the env's link Gaussians in storage order; slot
-//       (el, j) is at envs[el].rec_base + j in r0..r3, valid where bit j%32 of
-//       mask[envs[el].mask_base + j/32] is set.  Keys are (depth bits << 32 |
+//       (el, j) is slot s = envs[el].rec_base + j, valid where bit j%32 of
+//       mask[envs[el].mask_base + j/32] is set; its first three 16-byte words
+//       r0, r1, r2 lie side by side at float4 index kRecStride s of one array
+//       (the compositor gathers all three: two 32-byte sectors instead of
+//       three half-used ones), its fourth word r3 at index s of another (the
+//       binning reads only r3, coalesced across a warp).  Keys are (depth bits << 32 |
 //       i) with i the caller's local index (background: its index before the
 //       Morton reordering; links: j), so equal depths order by global index;
 //       the compositor maps i back to the record slot j.
@@ -34,6 +38,27 @@
 #include "gsbatch.h"
 
 namespace gsb {
+
+// float4 stride between the r0 (r1, r2) words of consecutive record slots
+// (r1 = r0 + 1, r2 = r0 + 2 in one array; see the layout above)
+constexpr int kRecStride = 3;
+
+// Stores the r0, r1, r2 words of a warp's 32 consecutive record slots
+// (slot0 = the slot of lane 0) from the warp's staging buffer st (96 float4:
+// word w of lane l at 3 l + w), with coalesced stores: lane l writes float4
+// l, l + 32 and l + 64 of the slots' interleaved region, each where its record
+// ((l + 32 k) / 3) is visible in m.  Direct per-lane stores at the 48-byte
+// stride would write half sectors.  Call with every lane of the warp, after
+// the lanes' staging writes and a __syncwarp().
+__device__ __forceinline__ void store_records(float4* r0, size_t slot0, const float4* st, uint32_t m, int lane) {
+    static_assert(kRecStride == 3, "three 16-byte words per record slot");
+    float4* dst = r0 + (size_t)kRecStride * slot0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = lane + 32 * k;
+        if ((m >> (i / 3)) & 1u) dst[i] = st[i];
+    }
+}
 
 enum : uint32_t {
     kStBadPose = 1u,     // zero or non-finite link pose quaternion

@@ -67,7 +67,7 @@ EnvInfo h_envs[kMaxWave + 1];
 ProjBlock h_blocks[kMaxBlocks];
 
 struct Layout {
-    size_t envs, blocks, cams, xf, r0, r1, r2, r3, mask, counts, off, cursor, env_total, env_base, work, pairs;
+    size_t envs, blocks, cams, xf, r012, r3, mask, counts, off, cursor, env_total, env_base, work, pairs;
 };
 
 Layout layout(int We, int nb, int xf_items, unsigned long long recs, unsigned long long words,
@@ -78,9 +78,7 @@ Layout layout(int We, int nb, int xf_items, unsigned long long recs, unsigned lo
     y.blocks = o;    o = up256(o + sizeof(ProjBlock) * (size_t)(nb > 0 ? nb : 1));
     y.cams = o;      o = up256(o + sizeof(gs_camera) * (size_t)We);
     y.xf = o;        o = up256(o + sizeof(LinkXf) * (size_t)xf_items);
-    y.r0 = o;        o = up256(o + recs * 16);
-    y.r1 = o;        o = up256(o + recs * 16);
-    y.r2 = o;        o = up256(o + recs * 16);
+    y.r012 = o;      o = up256(o + recs * 16 * kRecStride);
     y.r3 = o;        o = up256(o + recs * 16);
     y.mask = o;      o = up256(o + words * 4);
     y.counts = o;    o = up256(o + tiles * 4);
@@ -209,9 +207,9 @@ extern "C" gs_status gs_render_batch_noalloc(gs_scene s, int n_envs, const float
         P.envs = d_envs;
         P.cams = d_cams;
         P.xf = xf;
-        P.r0 = reinterpret_cast<float4*>(base + y.r0);
-        P.r1 = reinterpret_cast<float4*>(base + y.r1);
-        P.r2 = reinterpret_cast<float4*>(base + y.r2);
+        P.r0 = reinterpret_cast<float4*>(base + y.r012);
+        P.r1 = P.r0 + 1;
+        P.r2 = P.r0 + 2;
         P.r3 = reinterpret_cast<uint4*>(base + y.r3);
         P.mask = reinterpret_cast<uint32_t*>(base + y.mask);
         P.dbg_hxy = nullptr;

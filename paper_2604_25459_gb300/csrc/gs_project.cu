@@ -382,6 +382,7 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
     __shared__ int4 s_misc[kProjStageEnvs];     // W, H, xf_base, near plane (bits)
     __shared__ unsigned long long s_mb[kProjStageEnvs];  // visibility-word base
     __shared__ unsigned long long s_rb[kProjStageEnvs];  // record base
+    __shared__ float4 s_rec[8][3 * 32];                  // per warp: the records of an env, before their store
     const bool frame0 = blk.frame0 != 0;
     for (int c0 = blk.e0; c0 < blk.e1; c0 += kProjStageEnvs) {
     const int c1 = min(c0 + kProjStageEnvs, blk.e1);
@@ -478,9 +479,10 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
                         const uint32_t rx = (uint32_t)i0 | ((uint32_t)i1 << 16);
                         const uint32_t ry = (uint32_t)j0 | ((uint32_t)j1 << 16);
                         const size_t ri = (size_t)s_rb[ei] + local;
-                        P.r0[ri] = make_float4(u, v, a0.w, mz);
-                        P.r1[ri] = make_float4(l00, l01, l11, __uint_as_float(rx));
-                        P.r2[ri] = make_float4(r, gg, b, __uint_as_float(ry));
+                        float4* sr = s_rec[t >> 5] + 3 * lane;
+                        sr[0] = make_float4(u, v, a0.w, mz);
+                        sr[1] = make_float4(l00, l01, l11, __uint_as_float(rx));
+                        sr[2] = make_float4(r, gg, b, __uint_as_float(ry));
                         P.r3[ri] = make_uint4(rx, ry, __float_as_uint(mz), key_index);
                         if (P.dbg_hxy) P.dbg_hxy[ri] = make_float2(hx, hy);
                         vis = true;
@@ -489,6 +491,11 @@ __global__ void __launch_bounds__(256, 3) k_project(ProjParams P) {
             }
         }
         const uint32_t m = __ballot_sync(0xffffffffu, vis);
+        if (m) {  // warp-uniform
+            __syncwarp();
+            store_records(P.r0, (size_t)s_rb[ei] + local - lane, s_rec[t >> 5], m, lane);
+            __syncwarp();  // s_rec is rewritten for the next env
+        }
         if (lane == 0 && warp_live) {
             const unsigned long long mb = s_mb[ei];
             P.mask[(size_t)mb + (local >> 5)] = m;
