@@ -414,3 +414,35 @@ def test_device_resident_scene_inputs():
         sc.close()
     for a, b in zip(*outs):
         np.testing.assert_array_equal(a, b)
+
+
+def test_opaque_splats_cap_and_early_stop():
+    """c0 with 30 % of its splats near opaque (opacity U(0.9, 0.9999), scales
+    e^1.5 larger: alpha meets its 0.99 cap near their centres, and most pixels
+    stop, with T just above 1e-4, after a few splats).  The
+    compositor walks 32-splat chunks holding a splat of opacity > 0.98 with the
+    cap and the others without it, and blends both splats of a step at once
+    unless a pixel stops there: against the oracle (independent and keyed), and
+    bit for bit between the quadrant form (16x16 tiles at this size) and the
+    plain form (16x8 tiles)."""
+    w = synth.make_c0()
+    bg = w.background
+    rng = np.random.default_rng(7)
+    op = bg.opacity.copy()
+    sel = rng.random(bg.n) < 0.3
+    op[sel] = rng.uniform(0.9, 0.9999, int(sel.sum())).astype(op.dtype)
+    ls = bg.log_scale.copy()
+    ls[sel] += 1.5
+    w2 = synth.Workload(w.name, synth.Gaussians(bg.mean, bg.quat, ls, op, bg.sh), w.link_offsets, w.links,
+                        w.link_poses, w.cams)
+    out = gpu_render(w2, debug=True, keep_scene=True)
+    st_i, st_k, rec, proj = _keyed_check(w2, 0, out)
+    out["scene"].close()
+    print("opaque c0 independent", st_i, "keyed", st_k)
+    assert st_k["amb_frac"] < 0.1
+    vis = proj["valid"] == 1
+    assert int((proj["opacity"][vis] > 0.99).sum()) >= 100  # the cap is reached
+    assert float((out["alpha"][0] > 0.999).mean()) > 0.5  # most pixels stop early
+    plain = gpu_render(w2, tile=(16, 8))
+    for k in ("rgb", "depth", "alpha"):
+        assert np.array_equal(plain[k], out[k]), k
