@@ -460,6 +460,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     CK(sc.r3.ensure(wt.recs * 16), "alloc records");
     CK(sc.mask.ensure(wt.words * 4), "alloc masks");
     CK(sc.counts.ensure(wt.tiles * 4), "alloc counts");
+    CK(sc.zr.ensure((size_t)We * 8), "alloc depth ranges");
     CK(sc.off.ensure(wt.tiles * 4), "alloc offsets");
     CK(sc.cursor.ensure(wt.tiles * 4), "alloc cursors");
     CK(sc.env_total.ensure((size_t)We * 8), "alloc totals");
@@ -508,6 +509,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     ++*launches;
     // A3: counts + scan
     CK(cudaMemsetAsync(sc.counts.p, 0, wt.tiles * 4, st), "memset counts");
+    CK(cudaMemsetAsync(sc.zr.p, 0xff, (size_t)We * 8, st), "memset depth ranges");
     BinParams B{};
     B.envs = wt.envs;
     B.mask = P.mask;
@@ -525,6 +527,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
     B.wrap = io.lidars ? 1 : 0;         // LiDAR boxes may wrap across azimuth 0
     B.bg_index = s->bg_order.empty() ? nullptr : s->bg_index.as<int>();
     B.n_bg = (unsigned)s->D.n_bg;
+    B.zr = sc.zr.as<uint2>();
     PhaseTimer t3(s, st, GS_PHASE_COUNT, timers);
     CK(launch_count(B, We, wt.max_words, wt.max_T, st), "count");
     t3.done(1);
@@ -652,6 +655,7 @@ gs_status run_wave(gs_scene s, Scratch& sc, const WaveTables& wt, const WaveIO& 
         C.r0 = P.r0;
         C.r1 = P.r1;
         C.r2 = P.r2;
+        C.zr = sc.zr.as<uint2>();
         C.counts = sc.counts.as<uint32_t>();
         C.off_local = sc.off.as<uint32_t>();
         C.env_base = sc.env_base.as<unsigned long long>();

@@ -102,13 +102,20 @@ __device__ __forceinline__ int block_visible(const uint32_t* mask, int64_t w0, i
 // Rebuilds a block's tile histogram of env el's visible records (the block's
 // list from block_visible, records 32 w0 + lst[i]) in hist[0, T).  Neighbouring
 // threads take neighbouring records of the list.
-template <bool WRAP>
+// With RANGE, also the smallest and largest depth bits (r3.z) of the records
+// this thread visits, into zl and zh.
+template <bool WRAP, bool RANGE = false>
 __device__ __forceinline__ void block_histogram(const BinParams& P, const EnvInfo& E, int64_t w0, const uint16_t* lst,
-                                                int nvis, uint32_t* hist) {
+                                                int nvis, uint32_t* hist, uint32_t* zl = nullptr,
+                                                uint32_t* zh = nullptr) {
     const uint4* r3 = P.r3 + E.rec_base;
     const int sx = __ffs(P.tile_w) - 1, sy = __ffs(P.tile_h) - 1;
     for (int i = threadIdx.x; i < nvis; i += blockDim.x) {
         const uint4 q = r3[w0 * 32 + lst[i]];
+        if constexpr (RANGE) {
+            *zl = min(*zl, q.z);
+            *zh = max(*zh, q.z);
+        }
         for_span<WRAP>(q.x, q.y, sx, sy, E.ntx, [&](int t) { atomicAdd(&hist[t], 1u); });
     }
 }
@@ -128,7 +135,16 @@ __global__ void __launch_bounds__(256) k_count(BinParams P) {
     const int64_t w1 = min(w0 + (int64_t)P.words_per_block, words);
     for (int t = threadIdx.x; t < E.T; t += blockDim.x) hist[t] = 0;
     const int nvis = block_visible(P.mask + E.mask_base, w0, w1, wbuf, wtot);
-    block_histogram<WRAP>(P, E, w0, wbuf, nvis, hist);
+    uint32_t zl = 0xffffffffu, zh = 0u;
+    block_histogram<WRAP, true>(P, E, w0, wbuf, nvis, hist, &zl, &zh);
+    if (P.zr) {  // the env's depth-bit range: one atomic pair per warp
+        zl = __reduce_min_sync(0xffffffffu, zl);
+        zh = __reduce_max_sync(0xffffffffu, zh);
+        if ((threadIdx.x & 31) == 0 && zl <= zh) {
+            atomicMin(&P.zr[el].x, zl);
+            atomicMin(&P.zr[el].y, ~zh);
+        }
+    }
     __syncthreads();
     uint32_t* cnt = P.counts + E.tile_base;
     for (int t = threadIdx.x; t < E.T; t += blockDim.x) {

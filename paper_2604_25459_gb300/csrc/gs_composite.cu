@@ -1100,7 +1100,13 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         }
         if (!started) {
             started = true;
-            key_range(Lk, n, klo, kmax);
+            if (spill && P.zr) {  // the env's depth range bounds every key of its buckets
+                const uint2 r = P.zr[el];
+                klo = (unsigned long long)r.x << 32;
+                kmax = ((unsigned long long)~r.y << 32) | 0xffffffffull;
+            } else {
+                key_range(Lk, n, klo, kmax);
+            }
             if (!spill) {
                 seg = Lk;
                 seg_len = n;

@@ -55,9 +55,9 @@ struct DevBuf {
 // Device scratch of a render: one set per scene (eager calls) and one per plan.
 struct Scratch {
     DevBuf envs, blocks, cams, xf, r012, r3, mask, counts, off, cursor, env_total, env_base, pairs, dbg_hxy,
-        dbg_sorted, work, spill;  // r012: records' r0, r1, r2 interleaved (kRecStride)
-    DevBuf* all[17] = {&envs,  &blocks,   &cams,     &xf,    &r012,   &r3,        &mask, &counts, &off,
-                       &cursor, &env_total, &env_base, &pairs, &dbg_hxy, &dbg_sorted, &work, &spill};
+        dbg_sorted, work, spill, zr;  // r012: records' r0, r1, r2 interleaved (kRecStride); zr: depth ranges
+    DevBuf* all[18] = {&envs,   &blocks,    &cams,     &xf,    &r012,   &r3,         &mask, &counts, &off,
+                       &cursor, &env_total, &env_base, &pairs, &dbg_hxy, &dbg_sorted, &work, &spill, &zr};
     void release() {
         for (DevBuf* b : all) b->release();
     }

@@ -171,6 +171,10 @@ struct BinParams {
     const int* bg_index;
     unsigned int n_bg;
     int wrap;  // LiDAR: a box with x0 > x1 covers columns [x0, cols) and [0, x1]
+    // nullable, per env of the wave: (smallest depth bits, ~largest depth bits)
+    // of the env's visible records, taken by the count pass with atomicMin on
+    // both words (set to all ones before it)
+    uint2* zr;
 };
 
 struct CompParams {
@@ -182,6 +186,10 @@ struct CompParams {
     const float4* r0;
     const float4* r1;
     const float4* r2;
+    // nullable, per env of the wave: the depth-bit range of its keys (see
+    // BinParams::zr); long buckets are partitioned over it instead of over
+    // their own key range, which saves a pass over their keys
+    const uint2* zr;
     const uint32_t* counts;
     const uint32_t* off_local;
     const unsigned long long* env_base;
