@@ -346,20 +346,13 @@ __device__ __forceinline__ float group_sum(float v) {
     return v;
 }
 
-// alpha = min(0.99, o exp(-q/2)) = min(0.99, o 2^-((l00 dx + l01 dy)^2 + (l11 dy)^2))
+// alpha = min(0.99, o exp(-q/2)) = min(0.99, 2^(log2 o - (l00 dx + l01 dy)^2 - (l11 dy)^2))
 // where B = (l00, l01, l11) is the conic's upper Cholesky factor scaled by
-// sqrt(log2(e)/2): q is evaluated as a sum of two squares.
-__device__ __forceinline__ float splat_alpha(const float4& A, const float4& B, float dx, float dy) {
-    const float t = __fmaf_rn(B.y, dy, __fmul_rn(B.x, dx));
-    const float s = __fmul_rn(B.z, dy);
-    const float pw = -__fmaf_rn(t, t, __fmul_rn(s, s));
-    return fminf(0.99f, __fmul_rn(A.z, ex2_approx(pw)));
-}
-
-// The same alpha at a lane's two pixel centres (fpx, fpy.x) and (fpx, fpy.y),
-// with the paired FP32 instructions of sm_100+ (two round-to-nearest
-// operations per instruction, element for element the arithmetic of
-// splat_alpha, so the values are bit-identical).
+// sqrt(log2(e)/2): q is evaluated as a sum of two squares.  Evaluated at a
+// lane's two pixel centres (fpx, fpy.x) and (fpx, fpy.y) with the paired FP32
+// instructions of sm_100+ (two round-to-nearest operations per instruction).
+// CLAMP = false leaves out the 0.99 cap, for splats of opacity <= 0.98 (their
+// alpha stays below it).
 template <bool CLAMP = true>
 __device__ __forceinline__ float2 splat_alpha2(const float4& A, const float4& B, float fpx, float2 fpy) {
     const float dx = fpx - A.x;
@@ -367,8 +360,11 @@ __device__ __forceinline__ float2 splat_alpha2(const float4& A, const float4& B,
     const float bx = __fmul_rn(B.x, dx);
     const float2 t = __ffma2_rn(make_float2(B.y, B.y), dy, make_float2(bx, bx));
     const float2 s = __fmul2_rn(make_float2(B.z, B.z), dy);
-    const float2 q = __ffma2_rn(t, t, __fmul2_rn(s, s));
-    const float2 a = __fmul2_rn(make_float2(A.z, A.z), make_float2(ex2_approx(-q.x), ex2_approx(-q.y)));
+    // camera splats are staged with A.z = log2(o), folded into the exponent:
+    // alpha = 2^(log2 o - t^2 - s^2), two paired FMAs before the ex2
+    const float2 pw =
+        __ffma2_rn(make_float2(-t.x, -t.y), t, __ffma2_rn(make_float2(-s.x, -s.y), s, make_float2(A.z, A.z)));
+    const float2 a = make_float2(ex2_approx(pw.x), ex2_approx(pw.y));
     if constexpr (!CLAMP) return a;
     return make_float2(fminf(0.99f, a.x), fminf(0.99f, a.y));
 }
@@ -731,7 +727,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                     const float4 q1 = P.r1[kRecStride * ri];
                     const float4 q2 = P.r2[kRecStride * ri];
                     const uint32_t rx = __float_as_uint(q1.w), ry = __float_as_uint(q2.w);
-                    sA[s] = q0;
+                    sA[s] = LID ? q0 : make_float4(q0.x, q0.y, log2f(q0.z), q0.w);  // camera: log2(o)
                     if constexpr (LID) {
                         // g2 = |g2| (g0 x g1) / (|g0| |g1|): the rows of G are orthogonal
                         const float glen2 = __uint_as_float(P.r3[ri].w);
@@ -764,6 +760,7 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                     sA[s] = make_float4(0.f, 0.f, 0.f, 0.f);
                     sB[s] = sA[s];
                     sC[s] = sA[s];
+                    if constexpr (!LID) sA[s].z = -126.0f;  // log2 of a vanishing opacity
                     sR[s] = make_int4(1 << 20, -1, 1 << 20, -1);
                     atomicOr(P.status, kStOverflow);
                 }
@@ -813,7 +810,8 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                     // walks a copy of the loop without the cap (non-quadrant form;
                     // the quadrant form measured slower with the extra vote).
                     bool clamp_chunk = true;
-                    if constexpr (!LID && !QUAD) clamp_chunk = __any_sync(0xffffffffu, j < cnt_b && sA[j].z > 0.98f);
+                    if constexpr (!LID && !QUAD)  // staged log2(o) > log2(0.98)
+                        clamp_chunk = __any_sync(0xffffffffu, j < cnt_b && sA[j].z > -0.029146346f);
                     auto walk = [&](auto clamp_tag) {
                     constexpr bool CL = decltype(clamp_tag)::value;
                     // two splats per iteration: their four alpha evaluations are
@@ -1276,7 +1274,8 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
         const float dep = a > 0.0f ? d / a : 0.0f;
         if (P.rgb8) {
             auto q = [&](float v) {
-                v = fmaf(fmaf(v, gain, -0.5f), con, 0.5f + bri);
+                // no appearance given: the identity, exactly ((v - 0.5) + 0.5 would round)
+                if (P.appear) v = fmaf(fmaf(v, gain, -0.5f), con, 0.5f + bri);
                 return (uint8_t)__float2int_rn(fminf(fmaxf(v, 0.0f), 1.0f) * 255.0f);
             };
             P.rgb8[3 * pix] = q(cr);
