@@ -314,18 +314,18 @@ __device__ unsigned long long* window_sort(unsigned long long* keys, unsigned lo
 }
 
 // One pixel's blend step for a splat whose alpha is `al` (already >= 1/255);
-// returns the weight alpha T added (0 when the step stops instead):
-// T' = T (1 - alpha); stop (splat not added) when T' < 1e-4.  The products are
-// pinned to explicit round-to-nearest operations so every tile shape and
-// every pixel slot evaluates exactly the same arithmetic.
+// returns the weight w = alpha T added (0 when the step stops instead):
+// T' = T (1 - alpha), evaluated as T - w; stop (splat not added) when
+// T' < 1e-4.  The arithmetic is pinned to explicit round-to-nearest operations
+// so every tile shape and every pixel slot evaluates exactly the same.
 __device__ __forceinline__ float blend(float al, const float4& C, float z, float& T, float& r, float& g, float& b,
                                        float& d, bool& done) {
-    const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
+    const float w = __fmul_rn(al, T);
+    const float Tn = __fsub_rn(T, w);
     if (Tn < 1e-4f) {
         done = true;
         return 0.0f;
     }
-    const float w = __fmul_rn(al, T);
     r = __fmaf_rn(w, C.x, r);
     g = __fmaf_rn(w, C.y, g);
     b = __fmaf_rn(w, C.z, b);
@@ -376,11 +376,12 @@ __device__ __forceinline__ float2 splat_alpha2(const float4& A, const float4& B,
 __device__ __forceinline__ float blend2(float2 al, bool u0, bool u1, const float4& C, float z, float2& T, float2& r,
                                         float2& g, float2& b, float2& d, bool& done0, bool& done1) {
     const float2 am = make_float2(u0 ? al.x : 0.0f, u1 ? al.y : 0.0f);
-    const float2 Tn = __fmul2_rn(T, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am.x, -am.y)));
+    const float2 x = __fmul2_rn(am, T);
+    const float2 Tn = __fadd2_rn(T, make_float2(-x.x, -x.y));
     const bool s0 = u0 && Tn.x < 1e-4f, s1 = u1 && Tn.y < 1e-4f;
     done0 = done0 || s0;
     done1 = done1 || s1;
-    const float2 w = __fmul2_rn(make_float2(s0 ? 0.0f : am.x, s1 ? 0.0f : am.y), T);
+    const float2 w = make_float2(s0 ? 0.0f : x.x, s1 ? 0.0f : x.y);
     r = __ffma2_rn(w, make_float2(C.x, C.x), r);
     g = __ffma2_rn(w, make_float2(C.y, C.y), g);
     b = __ffma2_rn(w, make_float2(C.z, C.z), b);
@@ -867,17 +868,17 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                                 // as in the camera form: both splats with selects unless a ray stops
                                 const bool u10 = h10 && a10 >= (1.0f / 255.0f), u11 = h11 && a11 >= (1.0f / 255.0f);
                                 const float2 am1 = make_float2(u10 ? a10 : 0.0f, u11 ? a11 : 0.0f);
-                                const float2 Tn1 =
-                                    __fmul2_rn(Tp, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am1.x, -am1.y)));
+                                const float2 x1 = __fmul2_rn(am1, Tp);
+                                const float2 Tn1 = __fadd2_rn(Tp, make_float2(-x1.x, -x1.y));
                                 const bool v20 = h20 && a20 >= (1.0f / 255.0f), v21 = h21 && a21 >= (1.0f / 255.0f);
                                 const float2 am2 = make_float2(v20 ? a20 : 0.0f, v21 ? a21 : 0.0f);
-                                const float2 Tn2 =
-                                    __fmul2_rn(Tn1, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am2.x, -am2.y)));
+                                const float2 x2 = __fmul2_rn(am2, Tn1);
+                                const float2 Tn2 = __fadd2_rn(Tn1, make_float2(-x2.x, -x2.y));
                                 const bool stop = Tn2.x < 1e-4f || Tn2.y < 1e-4f;  // Tn2 <= Tn1
                                 if (!__any_sync(0xffffffffu, stop)) {
                                     if constexpr (CNT) ncomp += (uint32_t)u10 + (uint32_t)u11 + (uint32_t)v20 + (uint32_t)v21;
-                                    dp = __ffma2_rn(__fmul2_rn(am1, Tp), ts1, dp);
-                                    dp = __ffma2_rn(__fmul2_rn(am2, Tn1), ts2, dp);
+                                    dp = __ffma2_rn(x1, ts1, dp);
+                                    dp = __ffma2_rn(x2, ts2, dp);
                                     Tp = Tn2;
                                     voted = true;
                                 }
@@ -916,20 +917,19 @@ __global__ void __launch_bounds__(TW* TH / 2, (TW * TH >= 512 ? 4 : (TW * TH >= 
                             // no divergent branch around it (branches here measured slower
                             // than evaluating every lane's pixels).
                             const float2 am1 = make_float2(u10 ? a1.x : 0.0f, u11 ? a1.y : 0.0f);
-                            const float2 Tn1 =
-                                __fmul2_rn(Tp, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am1.x, -am1.y)));
+                            const float2 x1 = __fmul2_rn(am1, Tp);
+                            const float2 Tn1 = __fadd2_rn(Tp, make_float2(-x1.x, -x1.y));
                             const bool v20 = h20 && a2.x >= (1.0f / 255.0f);
                             const bool v21 = h21 && a2.y >= (1.0f / 255.0f);
                             const float2 am2 = make_float2(v20 ? a2.x : 0.0f, v21 ? a2.y : 0.0f);
-                            const float2 Tn2 =
-                                __fmul2_rn(Tn1, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-am2.x, -am2.y)));
-                            // Tn2 = Tn1 (1 - am2) <= Tn1 (1 - am2 <= 1, rounding is monotone),
+                            const float2 x2 = __fmul2_rn(am2, Tn1);
+                            const float2 Tn2 = __fadd2_rn(Tn1, make_float2(-x2.x, -x2.y));
+                            // Tn2 = Tn1 - am2 Tn1 <= Tn1 (am2 >= 0, rounding is monotone),
                             // so a pixel that stops at either splat has Tn2 < 1e-4
                             const bool stop = Tn2.x < 1e-4f || Tn2.y < 1e-4f;
                             if (!__any_sync(0xffffffffu, stop)) {
                                 if constexpr (CNT) ncomp += (uint32_t)u10 + (uint32_t)u11 + (uint32_t)v20 + (uint32_t)v21;
                                 const float4 C1 = sC[j1], C2 = sC[j2];
-                                const float2 x1 = __fmul2_rn(am1, Tp), x2 = __fmul2_rn(am2, Tn1);
                                 rp = __ffma2_rn(x1, make_float2(C1.x, C1.x), rp);
                                 gp = __ffma2_rn(x1, make_float2(C1.y, C1.y), gp);
                                 bp = __ffma2_rn(x1, make_float2(C1.z, C1.z), bp);
