@@ -38,9 +38,9 @@ UNIT = "env-frames/s"
 # DRAM traffic of the compositor per env of a launch, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over a 32-env launch, divided
 # by 32), valid only for the compositor sources it was taken on.
-COMPOSITE_TRAFFIC_PER_ENV = (0.678320e9 + 0.520330e9) / 32
+COMPOSITE_TRAFFIC_PER_ENV = (0.680517e9 + 0.523335e9) / 32
 COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu",)
-COMPOSITE_TRAFFIC_SHA = "4fdeb84b2294d864"
+COMPOSITE_TRAFFIC_SHA = "d79d0462f07becaa"
 
 
 def _sources_sha(paths) -> str:
