@@ -446,3 +446,44 @@ def test_opaque_splats_cap_and_early_stop():
     plain = gpu_render(w2, tile=(16, 8))
     for k in ("rgb", "depth", "alpha"):
         assert np.array_equal(plain[k], out[k]), k
+
+
+def test_crowded_depth_band_partition_and_selection():
+    """6,000 splats within 1e-3 m of one depth (3 m) in a few tiles, and a few
+    far splats (100 m) that widen the env's depth range.  Long buckets are
+    partitioned over the env's range, so the crowd falls into a single
+    partition bin, which the compositor cuts by radix selection: per-tile
+    depth-ordered lists bit-exact against the binning oracle fed the GPU's
+    keys, and the image against the oracle (independent and keyed)."""
+    w0 = synth.make_c0()
+    rng = np.random.default_rng(11)
+    n, nf = 6000, 16
+    mean = np.stack([rng.uniform(-0.05, 0.05, n), rng.uniform(-0.05, 0.05, n), rng.uniform(-1e-3, 1e-3, n)], 1)
+    q, ls, _, sh = synth._attributes(rng, n)
+    crowd = synth._gaussians(mean, q, ls - 0.5, rng.uniform(0.02, 0.2, n), sh)
+    fm = np.stack([rng.uniform(-20.0, 20.0, nf), rng.uniform(-15.0, 15.0, nf), np.full(nf, 97.0)], 1)
+    q2, ls2, o2, sh2 = synth._attributes(rng, nf)
+    far = synth._gaussians(fm, q2, np.zeros_like(ls2), o2, sh2)
+    bg = synth.Gaussians.concat([w0.background, crowd, far])
+    w = synth.Workload("crowd", bg, w0.link_offsets, w0.links, w0.link_poses, w0.cams)
+    W, H = 128, 96
+    out = gpu_render(w, debug=True, keep_scene=True)
+    scene = out["scene"]
+    rec = scene.debug_records(0, bg.n)
+    vis = np.nonzero(rec["visible"])[0]
+    assert rec["visible"][bg.n - nf:].sum() >= nf // 2  # the far splats widen the range
+    counts, lists = scene.debug_tiles(0, (W // 16) * (H // 16))
+    zb = rec["z"][vis].view(np.uint32)
+    oc, ol = oracle.bin_records(rec["u"][vis], rec["v"][vis], rec["hx"][vis], rec["hy"][vis], zb,
+                                vis.astype(np.uint32), W, H, 16, 16)
+    np.testing.assert_array_equal(counts.astype(np.int64), oc)
+    np.testing.assert_array_equal(lists, ol)
+    # the crowd's keys share one bin of the env's range (2048 bins over its depth bits)
+    lo, hi = int(zb.min()) << 32, (int(zb.max()) << 32) | 0xFFFFFFFF
+    shift = max(0, (hi - lo).bit_length() - 11)
+    crowd_keys = (zb[(vis >= w0.background.n) & (vis < bg.n - nf)].astype(np.uint64) << np.uint64(32))
+    bins = (crowd_keys - np.uint64(lo)) >> np.uint64(shift)
+    assert np.bincount(bins.astype(np.int64)).max() > 384 and counts.max() > 768
+    st_i, st_k, _, _ = _keyed_check(w, 0, out)
+    scene.close()
+    print("crowded band independent", st_i, "keyed", st_k)
