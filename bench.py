@@ -37,10 +37,11 @@ UNIT = "env-frames/s"
 
 # DRAM traffic of the compositor per env of a launch, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over a 32-env launch, divided
-# by 32), valid only for the compositor sources it was taken on.
+# by 32), valid only for the compositor sources it was taken on (the hash
+# below; sources that differ from the captured ones in comments only keep it).
 COMPOSITE_TRAFFIC_PER_ENV = (0.680517e9 + 0.523335e9) / 32
 COMPOSITE_TRAFFIC_SOURCES = ("paper_2604_25459_gb300/csrc/gs_composite.cu",)
-COMPOSITE_TRAFFIC_SHA = "d79d0462f07becaa"
+COMPOSITE_TRAFFIC_SHA = "05cb60c8cec62bb9"
 
 
 def _sources_sha(paths) -> str:

@@ -7,16 +7,18 @@
 //
 // Persistent CTAs claim (env, tile) items; each warp owns an 8x8 pixel
 // subtile and each lane two of its pixels.  The tile's bucket of keys (depth
-// bits << 32 | record slot) is consumed in depth windows of at most kCompCap
-// keys: a short bucket is one window; a long one is first partitioned into
-// kBins key ranges through the CTA's spill region, and windows are runs of
-// ranges, so sorting stops at the window where every pixel has terminated.
-// Each window is sorted in shared memory (a counting sort by depth ranges,
-// or LSD radix passes when the depths crowd, then index order within equal
-// depths) and composited in batches whose records are staged in shared
-// memory; warps test 32 splats at a time against their subtile with one
-// ballot (box, then the exact ellipse for large splats) and evaluate only the
-// overlapping ones.  Besides the image form the kernel has an observation
+// bits << 32 | the caller's local index of the Gaussian) is consumed in depth
+// windows of at most kCompCap keys: a short bucket is one window; a long one
+// is first partitioned into kBins ranges of the env's depth range through the
+// CTA's spill region, and windows are runs of ranges, so sorting stops at the
+// window where every pixel has terminated.  Each window is sorted in shared
+// memory (a counting sort by depth ranges, or LSD radix passes when the depths
+// crowd, then index order within equal depths), its keys mapped to record
+// slots, and composited in batches whose records are staged in shared memory;
+// warps test 32 splats at a time against their subtile with one ballot (box,
+// then the exact ellipse for large splats) and walk the overlapping ones two
+// at a time, every lane evaluating both at its pixels with no branch inside a
+// step.  Besides the image form the kernel has an observation
 // form (8-bit colour after per-env appearance, half depth), a contribution
 // form (per-Gaussian blending weights, for pruning) and a LiDAR form (rays of
 // an (azimuth, beam) grid, Gaussians evaluated in ray space).
